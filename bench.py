@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Throughput benchmark: RK4 integration of coupled HH networks on GB300.
+
+Default workload (the batched form): 4,096 independent networks, sizes
+U{20..300}, 80/20 E/I, pair probability U[0.1, 0.5], 200 ms at dt = 0.01 ms
+(20,000 RK4 steps), V recorded every 0.1 ms.  One benchmark step integrates
+the whole batch for ``--chunk`` RK4 steps (default 2,000 = 20 ms), so 10
+steps cover the full 200 ms.  Metric: neuron-RK4-steps per second
+(sum over networks of neurons x RK4 steps / time).
+
+Also reported: the single-network forward (the 120-neuron antennal-lobe
+network) on the same GPU, the roofline of the dominant kernel, the FP64
+oracle on the host cores (bounded sample) and an end-to-end number through
+the C interface with host buffers.
+
+Under torchrun each rank integrates its own batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "neuron-RK4-steps/sec FP32 (batched vs single); adjoint grad time / forward time"
+UNIT = "neuron-steps/s"
+
+# Algorithmic FP32 operation counts (FMA = 2) per unit and RK4 stage of the
+# formulation the kernels evaluate; kept in sync with the CUDA sources.
+FLOP_NEURON_STAGE = 80       # HH rates, currents, 4-variable stage update
+FLOP_COEF1_STAGE = 16        # per (presynaptic neuron, synapse type): T, r-map update
+FLOP_COEF2_STAGE = 20        # extra per (neuron, type) when second-order gates exist
+FLOP_SYN1_STAGE = 6          # first-order synapse: r = P + Q r0, w r (V - E) accumulate
+FLOP_SYN2_STAGE = 14         # second-order synapse: + s map, s^4 / (s^4 + Kd)
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+
+
+def workload_flops_per_step(spec) -> float:
+    """Algorithmic FLOP per RK4 step of the whole batch."""
+    kinds = spec.syn_params[:, 0]
+    nt = spec.syn_params.shape[0]
+    N = spec.n_neurons
+    syn2 = kinds[spec.syn_type] != 0
+    n_syn2 = int(syn2.sum())
+    n_syn1 = spec.n_synapses - n_syn2
+    # networks with second-order synapses pay the extra coefficient work
+    net_of_syn = np.searchsorted(spec.row_ptr[spec.net_neuron_off], np.nonzero(syn2)[0], side="right") - 1
+    has2 = np.zeros(spec.n_nets, bool)
+    has2[np.unique(net_of_syn)] = True
+    n_has2 = int(spec.net_sizes()[has2].sum())
+    per_stage = (FLOP_NEURON_STAGE * N + FLOP_COEF1_STAGE * N * nt + FLOP_COEF2_STAGE * n_has2 * nt
+                 + FLOP_SYN1_STAGE * n_syn1 + FLOP_SYN2_STAGE * n_syn2)
+    return 4.0 * per_stage
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1906_03958_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_1906_03958_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(p))
+    except Exception:
+        return None
+    e = t.get(f"{kernel}:{workload}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- cpu baseline
+
+def _oracle_job(args):
+    spec, nsteps = args
+    import oracle
+    t = time.perf_counter()
+    oracle.integrate(spec, oracle.rest_state(spec), nsteps)
+    return time.perf_counter() - t
+
+
+def cpu_sample(spec, n_nets: int, nsteps: int, seed: int = 0):
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(spec.n_nets, size=min(n_nets, spec.n_nets), replace=False))
+    return [spec.subset([int(b)]) for b in idx]
+
+
+def run_cpu_baseline(sample, nsteps: int, cores: int):
+    """FP64 oracle over the sample networks, one process per core (spawn)."""
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    neuron_steps = sum(s.n_neurons for s in sample) * nsteps
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_job, [(s, nsteps) for s in sample], chunksize=1)
+    wall = time.perf_counter() - t0
+    return neuron_steps / wall, wall
+
+
+# --------------------------------------------------------------- workloads
+
+def make_workload(name: str, rank: int):
+    from paper_1906_03958_gb300 import netgen as ng
+    if name == "batched":
+        return ng.batched(n_nets=4096, base_seed=4000 + 4096 * rank), \
+            "batched: 4096 HH networks, N~U{20..300}, 80/20 E/I, p~U[0.1,0.5], 200 ms, dt 0.01 ms", 20000
+    if name == "antennal_lobe":
+        return ng.antennal_lobe(seed=1002 + rank), \
+            "antennal lobe: 90 PN + 30 LN, ACh/GABA_A/GABA_B, 1000 ms, dt 0.01 ms", 100000
+    if name == "plain20":
+        return ng.plain20(seed=1001 + rank), "plain: 20 HH neurons, p=0.5, 100 ms, dt 0.01 ms", 10000
+    raise SystemExit(f"unknown workload {name}")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--chunk", type=int, default=2000, help="RK4 steps per benchmark step")
+    ap.add_argument("--workload", default="batched")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rec-stride", type=int, default=10)
+    ap.add_argument("--single-steps", type=int, default=20000)
+    ap.add_argument("--cpu-nets", type=int, default=64)
+    ap.add_argument("--cpu-steps", type=int, default=300)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    spec, wl_desc, sim_steps = make_workload(args.workload, rank)
+    cores = os.cpu_count() or 1
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # the FP64 oracle on the host cores, before any CUDA work (spawned pool)
+        sample = cpu_sample(spec, args.cpu_nets, args.cpu_steps)
+        val, wall = run_cpu_baseline(sample, args.cpu_steps, min(cores, len(sample)))
+        cpu = {"value": val, "unit": UNIT, "cores": min(cores, len(sample)), "kind": "oracle",
+               "sample": f"{len(sample)} networks drawn from the workload, {args.cpu_steps} RK4 steps each, "
+                         f"FP64, one process per core; {wall:.1f} s wall"}
+
+    import torch
+    from paper_1906_03958_gb300 import psst
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    psst.load()
+    frames = args.chunk // args.rec_stride if args.rec_stride else 0
+    net = psst.Network(spec, rec_stride=args.rec_stride, rec_capacity=max(frames, 1))
+    info = net.info()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        net.integrate(args.chunk)
+    net.status()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        net.integrate(args.chunk)
+        launches += net.info()["kernel_launches"]
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    net.status()
+    ms = ev0.elapsed_time(ev1)
+    t_local = ms / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_local], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        n = torch.tensor([float(spec.n_neurons)], device="cuda")
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        total_neurons = float(n.item())
+    else:
+        t_max, total_neurons = t_local, float(spec.n_neurons)
+    value = total_neurons * args.chunk * args.steps / t_max
+
+    # ---- end to end through the C interface with host buffers
+    dim = net.dim
+    h_state = torch.empty(dim, dtype=torch.float32).pin_memory()
+    h_state.copy_(net.get_state().cpu())
+    h_rec = torch.empty((max(frames, 1), spec.n_neurons), dtype=torch.float32).pin_memory()
+    h_out = torch.empty(dim, dtype=torch.float32).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        net.set_state(h_state)                  # H2D: the step's initial state
+        net.integrate(args.chunk)
+        net.read_record(out=h_rec.numpy())      # D2H: V frames of the chunk
+        net.get_state(out=h_out.numpy())        # D2H: final state
+    barrier()
+    e2e_t = time.perf_counter() - t0
+    e2e_val = spec.n_neurons * args.chunk * args.e2e_steps / e2e_t
+    h2d = dim * 4
+    d2h = frames * spec.n_neurons * 4 + dim * 4
+    net.status()
+    net.close()
+
+    # ---- single-network forward on the same GPU (context for "batched vs single")
+    single = None
+    if rank == 0:
+        from paper_1906_03958_gb300 import netgen as ng
+        al = ng.antennal_lobe()
+        with psst.Network(al) as sn:
+            sn.integrate(2000)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sn.integrate(args.single_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sn.status()
+            sms = e0.elapsed_time(e1)
+        single = {"workload": "antennal lobe, 120 neurons, one network per launch",
+                  "value": al.n_neurons * args.single_steps / (sms / 1e3), "unit": UNIT,
+                  "us_per_rk4_step": sms * 1e3 / args.single_steps}
+
+    # ---- roofline of the dominant kernel (the CTA-resident integrator)
+    peaks = measured_peaks()
+    smax = peaks.get("sm_max_mhz", 2070.0)
+    peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
+    flops_launch = workload_flops_per_step(spec) * args.chunk
+    dur = t_local / max(launches, 1)
+    roof = {"bound": "alu", "achieved": flops_launch / dur / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": flops_launch / dur / 1e12 / peak_tflops,
+            "traffic": traffic_for("cta_kernel", args.workload),
+            "kernel": "cta_kernel", "peak_source": f"FP32 FMA pipes: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                                    f"{smax:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": wl_desc, "rk4_steps_per_bench_step": args.chunk,
+                          "n_nets": spec.n_nets, "neurons": spec.n_neurons, "synapses": spec.n_synapses,
+                          "rec_stride": args.rec_stride, "l2": "working set larger than L2 (state+synapses "
+                          f"{(dim * 4 + spec.n_synapses * 8) / 1e6:.0f} MB)",
+                          "block_threads": info["block_threads"], "row_group": info["row_group"],
+                          "grid_ctas": info["grid_ctas"], "smem_bytes": info["smem_bytes"],
+                          "smem_nets": info["n_smem_nets"], "global_nets": info["n_global_nets"],
+                          "parallelism": f"replicas x{world}"},
+               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+               "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+               "single": single, "adjoint_over_forward": None}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def reference_arm(args, rank, world):
+    """The FP64 oracle as the reference implementation, on the host cores."""
+    if rank != 0:
+        return
+    spec, wl_desc, _ = make_workload(args.workload, 0)
+    cores = os.cpu_count() or 1
+    sample = cpu_sample(spec, args.cpu_nets, args.cpu_steps)
+    nc = min(cores, len(sample))
+    for _ in range(args.warmup):
+        run_cpu_baseline(sample[:nc], 20, nc)
+    times = []
+    for _ in range(args.steps):
+        _, wall = run_cpu_baseline(sample, args.cpu_steps, nc)
+        times.append(wall)
+    neuron_steps = sum(s.n_neurons for s in sample) * args.cpu_steps
+    t = sum(times)
+    value = neuron_steps * args.steps / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": wl_desc},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": nc, "kind": "oracle",
+                            "sample": f"{len(sample)} networks of the workload x {args.cpu_steps} RK4 steps per "
+                                      f"step, FP64, one process per core"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * psst.h -- C interface of the GB300 (sm_103a) library for fixed-step RK4
+ * integration of networks of coupled Hodgkin-Huxley neurons with kinetic
+ * synapses (Mohanta & Assisi, "Parallel scalable simulations of biological
+ * neural networks using TensorFlow", arXiv:1906.03958).
+ *
+ * The problem statement follows the paper:
+ *   - the initial value problem dy/dt = f(y, t), y(t0) = y0 (Eq. ode), with y
+ *     the vectorised state X' = [V, m, h, n] of Sec. "Brain simulations as
+ *     computational graphs" plus the synaptic variables;
+ *   - the recursion X_{i+1} = F(X_i, t_i, eps_i) over a time grid with F the
+ *     fourth-order Runge-Kutta step (same section, RK4 paragraph);
+ *   - synaptic variables stored sparsely, only for existing synapses
+ *     (Sec. "Circumventing memory constraints", item 1);
+ *   - a long simulation split into successive calls that continue from the
+ *     device-resident state (same section, item 2).
+ *
+ * Conventions for every function:
+ *   - return 0 (PSST_OK) or a negative PSST_ERR_* code; nothing throws
+ *     across this interface; psst_last_error() gives a message for the last
+ *     failing call on the calling thread;
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); device work is stream-ordered and asynchronous unless the
+ *     function says it synchronises;
+ *   - a handle is not thread-safe: one thread at a time per handle;
+ *   - all host arrays in psst_network_desc are read during
+ *     psst_create_network only; the caller keeps ownership.
+ */
+#ifndef PSST_H
+#define PSST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSST_OK 0
+#define PSST_ERR_INVALID_ARG (-1)  /* bad size, index, pointer or parameter */
+#define PSST_ERR_OOM (-2)          /* device allocation failed */
+#define PSST_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define PSST_ERR_NONFINITE (-4)    /* the state became NaN/Inf (device check) */
+#define PSST_ERR_TIMEOUT (-5)      /* a bounded device-wide wait gave up */
+#define PSST_ERR_STATE (-6)        /* call not valid in the handle's state */
+#define PSST_ERR_UNSUPPORTED (-7)  /* network shape outside what a mode handles */
+
+/* Columns of the neuron-type table (row per type), units mV, ms, uA/cm^2,
+   mS/cm^2, uF/cm^2:  C, gNa, gK, gL, ENa, EK, EL, gKL, EKL.
+   dV/dt = (I_ext - gNa m^3 h (V-ENa) - gK n^4 (V-EK) - gL (V-EL)
+            - gKL (V-EKL) - I_syn) / C, with the squid-axon rate functions
+   (-65 mV convention) for m, h, n. */
+#define PSST_NEURON_NPARAM 9
+/* Columns of the synapse-type table (row per type):
+   kind, a, b, K3, K4, Kd, E, Vp, Kp.
+   T = 1/(1+exp(-(V_pre-Vp)/Kp));
+   kind 0: dr/dt = a T (1-r) - b r,                         G = r;
+   kind 1: dr/dt = a T (1-r) - b r,  ds/dt = K3 r - K4 s,   G = s^4/(s^4+Kd);
+   current into the postsynaptic neuron: w G (V_post - E). */
+#define PSST_SYN_NPARAM 9
+#define PSST_MAX_SYN_TYPES 8
+
+/* Execution modes. */
+#define PSST_MODE_AUTO 0  /* CTA mode when every network fits one CTA, else grid */
+#define PSST_MODE_CTA 1   /* one CTA integrates one network at a time, many
+                             networks per launch (batched, ragged) */
+#define PSST_MODE_GRID 2  /* one network spread over the whole GPU with a
+                             device-wide barrier per RK4 stage (single network) */
+
+/*
+ * A batch of independent networks.  Neurons are numbered globally
+ * 0..N-1 (network b owns net_neuron_off[b] .. net_neuron_off[b+1]-1);
+ * synapses form one CSR matrix over the global rows, row = postsynaptic
+ * neuron, with the presynaptic index local to the row's network.
+ * State layout everywhere (get/set/init): [V(N), m(N), h(N), n(N), r(S), s(S)],
+ * float32.  Input current of neuron i at step k (held over the step's four
+ * stages, the paper's eps_i read as the step):
+ *   i_const[i] + (pulse_on[b] <= k < pulse_off[b] ? pulse_amp[i] : 0)
+ *   + (noise event ? noise_amp : 0),
+ * where the noise event is (Philox4x32-10(counter = {k lo, k hi, i, 0},
+ * key = {seed lo, seed hi}) word 0 >> 8) < noise_thresh.
+ */
+typedef struct {
+    int32_t n_nets;
+    const int32_t *net_neuron_off; /* [n_nets+1], increasing, starts at 0 */
+    const int32_t *neuron_type;    /* [N], 0..n_neuron_types-1 */
+    int32_t n_neuron_types;
+    const float *neuron_params;    /* [n_neuron_types * PSST_NEURON_NPARAM] */
+    const int64_t *row_ptr;        /* [N+1], row_ptr[0] = 0, non-decreasing */
+    const int32_t *pre;            /* [S], presynaptic neuron, local to the net */
+    const float *weight;           /* [S], maximal synaptic conductance */
+    const int32_t *syn_type;       /* [S], 0..n_syn_types-1 */
+    int32_t n_syn_types;           /* 1..PSST_MAX_SYN_TYPES */
+    const float *syn_params;       /* [n_syn_types * PSST_SYN_NPARAM] */
+    const float *i_const;          /* [N] */
+    const float *pulse_amp;        /* [N] or NULL (no pulse) */
+    const int64_t *pulse_on;       /* [n_nets] or NULL */
+    const int64_t *pulse_off;      /* [n_nets] or NULL */
+    uint64_t noise_seed;
+    uint32_t noise_thresh;         /* 0 = no noise; at most 2^24 */
+    float noise_amp;
+    float dt;                      /* ms, > 0 */
+    const float *init_state;       /* [4N+2S] or NULL: V=-65, gates at rest, r=s=0 */
+    int32_t rec_stride;            /* record V after global step k when k % stride == 0; 0 = off */
+    int64_t rec_capacity;          /* frames in the record ring buffer (>= 1 if stride > 0) */
+    int32_t mode;                  /* PSST_MODE_* */
+    int32_t block_threads;         /* CTA size (multiple of 32, <= 1024), 0 = tuned */
+    int32_t row_group;             /* lanes per CSR row in the reduction (1,2,...,32), 0 = tuned */
+    int32_t device;                /* CUDA device ordinal, -1 = current device */
+} psst_network_desc;
+
+typedef struct {
+    int32_t n_nets;
+    int64_t n_neurons, n_synapses;
+    int64_t steps_done;            /* global step index of the current state */
+    int64_t rec_frames;            /* frames recorded so far (all calls) */
+    int32_t mode, block_threads, row_group, grid_ctas;
+    int32_t smem_bytes;            /* dynamic shared memory per CTA */
+    int32_t n_smem_nets;           /* networks whose synapses live in shared memory */
+    int32_t n_global_nets;         /* networks whose synapses stay in global memory */
+    int32_t kernel_launches;       /* kernels the last psst_integrate enqueued */
+} psst_info;
+
+typedef struct psst_net psst_net;
+
+/* Validate the description, build the device layout and copy everything to
+   the device (synchronous).  Reads the host arrays of *d only during the
+   call.  Allocates device memory owned by the handle until
+   psst_destroy_network.  Errors: INVALID_ARG (with a message naming the
+   offending field/index), OOM, CUDA, UNSUPPORTED. */
+int psst_create_network(const psst_network_desc *d, psst_net **out);
+
+/* Advance every network by n_steps RK4 steps from the current state
+   (Sec. "Circumventing memory constraints", item 2: successive calls
+   continue where the previous one stopped; results are bitwise independent
+   of how the steps are split into calls).  Asynchronous on `stream`;
+   device-side failures (NONFINITE, TIMEOUT) are reported by psst_status.
+   n_steps = 0 is a no-op.  Errors: INVALID_ARG (n_steps < 0), CUDA. */
+int psst_integrate(psst_net *h, int64_t n_steps, void *stream);
+
+/* Synchronise `stream` and return the device error word (0 if none), then
+   clear it. */
+int psst_status(psst_net *h, void *stream);
+
+/* Copy the state [V, m, h, n, r, s] (4N+2S floats) to dst (host or device
+   memory as dst_on_device says), stream-ordered; synchronises the stream
+   when dst is on the host.  Errors: INVALID_ARG if n < 4N+2S. */
+int psst_get_state(const psst_net *h, float *dst, size_t n, int dst_on_device, void *stream);
+
+/* Overwrite the state from src (4N+2S floats, host or device). */
+int psst_set_state(psst_net *h, const float *src, size_t n, int src_on_device, void *stream);
+
+/* Set the global step index (time = step * dt) used for inputs and
+   recording; resets the record ring buffer. */
+int psst_set_step(psst_net *h, int64_t step);
+
+/* Copy the recorded V frames, oldest first, into dst ([frames][N] floats,
+   host or device); at most min(cap_frames, rec_capacity, frames recorded)
+   frames; *n_frames receives the count.  The ring keeps the newest
+   rec_capacity frames. Synchronises the stream when dst is on the host. */
+int psst_read_record(const psst_net *h, float *dst, size_t cap_frames, int64_t *n_frames,
+                     int dst_on_device, void *stream);
+
+/* Sizes, progress and the launch configuration. */
+int psst_query(const psst_net *h, psst_info *out);
+
+/* Free all device memory of the handle (synchronises its device). NULL is a no-op. */
+int psst_destroy_network(psst_net *h);
+
+/* Static description of an error code. */
+const char *psst_error_string(int code);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *psst_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSST_H */

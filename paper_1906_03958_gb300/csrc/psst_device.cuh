@@ -1,0 +1,169 @@
+// Device-side data view and model arithmetic shared by the CUDA kernels.
+//
+// Model (the paper gives the HH model only by name and state vector,
+// Sec. "Brain simulations as computational graphs"; the equations are the
+// textbook squid-axon set in the -65 mV convention):
+//   C dV/dt = I_ext - gNa m^3 h (V-ENa) - gK n^4 (V-EK) - gL (V-EL)
+//             - gKL (V-EKL) - I_syn
+//   dx/dt  = alpha_x(V) (1-x) - beta_x(V) x,   x in {m, h, n}
+//   synapse gate r (first order) or pair r, s (second order) per synapse,
+//   driven by the presynaptic transmitter T(V_pre); I_syn = sum w G (V-E).
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/psst.h"
+
+namespace psst {
+
+// Device pointers and sizes of one batch of networks (see psst.h for the
+// meaning of each array).  Passed by value to every kernel.
+struct NetView {
+    int n_nets;
+    int n_stypes;
+    long long N, S;
+    const int *net_off;          // [n_nets+1]
+    const long long *row_ptr;    // [N+1]
+    const uint32_t *syn_code;    // [S]: (type << 24) | (pre_local * n_stypes + type)
+    const float *weight;         // [S]
+    const int *neuron_type;      // [N]
+    const float *nparams;        // [n_ntypes * 9]
+    const float *sparams;        // [n_stypes * 9]
+    const float *i_const;        // [N]
+    const float *pulse_amp;      // [N] or null
+    const long long *pulse_on;   // [n_nets]
+    const long long *pulse_off;  // [n_nets]
+    unsigned long long noise_seed;
+    uint32_t noise_thresh;
+    float noise_amp;
+    float dt;
+    float *state;                // [4N + 2S]: V, m, h, n, r, s
+    float *rec;                  // [rec_cap][N] ring of V frames, or null
+    int rec_stride;
+    long long rec_cap;
+    const int *order;            // [n_nets] network processing order
+    const uint8_t *net_flags;    // [n_nets]: bit 0 second-order synapses, bit 1 synapses fit smem
+    int *work_counter;           // scratch: next work item
+    int *err;                    // device error word (first error wins)
+};
+
+enum : uint8_t { NET_HAS2 = 1, NET_FITS_SMEM = 2 };
+
+// Column indices of the parameter tables.
+enum { NP_C = 0, NP_GNA, NP_GK, NP_GL, NP_ENA, NP_EK, NP_EL, NP_GKL, NP_EKL };
+enum { SP_KIND = 0, SP_A, SP_B, SP_K3, SP_K4, SP_KD, SP_E, SP_VP, SP_KP };
+
+// Shared-memory layout of one network in the CTA kernel.  Computed the same
+// way on host (sizing) and device (addressing).  Offsets in bytes, 16-aligned.
+struct Layout {
+    int c2cur, c2fin, c2acc;  // float4 [N*nt]: s-coefficients (second order only)
+    int c1cur, c1fin, c1acc;  // float2 [N*nt]: r-coefficients
+    int y0, ys, acc;          // float [4N]: step-start state, stage state, k-sum
+    int prm;                  // float [9N]: 1/C, gNa, gK, gL, ENa, EK, EL, gKL, EKL
+    int iext, isyn;           // float [N]
+    int rowp;                 // int [N+1]
+    int r, s, w, code;        // [S] each when synapses live in smem (s only second order)
+    int total;
+};
+
+__host__ __device__ inline int lay_take(int &o, long long bytes) {
+    int at = o;
+    o += (int)((bytes + 15) & ~15LL);
+    return at;
+}
+
+__host__ __device__ inline Layout make_layout(int N, int S, int nt, bool has2, bool syn_smem) {
+    Layout L;
+    int o = 0;
+    const long long M = (long long)N * nt;
+    L.c2cur = has2 ? lay_take(o, 16 * M) : -1;
+    L.c2fin = has2 ? lay_take(o, 16 * M) : -1;
+    L.c2acc = has2 ? lay_take(o, 16 * M) : -1;
+    L.c1cur = lay_take(o, 8 * M);
+    L.c1fin = lay_take(o, 8 * M);
+    L.c1acc = lay_take(o, 8 * M);
+    L.y0 = lay_take(o, 16LL * N);
+    L.ys = lay_take(o, 16LL * N);
+    L.acc = lay_take(o, 16LL * N);
+    L.prm = lay_take(o, 36LL * N);
+    L.iext = lay_take(o, 4LL * N);
+    L.isyn = lay_take(o, 4LL * N);
+    L.rowp = lay_take(o, 4LL * (N + 1));
+    L.r = syn_smem ? lay_take(o, 4LL * S) : -1;
+    L.w = syn_smem ? lay_take(o, 4LL * S) : -1;
+    L.code = syn_smem ? lay_take(o, 4LL * S) : -1;
+    L.s = (syn_smem && has2) ? lay_take(o, 4LL * S) : -1;
+    L.total = o;
+    return L;
+}
+
+// ---------------------------------------------------------------- maths
+
+// u / (1 - exp(-u)); the removable singularity at u = 0 (alpha_m at -40 mV,
+// alpha_n at -55 mV) is evaluated by its Bernoulli series for |u| < 0.1,
+// where the FP32 difference 1 - exp(-u) would cancel.
+__device__ __forceinline__ float ratio_u(float u) {
+    if (fabsf(u) < 0.1f) {
+        const float u2 = u * u;
+        return fmaf(u2, fmaf(u2, -1.0f / 720.0f, 1.0f / 12.0f), fmaf(0.5f, u, 1.0f));
+    }
+    return __fdividef(u, 1.0f - __expf(-u));
+}
+
+struct Rates {
+    float am, bm, ah, bh, an, bn;
+};
+
+// Squid-axon rate functions (1/ms), V in mV, -65 mV rest convention.
+__device__ __forceinline__ Rates hh_rates(float V) {
+    Rates r;
+    r.am = ratio_u((V + 40.0f) * 0.1f);
+    r.bm = 4.0f * __expf((V + 65.0f) * (-1.0f / 18.0f));
+    r.ah = 0.07f * __expf((V + 65.0f) * (-1.0f / 20.0f));
+    r.bh = __frcp_rn(1.0f + __expf((V + 35.0f) * (-0.1f)));
+    r.an = 0.1f * ratio_u((V + 55.0f) * 0.1f);
+    r.bn = 0.125f * __expf((V + 65.0f) * (-1.0f / 80.0f));
+    return r;
+}
+
+// Transmitter release T(V_pre) = 1 / (1 + exp(-(V - Vp) / Kp)).
+__device__ __forceinline__ float transmitter(float V, float Vp, float inv_Kp) {
+    return __frcp_rn(1.0f + __expf((Vp - V) * inv_Kp));
+}
+
+// Philox4x32-10 (Salmon et al., SC'11), word 0 of the output block.
+__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return c0;
+}
+
+// External current of global neuron gi (network b) during global step k.
+__device__ __forceinline__ float input_current(const NetView &v, int b, long long gi, long long k) {
+    float I = v.i_const[gi];
+    if (v.pulse_amp && k >= v.pulse_on[b] && k < v.pulse_off[b]) I += v.pulse_amp[gi];
+    if (v.noise_thresh) {
+        const uint32_t x = philox_word0((uint32_t)k, (uint32_t)((unsigned long long)k >> 32),
+                                        (uint32_t)gi, 0u, (uint32_t)v.noise_seed,
+                                        (uint32_t)(v.noise_seed >> 32));
+        if ((x >> 8) < v.noise_thresh) I += v.noise_amp;
+    }
+    return I;
+}
+
+__device__ __forceinline__ void set_error(int *err, int code) { atomicCAS(err, 0, code); }
+
+}  // namespace psst
