@@ -335,7 +335,8 @@ def main():
                           f"{(dim * 4 + spec.n_synapses * 8) / 1e6:.0f} MB)",
                           "block_threads": info["block_threads"], "row_group": info["row_group"],
                           "grid_ctas": info["grid_ctas"], "smem_bytes": info["smem_bytes"],
-                          "smem_nets": info["n_smem_nets"], "global_nets": info["n_global_nets"],
+                          "single_cta_nets": info["n_single_cta_nets"], "cluster_nets": info["n_cluster_nets"],
+                          "launch_classes": info["n_launch_classes"],
                           "parallelism": f"replicas x{world}"},
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,

@@ -62,8 +62,9 @@ extern "C" {
 
 /* Execution modes. */
 #define PSST_MODE_AUTO 0  /* CTA mode when every network fits one CTA, else grid */
-#define PSST_MODE_CTA 1   /* one CTA integrates one network at a time, many
-                             networks per launch (batched, ragged) */
+#define PSST_MODE_CTA 1   /* each network held on chip by one CTA or a cluster of
+                             2 or 4 CTAs for all steps; many networks per launch
+                             (batched, ragged), one launch per size class */
 #define PSST_MODE_GRID 2  /* one network spread over the whole GPU with a
                              device-wide barrier per RK4 stage (single network) */
 
@@ -114,10 +115,12 @@ typedef struct {
     int64_t n_neurons, n_synapses;
     int64_t steps_done;            /* global step index of the current state */
     int64_t rec_frames;            /* frames recorded so far (all calls) */
-    int32_t mode, block_threads, row_group, grid_ctas;
-    int32_t smem_bytes;            /* dynamic shared memory per CTA */
-    int32_t n_smem_nets;           /* networks whose synapses live in shared memory */
-    int32_t n_global_nets;         /* networks whose synapses stay in global memory */
+    int32_t mode, block_threads, row_group; /* block/row_group of the smallest-network class */
+    int32_t grid_ctas;             /* CTAs of one integrate chunk (all launches) */
+    int32_t smem_bytes;            /* largest dynamic shared memory per CTA */
+    int32_t n_single_cta_nets;     /* CTA mode: networks held by one CTA */
+    int32_t n_cluster_nets;        /* CTA mode: networks spread over a cluster of 2 or 4 CTAs */
+    int32_t n_launch_classes;      /* CTA mode: launches per integrate chunk (size classes) */
     int32_t kernel_launches;       /* kernels the last psst_integrate enqueued */
 } psst_info;
 
@@ -137,6 +140,13 @@ int psst_create_network(const psst_network_desc *d, psst_net **out);
    device-side failures (NONFINITE, TIMEOUT) are reported by psst_status.
    n_steps = 0 is a no-op.  Errors: INVALID_ARG (n_steps < 0), CUDA. */
 int psst_integrate(psst_net *h, int64_t n_steps, void *stream);
+
+/* Grid mode only: time limit of one wait at the device-wide barrier between
+   RK4 stages (default 2 s).  On expiry the kernel records PSST_ERR_TIMEOUT,
+   every CTA returns, and the state keeps its value from before the call's
+   first step that failed.  0 makes every wait give up at once (a way to
+   exercise the error path without a hang). */
+int psst_set_barrier_timeout(psst_net *h, int64_t timeout_ns);
 
 /* Synchronise `stream` and return the device error word (0 if none), then
    clear it. */

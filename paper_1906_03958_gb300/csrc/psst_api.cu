@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <numeric>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -11,6 +12,7 @@
 
 #include "../../include/psst.h"
 #include "psst_internal.h"
+#include "psst_syn.cuh"
 
 using psst::NetView;
 
@@ -51,6 +53,8 @@ void rest_gates(double V, double out[3]) {
 struct psst_net {
     int device = 0;
     NetView v{};
+    psst::GridView gv{};
+    std::vector<psst::ClassLaunch> classes;  // CTA mode: one launch per size class
     std::vector<void *> allocs;
     long long step = 0;       // global step index of the current state
     long long rec_reset = 0;  // step at which the record ring was last reset
@@ -170,12 +174,214 @@ int validate(const psst_network_desc *d) {
     return PSST_OK;
 }
 
-// Lanes per CSR row: the power of two nearest half the mean row length,
-// clamped to 4..32.
-int default_row_group(double mean_row) {
-    int g = 4;
-    while (g < 32 && g < mean_row * 0.5) g <<= 1;
+// Per-row chunk counts (first- and second-order parts padded to 4) of the
+// whole batch, and which networks hold second-order synapses.
+void row_chunk_counts(const psst_network_desc *d, std::vector<int> &rowch, std::vector<uint8_t> &has2) {
+    const long long N = d->net_neuron_off[d->n_nets];
+    rowch.assign((size_t)N, 0);
+    has2.assign((size_t)d->n_nets, 0);
+    for (int b = 0; b < d->n_nets; ++b) {
+        for (long long i = d->net_neuron_off[b]; i < d->net_neuron_off[b + 1]; ++i) {
+            int n1 = 0, n2 = 0;
+            for (long long k = d->row_ptr[i]; k < d->row_ptr[i + 1]; ++k) {
+                if (d->syn_params[(size_t)d->syn_type[k] * PSST_SYN_NPARAM] != 0.0f) ++n2;
+                else ++n1;
+            }
+            rowch[i] = psst::row_chunks(n1, n2);
+            if (n2) has2[b] = 1;
+        }
+    }
+}
+
+// Split rows [0, n) with per-row cost into `parts` contiguous blocks of
+// about equal cost.  split has parts + 1 entries.
+void balanced_split(const std::vector<double> &cost, int parts, std::vector<int> &split) {
+    const int n = (int)cost.size();
+    std::vector<double> pref((size_t)n + 1, 0.0);
+    for (int i = 0; i < n; ++i) pref[i + 1] = pref[i] + cost[i];
+    split.assign((size_t)parts + 1, 0);
+    split[parts] = n;
+    for (int c = 1; c < parts; ++c) {
+        const double target = pref[n] * c / parts;
+        int lo = split[c - 1], hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (pref[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        split[c] = lo;
+    }
+}
+
+// Shared memory of one CTA owning rows [r0, r1) of an N-neuron network
+// (CTA/cluster mode: the neuron part covers all N neurons).
+long long cta_need(int N, int nt, bool has2, const int *rowch, int r0, int r1) {
+    long long ch = 0;
+    for (int i = r0; i < r1; ++i) ch += rowch[i];
+    const psst::NeuronLayout L = psst::make_nlayout(N, nt, has2, r1 - r0);
+    return L.syn + psst::syn_smem_bytes(ch, r1 - r0, has2);
+}
+
+// Lanes per CSR row: the power of two nearest half the mean number of
+// chunks per row, clamped to 2..32.
+int default_row_group(double mean_chunks) {
+    int g = 2;
+    while (g < 32 && g < mean_chunks * 0.5) g <<= 1;
     return g;
+}
+
+// Grid mode: one contiguous block of rows per CTA with balanced cost
+// (chunks plus a per-neuron share); the double-buffered gate-map tables and
+// the barrier words.
+int setup_grid(psst_net *h, const psst_network_desc *d, int max_smem, bool has2, const std::vector<int> &rowch,
+               cudaError_t *err) {
+    const long long N = h->v.N;
+    const int nt = h->v.n_stypes;
+    if (N * nt >= 65536)
+        return fail(PSST_ERR_UNSUPPORTED, "grid mode: %lld neurons x %d synapse types must stay below 65536", N, nt);
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return *err = e, cuda_fail(e, "device attributes");
+    const int parts = (int)std::max<long long>(1, std::min<long long>(sms, (N + 7) / 8));
+    std::vector<double> cost((size_t)N);
+    for (long long i = 0; i < N; ++i) cost[i] = rowch[i] + 10.0;
+    std::vector<int> split;
+    balanced_split(cost, parts, split);
+    std::vector<int> chunks((size_t)parts, 0);
+    int need = 0;
+    for (int c = 0; c < parts; ++c) {
+        const int n = split[c + 1] - split[c];
+        long long ch = 0;
+        for (int i = split[c]; i < split[c + 1]; ++i) ch += rowch[i];
+        const long long bytes = psst::make_nlayout(n, nt, has2, n).syn + psst::syn_smem_bytes(ch, n, has2);
+        if (bytes > max_smem)
+            return fail(PSST_ERR_UNSUPPORTED, "grid mode: block %d needs %lld B of shared memory (max %d)", c, bytes,
+                        max_smem);
+        chunks[c] = (int)ch;
+        need = std::max<int>(need, (int)bytes);
+    }
+    if (!h->block) h->block = 1024;
+    if (!h->G) h->G = default_row_group((double)std::accumulate(rowch.begin(), rowch.end(), 0LL) / (double)N);
+    h->smem = need;
+    int per_sm = 0;
+    e = psst::grid_occupancy(h->block, need, &per_sm);
+    if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid occupancy");
+    if (per_sm < 1) return fail(PSST_ERR_UNSUPPORTED, "grid mode: a CTA of %d threads does not fit an SM", h->block);
+    h->grid = parts;
+    h->n_smem = 1;
+    psst::GridView &g = h->gv;
+    int *rs = nullptr, *chd = nullptr;
+    e = upload(h, &rs, split.data(), split.size());
+    if (e == cudaSuccess) e = upload(h, &chd, chunks.data(), chunks.size());
+    if (e == cudaSuccess) e = h->alloc(&g.c1, (size_t)(2 * N * nt));
+    if (e == cudaSuccess && has2) e = h->alloc(&g.c2, (size_t)(2 * N * nt));
+    if (e == cudaSuccess) e = h->alloc(&g.bar, 2);
+    g.row_split = rs;
+    g.chunks = chd;
+    g.timeout_ns = 2000000000ULL;
+    if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid buffers");
+    return PSST_OK;
+}
+
+// CTA mode: choose each network's cluster size, group networks into size
+// classes (cluster size x CTAs per SM) and upload the launch lists.
+int setup_cta(psst_net *h, const psst_network_desc *d, int max_smem, const std::vector<int> &rowch,
+              const std::vector<uint8_t> &has2, cudaError_t *err) {
+    const int n_nets = d->n_nets, nt = d->n_syn_types;
+    std::vector<psst::NetPlan> plans((size_t)n_nets);
+    struct Key {
+        int cl, tier;
+    };
+    std::vector<Key> key((size_t)n_nets);
+    std::vector<long long> need((size_t)n_nets);
+    std::vector<double> cost((size_t)n_nets);
+    for (int b = 0; b < n_nets; ++b) {
+        const int n0 = d->net_neuron_off[b], N = d->net_neuron_off[b + 1] - n0;
+        if ((long long)N * nt >= 65536)
+            return fail(PSST_ERR_UNSUPPORTED, "net %d: %d neurons x %d synapse types must stay below 65536", b, N, nt);
+        const int *rc = rowch.data() + n0;
+        psst::NetPlan &pl = plans[b];
+        std::memset(&pl, 0, sizeof pl);
+        int chosen = 0;
+        long long nd = 0;
+        for (int cl = 1; cl <= PSST_MAX_CL && !chosen; cl *= 2) {
+            if (cl > 1 && N < 2 * cl) break;
+            std::vector<double> c((size_t)N);
+            for (int i = 0; i < N; ++i) c[i] = rc[i];
+            std::vector<int> split;
+            balanced_split(c, cl, split);
+            long long worst = 0;
+            for (int q = 0; q < cl; ++q) worst = std::max(worst, cta_need(N, nt, has2[b], rc, split[q], split[q + 1]));
+            if (worst <= max_smem) {
+                chosen = cl;
+                nd = worst;
+                for (int q = 0; q <= cl; ++q) pl.split[q] = split[q];
+                for (int q = 0; q < cl; ++q) {
+                    long long ch = 0;
+                    for (int i = split[q]; i < split[q + 1]; ++i) ch += rc[i];
+                    pl.chunks[q] = (int)ch;
+                }
+            }
+        }
+        if (!chosen)
+            return fail(PSST_ERR_UNSUPPORTED, "net %d (%d neurons, %lld synapses) does not fit %d CTAs", b, N,
+                        (long long)(d->row_ptr[n0 + N] - d->row_ptr[n0]), PSST_MAX_CL);
+        const int tier = nd * 4 <= max_smem ? 4 : nd * 2 <= max_smem ? 2 : 1;
+        key[b] = {chosen, tier};
+        need[b] = nd;
+        long long ch = 0;
+        for (int i = 0; i < N; ++i) ch += rc[i];
+        cost[b] = 4.0 * ch + 30.0 * N;
+    }
+    // classes in a fixed order: largest networks' classes first
+    const int cls[][2] = {{4, 1}, {4, 2}, {4, 4}, {2, 1}, {2, 2}, {2, 4}, {1, 1}, {1, 2}, {1, 4}};
+    std::vector<int> all_lists;
+    std::vector<std::pair<int, int>> ranges;
+    for (auto &ct : cls) {
+        std::vector<int> list;
+        for (int b = 0; b < n_nets; ++b)
+            if (key[b].cl == ct[0] && key[b].tier == ct[1]) list.push_back(b);
+        if (list.empty()) continue;
+        std::stable_sort(list.begin(), list.end(), [&](int a, int b2) { return cost[a] > cost[b2]; });
+        psst::ClassLaunch c{};
+        c.cl = ct[0];
+        c.n_nets = (int)list.size();
+        long long mx = 0, rows = 0, chunks = 0;
+        for (int b : list) {
+            mx = std::max(mx, need[b]);
+            rows += d->net_neuron_off[b + 1] - d->net_neuron_off[b];
+            for (int q = 0; q < ct[0]; ++q) chunks += plans[b].chunks[q];
+        }
+        c.smem = (int)mx;
+        c.block = d->block_threads ? d->block_threads : (ct[1] == 4 ? 256 : ct[1] == 2 ? 512 : 1024);
+        c.G = d->row_group ? d->row_group : default_row_group((double)chunks / (double)std::max(1LL, rows));
+        if (c.block % c.G) return fail(PSST_ERR_INVALID_ARG, "row_group must divide block_threads");
+        ranges.push_back({(int)all_lists.size(), (int)list.size()});
+        all_lists.insert(all_lists.end(), list.begin(), list.end());
+        h->classes.push_back(c);
+    }
+    int *dl = nullptr;
+    psst::NetPlan *dp = nullptr;
+    cudaError_t e = upload(h, &dl, all_lists.data(), all_lists.size());
+    if (e == cudaSuccess) e = upload(h, &dp, plans.data(), plans.size());
+    for (size_t i = 0; e == cudaSuccess && i < h->classes.size(); ++i) {
+        h->classes[i].list = dl + ranges[i].first;
+        h->classes[i].plans = dp;
+        e = psst::cta_prepare(h->classes[i].cl, max_smem);
+    }
+    if (e != cudaSuccess) return *err = e, cuda_fail(e, "CTA mode setup");
+    // summary for psst_query: the largest class
+    h->block = h->classes.empty() ? 0 : h->classes.back().block;
+    h->G = h->classes.empty() ? 0 : h->classes.back().G;
+    h->smem = 0;
+    h->grid = 0;
+    for (auto &c : h->classes) {
+        h->smem = std::max(h->smem, c.smem);
+        h->grid += c.n_nets * c.cl;
+        if (c.cl == 1) h->n_smem += c.n_nets;
+        else h->n_global += c.n_nets;
+    }
+    return PSST_OK;
 }
 
 }  // namespace
@@ -209,8 +415,40 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
 
     const int n_nets = d->n_nets, nt = d->n_syn_types;
     const long long N = d->net_neuron_off[n_nets], S = d->row_ptr[N];
+    const int max_smem = psst::cta_max_smem(dev);
+    if (max_smem <= 0) return fail(PSST_ERR_CUDA, "cannot query shared memory size of device %d", dev);
+
+    std::vector<int> rowch;
+    std::vector<uint8_t> has2;
+    row_chunk_counts(d, rowch, has2);
+    // cluster sizes needed in CTA mode (0 = does not fit)
+    bool all_fit = true;
+    for (int b = 0; b < n_nets && all_fit; ++b) {
+        const int n0 = d->net_neuron_off[b], Nb = d->net_neuron_off[b + 1] - n0;
+        bool fit = false;
+        for (int cl = 1; cl <= PSST_MAX_CL && !fit; cl *= 2) {
+            if (cl > 1 && Nb < 2 * cl) break;
+            std::vector<double> c((size_t)Nb);
+            for (int i = 0; i < Nb; ++i) c[i] = rowch[n0 + i];
+            std::vector<int> split;
+            balanced_split(c, cl, split);
+            long long worst = 0;
+            for (int q = 0; q < cl; ++q)
+                worst = std::max(worst, cta_need(Nb, nt, has2[b], rowch.data() + n0, split[q], split[q + 1]));
+            fit = worst <= max_smem;
+        }
+        all_fit = fit;
+    }
+    int mode = d->mode;
+    if (mode == PSST_MODE_AUTO) mode = all_fit ? PSST_MODE_CTA : PSST_MODE_GRID;
+    if (mode == PSST_MODE_GRID && n_nets != 1)
+        return fail(PSST_ERR_UNSUPPORTED, "grid mode integrates a single network (got %d)", n_nets);
+
     psst_net *h = new psst_net();
     h->device = dev;
+    h->mode = mode;
+    h->block = d->block_threads;
+    h->G = d->row_group;
     NetView &v = h->v;
     v.n_nets = n_nets;
     v.n_stypes = nt;
@@ -223,72 +461,10 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
     v.rec_stride = d->rec_stride;
     v.rec_cap = d->rec_stride > 0 ? d->rec_capacity : 0;
 
-    // per-synapse code and per-network flags, work order
     std::vector<uint32_t> code((size_t)S);
-    std::vector<uint8_t> flags((size_t)n_nets, 0);
-    std::vector<int> order((size_t)n_nets);
-    std::vector<double> cost((size_t)n_nets);
-    int max_smem = psst::cta_max_smem(dev);
-    if (max_smem <= 0) {
-        delete h;
-        return fail(PSST_ERR_CUDA, "cannot query shared memory size");
-    }
-    int need_smem = 0;
-    int n_smem = 0, n_global = 0;
-    long long max_n = 0;
-    bool any_over = false;
-    for (int b = 0; b < n_nets; ++b) {
-        const long long n0 = d->net_neuron_off[b], n1 = d->net_neuron_off[b + 1];
-        const long long s0 = d->row_ptr[n0], s1 = d->row_ptr[n1];
-        bool has2 = false;
-        for (long long k = s0; k < s1; ++k) {
-            const int t = d->syn_type[k];
-            code[k] = ((uint32_t)t << 24) | (uint32_t)(d->pre[k] * nt + t);
-            has2 |= d->syn_params[(size_t)t * PSST_SYN_NPARAM] == 1.0f;
-        }
-        const int nb = (int)(n1 - n0), sb = (int)(s1 - s0);
-        max_n = std::max<long long>(max_n, nb);
-        const psst::Layout full = psst::make_layout(nb, sb, nt, has2, true);
-        const psst::Layout part = psst::make_layout(nb, sb, nt, has2, false);
-        uint8_t f = has2 ? psst::NET_HAS2 : 0;
-        if (full.total <= max_smem) {
-            f |= psst::NET_FITS_SMEM;
-            need_smem = std::max(need_smem, full.total);
-            ++n_smem;
-        } else {
-            need_smem = std::max(need_smem, part.total);
-            any_over |= part.total > max_smem;
-            ++n_global;
-        }
-        flags[b] = f;
-        order[b] = b;
-        cost[b] = (double)sb + 40.0 * nb;
-    }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    for (long long k = 0; k < S; ++k)
+        code[k] = ((uint32_t)d->syn_type[k] << 24) | (uint32_t)(d->pre[k] * nt + d->syn_type[k]);
 
-    int mode = d->mode;
-    if (mode == PSST_MODE_AUTO) mode = PSST_MODE_CTA;
-    if (mode == PSST_MODE_GRID) {
-        delete h;
-        return fail(PSST_ERR_UNSUPPORTED, "grid mode is not available in this build");
-    }
-    if (any_over) {
-        delete h;
-        return fail(PSST_ERR_UNSUPPORTED, "a network has too many neurons for one CTA (max %lld)", max_n);
-    }
-    h->mode = mode;
-    h->n_smem = n_smem;
-    h->n_global = n_global;
-    h->smem = need_smem;
-    h->block = d->block_threads ? d->block_threads : 512;
-    const double mean_row = N ? (double)S / (double)N : 0.0;
-    h->G = d->row_group ? d->row_group : default_row_group(mean_row);
-    if (h->G > 32 || h->block % h->G) {
-        delete h;
-        return fail(PSST_ERR_INVALID_ARG, "row_group must divide block_threads");
-    }
-
-    // device arrays
     cudaError_t e = cudaSuccess;
     std::vector<long long> rp(d->row_ptr, d->row_ptr + N + 1);
     std::vector<long long> pon((size_t)n_nets, 0), poff((size_t)n_nets, 0);
@@ -299,7 +475,7 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
         if (e == cudaSuccess) e = upload(h, &(dst), (src), (size_t)(cnt)); \
     } while (0)
     {
-        int *p_off, *p_nt, *p_order;
+        int *p_off, *p_nt;
         long long *p_rp, *p_on, *p_offp;
         uint32_t *p_code;
         float *p_w, *p_np, *p_sp, *p_ic, *p_pa = nullptr;
@@ -315,8 +491,7 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
         if (d->pulse_amp) UP(p_pa, d->pulse_amp, N);
         UP(p_on, pon.data(), n_nets);
         UP(p_offp, poff.data(), n_nets);
-        UP(p_order, order.data(), n_nets);
-        UP(p_fl, flags.data(), n_nets);
+        UP(p_fl, has2.data(), n_nets);
         v.net_off = p_off;
         v.row_ptr = p_rp;
         v.syn_code = p_code;
@@ -328,14 +503,12 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
         v.pulse_amp = p_pa;
         v.pulse_on = p_on;
         v.pulse_off = p_offp;
-        v.order = p_order;
         v.net_flags = p_fl;
     }
 #undef UP
     const long long dim = 4 * N + 2 * S;
     if (e == cudaSuccess) e = h->alloc(&v.state, (size_t)dim);
     if (e == cudaSuccess && v.rec_cap > 0) e = h->alloc(&v.rec, (size_t)(v.rec_cap * N));
-    if (e == cudaSuccess) e = h->alloc(&v.work_counter, 4);
     if (e == cudaSuccess) e = h->alloc(&v.err, 1);
     if (e == cudaSuccess) e = cudaMemset(v.err, 0, sizeof(int));
     if (e == cudaSuccess && v.rec) e = cudaMemset(v.rec, 0, (size_t)v.rec_cap * N * sizeof(float));
@@ -355,22 +528,17 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
             e = cudaMemcpy(v.state, y.data(), (size_t)dim * sizeof(float), cudaMemcpyHostToDevice);
         }
     }
-    if (e == cudaSuccess) {
-        int per_sm = 0, sms = 0;
-        e = psst::cta_occupancy(h->block, h->smem, &per_sm);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess && per_sm < 1) {
-            h->release();
-            delete h;
-            return fail(PSST_ERR_UNSUPPORTED, "block of %d threads with %d B shared memory cannot launch",
-                        d->block_threads ? d->block_threads : 512, need_smem);
-        }
-        h->grid = (int)std::min<long long>(n_nets, (long long)per_sm * sms);
-    }
     if (e != cudaSuccess) {
         h->release();
         delete h;
         return cuda_fail(e, "psst_create_network");
+    }
+    rc = mode == PSST_MODE_GRID ? setup_grid(h, d, max_smem, has2[0] != 0, rowch, &e)
+                                : setup_cta(h, d, max_smem, rowch, has2, &e);
+    if (rc) {
+        h->release();
+        delete h;
+        return rc;
     }
     *out = h;
     return PSST_OK;
@@ -386,12 +554,27 @@ int psst_integrate(psst_net *h, int64_t n_steps, void *stream) {
     const long long chunk = 1LL << 30;
     for (long long done = 0; done < n_steps;) {
         const int n = (int)std::min<long long>(chunk, n_steps - done);
-        cudaError_t e = psst::cta_launch(h->v, h->step + done, n, h->grid, h->block, h->G, h->smem, st);
-        if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
-        ++h->launches;
+        if (h->mode == PSST_MODE_GRID) {
+            cudaError_t e = psst::grid_launch(h->v, h->gv, h->step + done, n, h->grid, h->block, h->G, h->smem, st);
+            if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
+            ++h->launches;
+        } else {
+            for (const psst::ClassLaunch &c : h->classes) {
+                cudaError_t e = psst::cta_launch(h->v, c, h->step + done, n, st);
+                if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
+                ++h->launches;
+            }
+        }
         done += n;
     }
     h->step += n_steps;
+    return PSST_OK;
+}
+
+int psst_set_barrier_timeout(psst_net *h, int64_t timeout_ns) {
+    if (!h) return fail(PSST_ERR_INVALID_ARG, "handle is NULL");
+    if (timeout_ns < 0) return fail(PSST_ERR_INVALID_ARG, "timeout must be >= 0");
+    h->gv.timeout_ns = (unsigned long long)timeout_ns;
     return PSST_OK;
 }
 
@@ -485,8 +668,9 @@ int psst_query(const psst_net *h, psst_info *out) {
     out->row_group = h->G;
     out->grid_ctas = h->grid;
     out->smem_bytes = h->smem;
-    out->n_smem_nets = h->n_smem;
-    out->n_global_nets = h->n_global;
+    out->n_single_cta_nets = h->n_smem;
+    out->n_cluster_nets = h->n_global;
+    out->n_launch_classes = (int32_t)h->classes.size();
     out->kernel_launches = h->launches;
     return PSST_OK;
 }

@@ -41,29 +41,49 @@ struct NetView {
     float *rec;                  // [rec_cap][N] ring of V frames, or null
     int rec_stride;
     long long rec_cap;
-    const int *order;            // [n_nets] network processing order
-    const uint8_t *net_flags;    // [n_nets]: bit 0 second-order synapses, bit 1 synapses fit smem
-    int *work_counter;           // scratch: next work item
+    const uint8_t *net_flags;    // [n_nets]: bit 0 = has second-order synapses
     int *err;                    // device error word (first error wins)
 };
 
-enum : uint8_t { NET_HAS2 = 1, NET_FITS_SMEM = 2 };
+enum : uint8_t { NET_HAS2 = 1 };
+
+// Extra device state of the grid-wide mode (one network over all SMs).
+struct GridView {
+    float2 *c1;                  // [2][N * n_stypes] gate maps (r), double-buffered by stage parity
+    float4 *c2;                  // [2][N * n_stypes] gate maps (s), second-order networks only
+    unsigned *bar;               // [2] barrier arrival counter and generation
+    const int *row_split;        // [gridDim.x + 1] first row owned by each CTA
+    const int *chunks;           // [gridDim.x] synapse chunks of each CTA's rows
+    unsigned long long timeout_ns;  // limit of one barrier wait
+};
 
 // Column indices of the parameter tables.
 enum { NP_C = 0, NP_GNA, NP_GK, NP_GL, NP_ENA, NP_EK, NP_EL, NP_GKL, NP_EKL };
 enum { SP_KIND = 0, SP_A, SP_B, SP_K3, SP_K4, SP_KD, SP_E, SP_VP, SP_KP };
 
-// Shared-memory layout of one network in the CTA kernel.  Computed the same
-// way on host (sizing) and device (addressing).  Offsets in bytes, 16-aligned.
-struct Layout {
-    int c2cur, c2fin, c2acc;  // float4 [N*nt]: s-coefficients (second order only)
-    int c1cur, c1fin, c1acc;  // float2 [N*nt]: r-coefficients
-    int y0, ys, acc;          // float [4N]: step-start state, stage state, k-sum
-    int prm;                  // float [9N]: 1/C, gNa, gK, gL, ENa, EK, EL, gKL, EKL
-    int iext, isyn;           // float [N]
-    int rowp;                 // int [N+1]
-    int r, s, w, code;        // [S] each when synapses live in smem (s only second order)
-    int total;
+#define PSST_MAX_CL 4
+
+// Per-network plan of the CTA/cluster kernel: the rows owned by each CTA of
+// the network's cluster and their number of 4-wide synapse chunks.
+struct NetPlan {
+    int split[PSST_MAX_CL + 1];
+    int chunks[PSST_MAX_CL];
+};
+
+// Shared-memory layout of the neuron part (all N neurons of the network, or
+// a grid CTA's own neurons) followed by the synapse chunks of the CTA's own
+// rows.  Computed the same way on host (sizing) and device (addressing).
+// Offsets in bytes, 16-aligned.
+struct NeuronLayout {
+    int cur2, acc2, fin2;  // float4 [N*nt]: s-maps (second order only)
+    int cur1, acc1, fin1;  // float2 [N*nt]: r-maps
+    int y0, ys, acc;       // float [4N]: step-start state, stage m/h/n, RK4 k-sum
+    int prm;               // float [9N]: 1/C, gNa, gK, gL, ENa, EK, EL, gKL, EKL
+    int iext;              // float [N]
+    int isyn;              // float [2][N]: synaptic current, by stage parity
+    int vst;               // float [2][N]: stage potential, by stage parity
+    int tmp;               // int [nrows+1]: scan scratch
+    int syn;               // start of the synapse chunks
 };
 
 __host__ __device__ inline int lay_take(int &o, long long bytes) {
@@ -72,28 +92,25 @@ __host__ __device__ inline int lay_take(int &o, long long bytes) {
     return at;
 }
 
-__host__ __device__ inline Layout make_layout(int N, int S, int nt, bool has2, bool syn_smem) {
-    Layout L;
+__host__ __device__ inline NeuronLayout make_nlayout(int N, int nt, bool has2, int nrows) {
+    NeuronLayout L;
     int o = 0;
     const long long M = (long long)N * nt;
-    L.c2cur = has2 ? lay_take(o, 16 * M) : -1;
-    L.c2fin = has2 ? lay_take(o, 16 * M) : -1;
-    L.c2acc = has2 ? lay_take(o, 16 * M) : -1;
-    L.c1cur = lay_take(o, 8 * M);
-    L.c1fin = lay_take(o, 8 * M);
-    L.c1acc = lay_take(o, 8 * M);
+    L.cur2 = has2 ? lay_take(o, 16 * M) : -1;
+    L.acc2 = has2 ? lay_take(o, 16 * M) : -1;
+    L.fin2 = has2 ? lay_take(o, 16 * M) : -1;
+    L.cur1 = lay_take(o, 8 * M);
+    L.acc1 = lay_take(o, 8 * M);
+    L.fin1 = lay_take(o, 8 * M);
     L.y0 = lay_take(o, 16LL * N);
     L.ys = lay_take(o, 16LL * N);
     L.acc = lay_take(o, 16LL * N);
     L.prm = lay_take(o, 36LL * N);
     L.iext = lay_take(o, 4LL * N);
-    L.isyn = lay_take(o, 4LL * N);
-    L.rowp = lay_take(o, 4LL * (N + 1));
-    L.r = syn_smem ? lay_take(o, 4LL * S) : -1;
-    L.w = syn_smem ? lay_take(o, 4LL * S) : -1;
-    L.code = syn_smem ? lay_take(o, 4LL * S) : -1;
-    L.s = (syn_smem && has2) ? lay_take(o, 4LL * S) : -1;
-    L.total = o;
+    L.isyn = lay_take(o, 8LL * N);
+    L.vst = lay_take(o, 8LL * N);
+    L.tmp = lay_take(o, 4LL * (nrows + 1));
+    L.syn = o;
     return L;
 }
 

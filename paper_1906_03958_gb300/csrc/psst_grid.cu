@@ -1,0 +1,220 @@
+// Grid-wide RK4 integration of one large network (cooperative launch, one
+// CTA per SM).  CTA c owns a contiguous block of CSR rows (postsynaptic
+// neurons) chosen by the host to balance synapse chunks; its neurons and its
+// rows' synapses stay in shared memory for the whole launch (4-wide chunk
+// layout of psst_syn.cuh).
+//
+// The only data every CTA needs from the others is, per presynaptic neuron
+// and synapse type, the affine gate map of the next stage (psst_cta.cu
+// explains the gate formulation).  Each CTA writes the maps of its own
+// neurons to a double-buffered table in global memory and reads the whole
+// table through L2; one device-wide barrier per RK4 stage separates writers
+// from readers, and double buffering removes the write-after-read hazard.
+// The barrier spins with a time limit: on expiry it records
+// PSST_ERR_TIMEOUT and every CTA returns.
+#include <cuda_runtime.h>
+
+#include "psst_device.cuh"
+#include "psst_internal.h"
+#include "psst_syn.cuh"
+
+namespace psst {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned x;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(x) : "l"(p) : "memory");
+    return x;
+}
+
+// Device-wide barrier over gridDim.x co-resident CTAs.  bar[0] counts
+// arrivals, bar[1] is the generation.  Returns false (after recording the
+// error) when the wait ran out of time or another CTA already failed.
+__device__ bool grid_barrier(unsigned *bar, unsigned long long timeout_ns, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned gen = ld_acquire(bar + 1);
+        __threadfence();
+        const unsigned prev = atomicAdd(bar, 1u);
+        int ok = 1;
+        if (prev == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = globaltimer();
+            while (ld_acquire(bar + 1) == gen) {
+                if (*(volatile int *)err != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (globaltimer() - t0 > timeout_ns) {
+                    set_error(err, PSST_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+struct GlobalCoef {
+    const float2 *t1;
+    const float4 *t2;
+    __device__ __forceinline__ float2 r(int i) const { return __ldcg(t1 + i); }
+    __device__ __forceinline__ float4 s(int i) const { return __ldcg(t2 + i); }
+};
+
+struct LocalOut {
+    float *isyn;
+    __device__ __forceinline__ void operator()(int row, float x) const { isyn[row] = x; }
+};
+
+template <bool HAS2>
+__device__ void grid_run(const NetView &v, const GridView &g, long long step0, int nsteps, int G,
+                         unsigned char *smem, const float *stab) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lo = g.row_split[blockIdx.x], N = g.row_split[blockIdx.x + 1] - lo;
+    const int nt = v.n_stypes, Mloc = N * nt;
+    const int M = (int)(v.N * nt);
+    const NeuronLayout L = make_nlayout(N, nt, HAS2, N);
+    float *y0 = (float *)(smem + L.y0), *ys = (float *)(smem + L.ys), *acc = (float *)(smem + L.acc);
+    float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext);
+    float *isyn = (float *)(smem + L.isyn), *vst = (float *)(smem + L.vst);
+    float2 *cur1 = (float2 *)(smem + L.cur1), *acc1 = (float2 *)(smem + L.acc1);
+    float4 *cur2 = HAS2 ? (float4 *)(smem + L.cur2) : nullptr;
+    float4 *acc2 = HAS2 ? (float4 *)(smem + L.acc2) : nullptr;
+    int *tmp = (int *)(smem + L.tmp);
+    RowChunks rc = carve_rows(smem + L.syn, N, g.chunks[blockIdx.x], HAS2);
+
+    float *gV = v.state + lo;
+    float *gr = v.state + 4 * v.N;
+    float *gs = v.state + 4 * v.N + v.S;
+
+    for (int i = tid; i < N; i += nthr) {
+        const float V = gV[i];
+        y0[i] = V;
+        vst[i] = V;
+#pragma unroll
+        for (int x = 1; x < 4; ++x) {
+            const float y = gV[(long long)x * v.N + i];
+            y0[x * N + i] = y;
+            ys[x * N + i] = y;
+        }
+        const float *p = v.nparams + (long long)v.neuron_type[lo + i] * PSST_NEURON_NPARAM;
+        prm[NP_C * N + i] = 1.0f / p[NP_C];
+#pragma unroll
+        for (int x = 1; x < PSST_NEURON_NPARAM; ++x) prm[x * N + i] = p[x];
+    }
+    // identity step-end maps of the own pairs in table 0 (read by stage 0)
+    for (int p = tid; p < Mloc; p += nthr) {
+        const int gi = lo * nt + p;
+        g.c1[gi] = make_float2(0.0f, 1.0f);
+        if (HAS2) {
+            const float *sp = stab + (p % nt) * 9;
+            g.c2[gi] = make_float4(0.0f, 0.0f, 1.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
+        }
+    }
+    load_rows<HAS2>(rc, v, 0, 0, lo, gr, gs, v.weight, v.syn_code, stab, tmp);
+    bool ok = grid_barrier(g.bar, g.timeout_ns, v.err);
+
+    const float dt = v.dt;
+    int tq = tid - N % nthr;
+    if (tq < 0) tq += nthr;
+    for (int it = 0; ok && it < nsteps; ++it) {
+        const long long step = step0 + it;
+        for (int i = tid; i < N; i += nthr) iext[i] = input_current(v, 0, (long long)lo + i, step);
+#define PSST_GSTAGE(ST)                                                                                    \
+    if (ok) {                                                                                              \
+        const float *vcur = vst + (ST & 1) * N;                                                            \
+        float *vnxt = vst + ((ST + 1) & 1) * N;                                                            \
+        const GlobalCoef cf{g.c1 + (size_t)(ST & 1) * M, HAS2 ? g.c2 + (size_t)(ST & 1) * M : nullptr};    \
+        sphase<ST, HAS2>(rc, vcur, cf, G, LocalOut{isyn});                                                 \
+        __syncthreads();                                                                                   \
+        for (int i = tid; i < N; i += nthr) {                                                              \
+            const float vn = neuron_update<ST>(i, N, vcur[i], y0, acc, ys, prm, iext[i], isyn[i], dt);     \
+            vnxt[i] = vn;                                                                                  \
+            if (ST == 3 && v.rec_stride > 0 && ((step + 1) % v.rec_stride) == 0) {                         \
+                const long long frame = (step + 1) / v.rec_stride - 1;                                     \
+                v.rec[(frame % v.rec_cap) * v.N + lo + i] = vn;                                            \
+            }                                                                                              \
+        }                                                                                                  \
+        float2 *o1 = g.c1 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt;                                  \
+        float4 *o2 = HAS2 ? g.c2 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt : nullptr;                 \
+        for (int p = tq; p < Mloc; p += nthr) {                                                            \
+            float2 f1;                                                                                     \
+            float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;                                          \
+            float4 &c2 = HAS2 ? cur2[p] : d4;                                                              \
+            float4 &a2 = HAS2 ? acc2[p] : d4;                                                              \
+            coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2); \
+            o1[p] = ST == 3 ? f1 : cur1[p];                                                                \
+            if (HAS2) o2[p] = ST == 3 ? f2 : cur2[p];                                                      \
+        }                                                                                                  \
+        ok = grid_barrier(g.bar, g.timeout_ns, v.err);                                                     \
+    }
+        PSST_GSTAGE(0)
+        PSST_GSTAGE(1)
+        PSST_GSTAGE(2)
+        PSST_GSTAGE(3)
+#undef PSST_GSTAGE
+    }
+    if (!ok) return;  // error recorded; global state keeps its value from before the call
+
+    const GlobalCoef fin{g.c1, HAS2 ? g.c2 : nullptr};
+    store_rows<HAS2>(rc, v, 0, 0, lo, gr, gs, v.syn_code, stab, fin);
+    bool bad = false;
+    for (int i = tid; i < N; i += nthr) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const float y = y0[x * N + i];
+            bad |= !isfinite(y);
+            gV[(long long)x * v.N + i] = y;
+        }
+    }
+    if (bad) set_error(v.err, PSST_ERR_NONFINITE);
+}
+
+__global__ void __launch_bounds__(1024, 1) grid_kernel(NetView v, GridView g, long long step0, int nsteps,
+                                                        int G) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float stab[PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM];
+    for (int i = threadIdx.x; i < v.n_stypes * PSST_SYN_NPARAM; i += blockDim.x) {
+        float x = v.sparams[i];
+        if (i % PSST_SYN_NPARAM == SP_KP) x = 1.0f / x;
+        stab[i] = x;
+    }
+    __syncthreads();
+    if (v.net_flags[0] & NET_HAS2) grid_run<true>(v, g, step0, nsteps, G, smem, stab);
+    else grid_run<false>(v, g, step0, nsteps, G, smem, stab);
+}
+
+}  // namespace
+
+cudaError_t grid_occupancy(int block, int smem, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, grid_kernel, block, smem);
+}
+
+cudaError_t grid_launch(const NetView &v, const GridView &g, long long step0, int nsteps, int grid, int block,
+                        int G, int smem, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(g.bar, 0, 2 * sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&v, (void *)&g, (void *)&step0, (void *)&nsteps, (void *)&G};
+    return cudaLaunchCooperativeKernel((const void *)grid_kernel, dim3(grid), dim3(block), args, (size_t)smem,
+                                       stream);
+}
+
+}  // namespace psst

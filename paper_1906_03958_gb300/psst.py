@@ -25,7 +25,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOU
 
 EXPORTED = ("psst_create_network", "psst_integrate", "psst_status", "psst_get_state",
             "psst_set_state", "psst_set_step", "psst_read_record", "psst_query",
-            "psst_destroy_network", "psst_error_string", "psst_last_error")
+            "psst_destroy_network", "psst_error_string", "psst_last_error",
+            "psst_set_barrier_timeout")
 
 
 class PsstError(RuntimeError):
@@ -51,8 +52,9 @@ class Info(C.Structure):
     _fields_ = [("n_nets", C.c_int32), ("n_neurons", C.c_int64), ("n_synapses", C.c_int64),
                 ("steps_done", C.c_int64), ("rec_frames", C.c_int64), ("mode", C.c_int32),
                 ("block_threads", C.c_int32), ("row_group", C.c_int32), ("grid_ctas", C.c_int32),
-                ("smem_bytes", C.c_int32), ("n_smem_nets", C.c_int32),
-                ("n_global_nets", C.c_int32), ("kernel_launches", C.c_int32)]
+                ("smem_bytes", C.c_int32), ("n_single_cta_nets", C.c_int32),
+                ("n_cluster_nets", C.c_int32), ("n_launch_classes", C.c_int32),
+                ("kernel_launches", C.c_int32)]
 
 
 _lib = None
@@ -82,6 +84,7 @@ def load(build_if_missing: bool = False):
         lib.psst_get_state.argtypes = [P, P, SZ, I32, P]
         lib.psst_set_state.argtypes = [P, P, SZ, I32, P]
         lib.psst_set_step.argtypes = [P, I64]
+        lib.psst_set_barrier_timeout.argtypes = [P, I64]
         lib.psst_read_record.argtypes = [P, P, SZ, C.POINTER(C.c_int64), I32, P]
         lib.psst_query.argtypes = [P, C.POINTER(Info)]
         lib.psst_destroy_network.argtypes = [P]
@@ -177,6 +180,9 @@ class Network:
 
     def set_step(self, step: int):
         _check(load().psst_set_step(self._h, int(step)))
+
+    def set_barrier_timeout(self, ns: int):
+        _check(load().psst_set_barrier_timeout(self._h, int(ns)))
 
     # -- state
     def get_state(self, out=None, stream=None):

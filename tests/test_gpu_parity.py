@@ -159,7 +159,7 @@ def test_batched_equals_alone_bitwise():
 
 def test_ragged_batch_single_step():
     # several CTAs' worth of networks of uneven size, incl. a ragged tail of
-    # tiny ones, and networks too large for shared memory (global path)
+    # tiny ones, and networks too large for one SM (cluster of CTAs)
     small = ng.batched(n_nets=40, base_seed=900, n_min=2, n_max=120)
     big = ng.batched(n_nets=3, base_seed=950, n_min=290, n_max=300)
     spec = ng.concat_specs([small, big])
@@ -173,7 +173,7 @@ def test_ragged_batch_single_step():
             net.integrate(1)
             net.status()
             got = net.get_state_numpy()
-        assert info["n_global_nets"] >= 1 and info["n_smem_nets"] >= 40
+        assert info["n_cluster_nets"] >= 1 and info["n_single_cta_nets"] >= 40
         assert step_error(got, y64, N, S) <= STEP_TOL
 
 
