@@ -333,7 +333,7 @@ def main():
                           "n_nets": spec.n_nets, "neurons": spec.n_neurons, "synapses": spec.n_synapses,
                           "rec_stride": args.rec_stride, "l2": "working set larger than L2 (state+synapses "
                           f"{(dim * 4 + spec.n_synapses * 8) / 1e6:.0f} MB)",
-                          "block_threads": info["block_threads"], "row_group": info["row_group"],
+                          "block_threads": info["block_threads"], "item_chunks": info["item_chunks"],
                           "grid_ctas": info["grid_ctas"], "smem_bytes": info["smem_bytes"],
                           "single_cta_nets": info["n_single_cta_nets"], "cluster_nets": info["n_cluster_nets"],
                           "launch_classes": info["n_launch_classes"],

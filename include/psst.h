@@ -106,7 +106,7 @@ typedef struct {
     int64_t rec_capacity;          /* frames in the record ring buffer (>= 1 if stride > 0) */
     int32_t mode;                  /* PSST_MODE_* */
     int32_t block_threads;         /* CTA size (multiple of 32, <= 1024), 0 = tuned */
-    int32_t row_group;             /* lanes per CSR row in the reduction (1,2,...,32), 0 = tuned */
+    int32_t item_chunks;           /* 4-synapse chunks per work item of the synaptic sum (1..64), 0 = tuned */
     int32_t device;                /* CUDA device ordinal, -1 = current device */
 } psst_network_desc;
 
@@ -115,7 +115,7 @@ typedef struct {
     int64_t n_neurons, n_synapses;
     int64_t steps_done;            /* global step index of the current state */
     int64_t rec_frames;            /* frames recorded so far (all calls) */
-    int32_t mode, block_threads, row_group; /* block/row_group of the smallest-network class */
+    int32_t mode, block_threads, item_chunks; /* CTA size and work-item chunks of the last class */
     int32_t grid_ctas;             /* CTAs of one integrate chunk (all launches) */
     int32_t smem_bytes;            /* largest dynamic shared memory per CTA */
     int32_t n_single_cta_nets;     /* CTA mode: networks held by one CTA */

@@ -59,7 +59,7 @@ struct psst_net {
     long long step = 0;       // global step index of the current state
     long long rec_reset = 0;  // step at which the record ring was last reset
     int mode = PSST_MODE_CTA;
-    int block = 0, G = 0, smem = 0, grid = 0;
+    int block = 0, K = 0, smem = 0, grid = 0;
     int n_smem = 0, n_global = 0;
     int launches = 0;
 
@@ -122,8 +122,8 @@ int validate(const psst_network_desc *d) {
         return fail(PSST_ERR_INVALID_ARG, "pulse_amp given without pulse_on/pulse_off");
     if (d->block_threads && (d->block_threads % 32 || d->block_threads < 32 || d->block_threads > 1024))
         return fail(PSST_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in 32..1024");
-    if (d->row_group && (d->row_group > 32 || (d->row_group & (d->row_group - 1))))
-        return fail(PSST_ERR_INVALID_ARG, "row_group must be a power of two <= 32");
+    if (d->item_chunks < 0 || d->item_chunks > 64)
+        return fail(PSST_ERR_INVALID_ARG, "item_chunks must be in 0..64");
     for (int t = 0; t < d->n_neuron_types; ++t) {
         const float *p = d->neuron_params + (size_t)t * PSST_NEURON_NPARAM;
         for (int x = 0; x < PSST_NEURON_NPARAM; ++x)
@@ -174,21 +174,20 @@ int validate(const psst_network_desc *d) {
     return PSST_OK;
 }
 
-// Per-row chunk counts (first- and second-order parts padded to 4) of the
-// whole batch, and which networks hold second-order synapses.
-void row_chunk_counts(const psst_network_desc *d, std::vector<int> &rowch, std::vector<uint8_t> &has2) {
+// Per-row counts of first- and second-order synapses, and which networks
+// hold second-order synapses.
+void row_counts(const psst_network_desc *d, std::vector<int> &n1, std::vector<int> &n2, std::vector<uint8_t> &has2) {
     const long long N = d->net_neuron_off[d->n_nets];
-    rowch.assign((size_t)N, 0);
+    n1.assign((size_t)N, 0);
+    n2.assign((size_t)N, 0);
     has2.assign((size_t)d->n_nets, 0);
     for (int b = 0; b < d->n_nets; ++b) {
         for (long long i = d->net_neuron_off[b]; i < d->net_neuron_off[b + 1]; ++i) {
-            int n1 = 0, n2 = 0;
             for (long long k = d->row_ptr[i]; k < d->row_ptr[i + 1]; ++k) {
-                if (d->syn_params[(size_t)d->syn_type[k] * PSST_SYN_NPARAM] != 0.0f) ++n2;
-                else ++n1;
+                if (d->syn_params[(size_t)d->syn_type[k] * PSST_SYN_NPARAM] != 0.0f) ++n2[i];
+                else ++n1[i];
             }
-            rowch[i] = psst::row_chunks(n1, n2);
-            if (n2) has2[b] = 1;
+            if (n2[i]) has2[b] = 1;
         }
     }
 }
@@ -213,28 +212,100 @@ void balanced_split(const std::vector<double> &cost, int parts, std::vector<int>
     }
 }
 
-// Shared memory of one CTA owning rows [r0, r1) of an N-neuron network
-// (CTA/cluster mode: the neuron part covers all N neurons).
-long long cta_need(int N, int nt, bool has2, const int *rowch, int r0, int r1) {
-    long long ch = 0;
-    for (int i = r0; i < r1; ++i) ch += rowch[i];
-    const psst::NeuronLayout L = psst::make_nlayout(N, nt, has2, r1 - r0);
-    return L.syn + psst::syn_smem_bytes(ch, r1 - r0, has2);
+struct SmemCaps {
+    int max_dyn;   // largest dynamic shared memory of one CTA
+    int per_sm;    // shared memory of one SM
+    int per_cta;   // per-CTA overhead: static shared memory + reserved
+};
+
+int smem_caps(int dev, SmemCaps *c) {
+    int optin = 0, per_sm = 0, reserved = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+        return fail(PSST_ERR_CUDA, "cannot query shared memory sizes of device %d", dev);
+    const int stat = psst::cta_static_smem() + 64;  // static table + small shared variables
+    c->max_dyn = optin - stat;
+    c->per_sm = per_sm;
+    c->per_cta = stat + reserved;
+    return PSST_OK;
 }
 
-// Lanes per CSR row: the power of two nearest half the mean number of
-// chunks per row, clamped to 2..32.
-int default_row_group(double mean_chunks) {
-    int g = 2;
-    while (g < 32 && g < mean_chunks * 0.5) g <<= 1;
-    return g;
+// 4-synapse chunks per work item: about 768 threads' worth of items for the
+// largest CTA share, 1..8 (or the caller's choice).
+int choose_K(long long chunks, int user) {
+    if (user > 0) return user;
+    const long long k = (chunks + 767) / 768;
+    return (int)std::max(1LL, std::min(8LL, k));
 }
 
-// Grid mode: one contiguous block of rows per CTA with balanced cost
-// (chunks plus a per-neuron share); the double-buffered gate-map tables and
-// the barrier words.
-int setup_grid(psst_net *h, const psst_network_desc *d, int max_smem, bool has2, const std::vector<int> &rowch,
-               cudaError_t *err) {
+struct Share {  // one CTA's share of a network
+    int r0, r1, items1, items2;
+    long long chunks;
+};
+
+// Shares of `parts` CTAs over rows [0, n) (row i of the network at n1[i],
+// n2[i]) and the work-item size.
+void make_shares(const int *n1, const int *n2, int n, int parts, int user_K, std::vector<Share> &sh, int *K) {
+    std::vector<double> cost((size_t)n);
+    for (int i = 0; i < n; ++i) cost[i] = (n1[i] + 3) / 4 + (n2[i] + 3) / 4 + 2.0;
+    std::vector<int> split;
+    balanced_split(cost, parts, split);
+    sh.assign((size_t)parts, Share{});
+    long long worst = 0;
+    for (int q = 0; q < parts; ++q) {
+        sh[q].r0 = split[q];
+        sh[q].r1 = split[q + 1];
+        for (int i = split[q]; i < split[q + 1]; ++i) sh[q].chunks += (n1[i] + 3) / 4 + (n2[i] + 3) / 4;
+        worst = std::max(worst, sh[q].chunks);
+    }
+    *K = choose_K(worst, user_K);
+    for (int q = 0; q < parts; ++q) {
+        sh[q].items1 = sh[q].items2 = 0;
+        for (int i = split[q]; i < split[q + 1]; ++i) {
+            sh[q].items1 += psst::part_items(n1[i], *K);
+            sh[q].items2 += psst::part_items(n2[i], *K);
+        }
+    }
+}
+
+// Dynamic shared memory of one CTA of a network of N neurons in CTA mode.
+long long cta_share_bytes(int N, int nt, bool has2, const Share &s, int K) {
+    const psst::NeuronLayout L = psst::make_nlayout(s.r1 - s.r0, N, N * nt, has2);
+    return L.syn + psst::items_smem_bytes(s.items1, s.items2, K, s.r1 - s.r0, has2);
+}
+
+// Smallest cluster size (1, 2, 4) whose CTAs all fit; 0 if none.
+int plan_network(const psst_network_desc *d, int b, const std::vector<int> &n1, const std::vector<int> &n2,
+                 bool has2, const SmemCaps &caps, psst::NetPlan *pl, long long *need) {
+    const int n0 = d->net_neuron_off[b], N = d->net_neuron_off[b + 1] - n0, nt = d->n_syn_types;
+    for (int cl = 1; cl <= PSST_MAX_CL; cl *= 2) {
+        if (cl > 1 && N < 2 * cl) break;
+        std::vector<Share> sh;
+        int K = 1;
+        make_shares(n1.data() + n0, n2.data() + n0, N, cl, d->item_chunks, sh, &K);
+        long long worst = 0;
+        for (int q = 0; q < cl; ++q) worst = std::max(worst, cta_share_bytes(N, nt, has2, sh[q], K));
+        if (worst <= caps.max_dyn) {
+            std::memset(pl, 0, sizeof *pl);
+            pl->K = K;
+            for (int q = 0; q < cl; ++q) {
+                pl->split[q] = sh[q].r0;
+                pl->n1[q] = sh[q].items1;
+                pl->n2[q] = sh[q].items2;
+            }
+            pl->split[cl] = N;
+            *need = worst;
+            return cl;
+        }
+    }
+    return 0;
+}
+
+// Grid mode: one contiguous block of rows per CTA with balanced cost, the
+// double-buffered gate-map tables and the barrier words.
+int setup_grid(psst_net *h, const psst_network_desc *d, const SmemCaps &caps, bool has2, const std::vector<int> &n1,
+               const std::vector<int> &n2, cudaError_t *err) {
     const long long N = h->v.N;
     const int nt = h->v.n_stypes;
     if (N * nt >= 65536)
@@ -243,122 +314,90 @@ int setup_grid(psst_net *h, const psst_network_desc *d, int max_smem, bool has2,
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "device attributes");
     const int parts = (int)std::max<long long>(1, std::min<long long>(sms, (N + 7) / 8));
-    std::vector<double> cost((size_t)N);
-    for (long long i = 0; i < N; ++i) cost[i] = rowch[i] + 10.0;
-    std::vector<int> split;
-    balanced_split(cost, parts, split);
-    std::vector<int> chunks((size_t)parts, 0);
+    std::vector<Share> sh;
+    int K = 1;
+    make_shares(n1.data(), n2.data(), (int)N, parts, d->item_chunks, sh, &K);
+    std::vector<int> split((size_t)parts + 1), items((size_t)2 * parts);
     int need = 0;
     for (int c = 0; c < parts; ++c) {
-        const int n = split[c + 1] - split[c];
-        long long ch = 0;
-        for (int i = split[c]; i < split[c + 1]; ++i) ch += rowch[i];
-        const long long bytes = psst::make_nlayout(n, nt, has2, n).syn + psst::syn_smem_bytes(ch, n, has2);
-        if (bytes > max_smem)
+        const int n = sh[c].r1 - sh[c].r0;
+        const long long bytes = psst::make_nlayout(n, n, n * nt, has2).syn +
+                                psst::items_smem_bytes(sh[c].items1, sh[c].items2, K, n, has2);
+        if (bytes > caps.max_dyn)
             return fail(PSST_ERR_UNSUPPORTED, "grid mode: block %d needs %lld B of shared memory (max %d)", c, bytes,
-                        max_smem);
-        chunks[c] = (int)ch;
+                        caps.max_dyn);
+        split[c] = sh[c].r0;
+        items[c] = sh[c].items1;
+        items[parts + c] = sh[c].items2;
         need = std::max<int>(need, (int)bytes);
     }
+    split[parts] = (int)N;
     if (!h->block) h->block = 1024;
-    if (!h->G) h->G = default_row_group((double)std::accumulate(rowch.begin(), rowch.end(), 0LL) / (double)N);
+    h->K = K;
     h->smem = need;
     int per_sm = 0;
     e = psst::grid_occupancy(h->block, need, &per_sm);
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid occupancy");
     if (per_sm < 1) return fail(PSST_ERR_UNSUPPORTED, "grid mode: a CTA of %d threads does not fit an SM", h->block);
     h->grid = parts;
-    h->n_smem = 1;
     psst::GridView &g = h->gv;
-    int *rs = nullptr, *chd = nullptr;
+    int *rs = nullptr, *itd = nullptr;
     e = upload(h, &rs, split.data(), split.size());
-    if (e == cudaSuccess) e = upload(h, &chd, chunks.data(), chunks.size());
+    if (e == cudaSuccess) e = upload(h, &itd, items.data(), items.size());
     if (e == cudaSuccess) e = h->alloc(&g.c1, (size_t)(2 * N * nt));
     if (e == cudaSuccess && has2) e = h->alloc(&g.c2, (size_t)(2 * N * nt));
     if (e == cudaSuccess) e = h->alloc(&g.bar, 2);
     g.row_split = rs;
-    g.chunks = chd;
+    g.items = itd;
+    g.K = K;
     g.timeout_ns = 2000000000ULL;
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid buffers");
     return PSST_OK;
 }
 
-// CTA mode: choose each network's cluster size, group networks into size
-// classes (cluster size x CTAs per SM) and upload the launch lists.
-int setup_cta(psst_net *h, const psst_network_desc *d, int max_smem, const std::vector<int> &rowch,
-              const std::vector<uint8_t> &has2, cudaError_t *err) {
+// CTA mode: each network's cluster size and work items, size classes by
+// cluster size x CTAs per SM, launch lists (largest networks first).
+int setup_cta(psst_net *h, const psst_network_desc *d, const SmemCaps &caps, const std::vector<int> &n1,
+              const std::vector<int> &n2, const std::vector<uint8_t> &has2, cudaError_t *err) {
     const int n_nets = d->n_nets, nt = d->n_syn_types;
     std::vector<psst::NetPlan> plans((size_t)n_nets);
-    struct Key {
-        int cl, tier;
-    };
-    std::vector<Key> key((size_t)n_nets);
+    std::vector<int> cl_of((size_t)n_nets), per_sm((size_t)n_nets);
     std::vector<long long> need((size_t)n_nets);
     std::vector<double> cost((size_t)n_nets);
     for (int b = 0; b < n_nets; ++b) {
         const int n0 = d->net_neuron_off[b], N = d->net_neuron_off[b + 1] - n0;
         if ((long long)N * nt >= 65536)
             return fail(PSST_ERR_UNSUPPORTED, "net %d: %d neurons x %d synapse types must stay below 65536", b, N, nt);
-        const int *rc = rowch.data() + n0;
-        psst::NetPlan &pl = plans[b];
-        std::memset(&pl, 0, sizeof pl);
-        int chosen = 0;
-        long long nd = 0;
-        for (int cl = 1; cl <= PSST_MAX_CL && !chosen; cl *= 2) {
-            if (cl > 1 && N < 2 * cl) break;
-            std::vector<double> c((size_t)N);
-            for (int i = 0; i < N; ++i) c[i] = rc[i];
-            std::vector<int> split;
-            balanced_split(c, cl, split);
-            long long worst = 0;
-            for (int q = 0; q < cl; ++q) worst = std::max(worst, cta_need(N, nt, has2[b], rc, split[q], split[q + 1]));
-            if (worst <= max_smem) {
-                chosen = cl;
-                nd = worst;
-                for (int q = 0; q <= cl; ++q) pl.split[q] = split[q];
-                for (int q = 0; q < cl; ++q) {
-                    long long ch = 0;
-                    for (int i = split[q]; i < split[q + 1]; ++i) ch += rc[i];
-                    pl.chunks[q] = (int)ch;
-                }
-            }
-        }
-        if (!chosen)
+        const int cl = plan_network(d, b, n1, n2, has2[b], caps, &plans[b], &need[b]);
+        if (!cl)
             return fail(PSST_ERR_UNSUPPORTED, "net %d (%d neurons, %lld synapses) does not fit %d CTAs", b, N,
                         (long long)(d->row_ptr[n0 + N] - d->row_ptr[n0]), PSST_MAX_CL);
-        const int tier = nd * 4 <= max_smem ? 4 : nd * 2 <= max_smem ? 2 : 1;
-        key[b] = {chosen, tier};
-        need[b] = nd;
-        long long ch = 0;
-        for (int i = 0; i < N; ++i) ch += rc[i];
-        cost[b] = 4.0 * ch + 30.0 * N;
+        cl_of[b] = cl;
+        per_sm[b] = (int)std::max(1LL, std::min(4LL, (long long)caps.per_sm / (need[b] + caps.per_cta)));
+        double c = 0;
+        for (int i = n0; i < n0 + N; ++i) c += n1[i] + n2[i] + 30.0;
+        cost[b] = c;
     }
-    // classes in a fixed order: largest networks' classes first
-    const int cls[][2] = {{4, 1}, {4, 2}, {4, 4}, {2, 1}, {2, 2}, {2, 4}, {1, 1}, {1, 2}, {1, 4}};
     std::vector<int> all_lists;
     std::vector<std::pair<int, int>> ranges;
-    for (auto &ct : cls) {
-        std::vector<int> list;
-        for (int b = 0; b < n_nets; ++b)
-            if (key[b].cl == ct[0] && key[b].tier == ct[1]) list.push_back(b);
-        if (list.empty()) continue;
-        std::stable_sort(list.begin(), list.end(), [&](int a, int b2) { return cost[a] > cost[b2]; });
-        psst::ClassLaunch c{};
-        c.cl = ct[0];
-        c.n_nets = (int)list.size();
-        long long mx = 0, rows = 0, chunks = 0;
-        for (int b : list) {
-            mx = std::max(mx, need[b]);
-            rows += d->net_neuron_off[b + 1] - d->net_neuron_off[b];
-            for (int q = 0; q < ct[0]; ++q) chunks += plans[b].chunks[q];
+    for (int cl = PSST_MAX_CL; cl >= 1; cl /= 2) {
+        for (int k = 1; k <= 4; ++k) {
+            std::vector<int> list;
+            for (int b = 0; b < n_nets; ++b)
+                if (cl_of[b] == cl && per_sm[b] == k) list.push_back(b);
+            if (list.empty()) continue;
+            std::stable_sort(list.begin(), list.end(), [&](int a, int b2) { return cost[a] > cost[b2]; });
+            psst::ClassLaunch c{};
+            c.cl = cl;
+            c.n_nets = (int)list.size();
+            long long mx = 0;
+            for (int b : list) mx = std::max(mx, need[b]);
+            c.smem = (int)mx;
+            c.block = d->block_threads ? d->block_threads : ((1024 / k) / 32) * 32;
+            ranges.push_back({(int)all_lists.size(), (int)list.size()});
+            all_lists.insert(all_lists.end(), list.begin(), list.end());
+            h->classes.push_back(c);
         }
-        c.smem = (int)mx;
-        c.block = d->block_threads ? d->block_threads : (ct[1] == 4 ? 256 : ct[1] == 2 ? 512 : 1024);
-        c.G = d->row_group ? d->row_group : default_row_group((double)chunks / (double)std::max(1LL, rows));
-        if (c.block % c.G) return fail(PSST_ERR_INVALID_ARG, "row_group must divide block_threads");
-        ranges.push_back({(int)all_lists.size(), (int)list.size()});
-        all_lists.insert(all_lists.end(), list.begin(), list.end());
-        h->classes.push_back(c);
     }
     int *dl = nullptr;
     psst::NetPlan *dp = nullptr;
@@ -367,12 +406,11 @@ int setup_cta(psst_net *h, const psst_network_desc *d, int max_smem, const std::
     for (size_t i = 0; e == cudaSuccess && i < h->classes.size(); ++i) {
         h->classes[i].list = dl + ranges[i].first;
         h->classes[i].plans = dp;
-        e = psst::cta_prepare(h->classes[i].cl, max_smem);
+        e = psst::cta_prepare(h->classes[i].cl, caps.max_dyn);
     }
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "CTA mode setup");
-    // summary for psst_query: the largest class
     h->block = h->classes.empty() ? 0 : h->classes.back().block;
-    h->G = h->classes.empty() ? 0 : h->classes.back().G;
+    h->K = plans.empty() ? 0 : plans[h->classes.empty() ? 0 : all_lists.back()].K;
     h->smem = 0;
     h->grid = 0;
     for (auto &c : h->classes) {
@@ -415,29 +453,18 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
 
     const int n_nets = d->n_nets, nt = d->n_syn_types;
     const long long N = d->net_neuron_off[n_nets], S = d->row_ptr[N];
-    const int max_smem = psst::cta_max_smem(dev);
-    if (max_smem <= 0) return fail(PSST_ERR_CUDA, "cannot query shared memory size of device %d", dev);
+    SmemCaps caps;
+    rc = smem_caps(dev, &caps);
+    if (rc) return rc;
 
-    std::vector<int> rowch;
+    std::vector<int> n1, n2;
     std::vector<uint8_t> has2;
-    row_chunk_counts(d, rowch, has2);
-    // cluster sizes needed in CTA mode (0 = does not fit)
+    row_counts(d, n1, n2, has2);
     bool all_fit = true;
     for (int b = 0; b < n_nets && all_fit; ++b) {
-        const int n0 = d->net_neuron_off[b], Nb = d->net_neuron_off[b + 1] - n0;
-        bool fit = false;
-        for (int cl = 1; cl <= PSST_MAX_CL && !fit; cl *= 2) {
-            if (cl > 1 && Nb < 2 * cl) break;
-            std::vector<double> c((size_t)Nb);
-            for (int i = 0; i < Nb; ++i) c[i] = rowch[n0 + i];
-            std::vector<int> split;
-            balanced_split(c, cl, split);
-            long long worst = 0;
-            for (int q = 0; q < cl; ++q)
-                worst = std::max(worst, cta_need(Nb, nt, has2[b], rowch.data() + n0, split[q], split[q + 1]));
-            fit = worst <= max_smem;
-        }
-        all_fit = fit;
+        psst::NetPlan pl;
+        long long need = 0;
+        all_fit = plan_network(d, b, n1, n2, has2[b], caps, &pl, &need) != 0;
     }
     int mode = d->mode;
     if (mode == PSST_MODE_AUTO) mode = all_fit ? PSST_MODE_CTA : PSST_MODE_GRID;
@@ -448,7 +475,6 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
     h->device = dev;
     h->mode = mode;
     h->block = d->block_threads;
-    h->G = d->row_group;
     NetView &v = h->v;
     v.n_nets = n_nets;
     v.n_stypes = nt;
@@ -533,8 +559,8 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
         delete h;
         return cuda_fail(e, "psst_create_network");
     }
-    rc = mode == PSST_MODE_GRID ? setup_grid(h, d, max_smem, has2[0] != 0, rowch, &e)
-                                : setup_cta(h, d, max_smem, rowch, has2, &e);
+    rc = mode == PSST_MODE_GRID ? setup_grid(h, d, caps, has2[0] != 0, n1, n2, &e)
+                                : setup_cta(h, d, caps, n1, n2, has2, &e);
     if (rc) {
         h->release();
         delete h;
@@ -555,7 +581,7 @@ int psst_integrate(psst_net *h, int64_t n_steps, void *stream) {
     for (long long done = 0; done < n_steps;) {
         const int n = (int)std::min<long long>(chunk, n_steps - done);
         if (h->mode == PSST_MODE_GRID) {
-            cudaError_t e = psst::grid_launch(h->v, h->gv, h->step + done, n, h->grid, h->block, h->G, h->smem, st);
+            cudaError_t e = psst::grid_launch(h->v, h->gv, h->step + done, n, h->grid, h->block, h->smem, st);
             if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
             ++h->launches;
         } else {
@@ -665,7 +691,7 @@ int psst_query(const psst_net *h, psst_info *out) {
     out->rec_frames = h->v.rec_stride > 0 ? h->step / h->v.rec_stride - h->rec_reset / h->v.rec_stride : 0;
     out->mode = h->mode;
     out->block_threads = h->block;
-    out->row_group = h->G;
+    out->item_chunks = h->K;
     out->grid_ctas = h->grid;
     out->smem_bytes = h->smem;
     out->n_single_cta_nets = h->n_smem;

@@ -2,23 +2,25 @@
 //
 // One network is owned by a cluster of CL CTAs (CL = 1, 2 or 4, chosen per
 // network by its shared-memory footprint) for all of a launch's steps.  Each
-// CTA of the cluster holds every neuron of the network and the synapses of
-// its own block of CSR rows (postsynaptic neurons) in shared memory.  One
-// launch per size class integrates all networks of that class; blocks are
-// ordered largest network first.
+// CTA of the cluster owns a block of rows (postsynaptic neurons): their
+// synapses, as work items in shared memory (psst_syn.cuh), and their neuron
+// state.  Every CTA keeps the stage potential of all N neurons and the gate
+// maps of all (neuron, type) pairs.  One launch per size class integrates
+// all networks of that class, largest first.
 //
 // Per RK4 step (classic tableau, Sec. "Brain simulations as computational
 // graphs", RK4 paragraph) and stage s = 0..3:
-//   S-phase: synaptic current of the CTA's own rows at stage s (padded
-//            4-wide chunks, see psst_syn.cuh); each row's value is written to
-//            every CTA of the cluster (distributed shared memory);
-//   barrier: CTA barrier (CL = 1) or cluster barrier (CL > 1);
-//   N-phase: every CTA evaluates the HH right-hand side of all N neurons and
-//            the gate maps of all (presynaptic neuron, type) pairs -- the same
-//            values in every CTA, so nothing else has to be exchanged;
-//   barrier: CTA barrier.
-// The synaptic current is double-buffered by stage parity so a fast CTA can
-// write the next stage's values while a peer still reads this stage's.
+//   S-phase   each thread sums w G and wE G over its work items;
+//   barrier   (CTA);
+//   N-phase   the thread of owned neuron i adds its row's item partials
+//             (I_syn,i = V_i A_i - B_i), evaluates the HH right-hand side and
+//             the RK4 stage/combine, and writes the next stage potential to
+//             every CTA of the cluster (distributed shared memory); the other
+//             threads update the gate maps of all pairs from the stage-s
+//             potentials (identical values in every CTA);
+//   barrier   CTA barrier (CL = 1) or cluster barrier (CL > 1).
+// Stage potentials are double-buffered by stage parity, so a CTA can write
+// the next stage's values while a peer still reads this stage's.
 //
 // Synaptic gates: a gate's equation dr/dt = a T_j (1 - r) - b r is affine in
 // r with coefficients set by its presynaptic neuron j alone, so each RK4
@@ -26,7 +28,7 @@
 // s^(s) = U_s + X_s r0 + Z_s s0) with the maps propagated once per
 // (neuron, type) and stage; the step-end map is applied lazily at the next
 // step's first stage.  This evaluates the same RK4 map as the textbook stage
-// recursion, with each synapse costing one FMA per stage.
+// recursion, with each synapse costing one FMA per stage for its gate.
 #include <cuda_runtime.h>
 
 #include "psst_device.cuh"
@@ -62,40 +64,61 @@ struct SmemCoef {
     __device__ __forceinline__ float4 s(int i) const { return t2[i]; }
 };
 
-template <int CL>
-struct IsynOut {
-    float *isyn;  // this stage's buffer, indexed by network row
-    int r_lo;
-    unsigned rank;
-    __device__ __forceinline__ void operator()(int row, float x) const {
-        float *p = isyn + r_lo + row;
-        *p = x;
+template <int ST, int CL, bool HAS2>
+__device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0, int N, int nt, int r_lo, int nown,
+                                      unsigned rank, int tq, long long step, float dt, float *vst, float *y0,
+                                      float *acc, float *ys, const float *prm, const float *iext, float2 *cur1,
+                                      float2 *acc1, float2 *fin1, float4 *cur2, float4 *acc2, float4 *fin2,
+                                      const float *stab) {
+    const int tid = threadIdx.x, nthr = blockDim.x, M = N * nt;
+    const float *vcur = vst + (ST & 1) * N;
+    float *vnxt = vst + ((ST + 1) & 1) * N;
+    sphase<ST, HAS2>(it, SmemCoef{ST == 0 ? fin1 : cur1, ST == 0 ? fin2 : cur2});
+    __syncthreads();
+    for (int i = tid; i < nown; i += nthr) {
+        const float V = vcur[r_lo + i];
+        const float isyn = row_current<HAS2>(it, i, V);
+        const float vn = neuron_update<ST>(i, nown, V, y0, acc, ys, prm, iext[i], isyn, dt);
+        vnxt[r_lo + i] = vn;
         if (CL > 1) {
 #pragma unroll
-            for (unsigned q = 1; q < CL; ++q) st_peer(p, (rank + q) % CL, x);
+            for (unsigned q = 1; q < CL; ++q) st_peer(vnxt + r_lo + i, (rank + q) % CL, vn);
+        }
+        if (ST == 3 && v.rec_stride > 0 && ((step + 1) % v.rec_stride) == 0) {
+            const long long frame = (step + 1) / v.rec_stride - 1;
+            v.rec[(frame % v.rec_cap) * v.N + n0 + r_lo + i] = vn;
         }
     }
-};
+    for (int p = tq; p < M; p += nthr) {
+        float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 &c2 = HAS2 ? cur2[p] : d4;
+        float4 &a2 = HAS2 ? acc2[p] : d4;
+        float4 &f2 = HAS2 ? fin2[p] : d4;
+        coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], fin1[p], c2, a2, f2);
+    }
+    if (CL > 1) cluster_sync();
+    else __syncthreads();
+}
 
 template <int CL, bool HAS2>
-__device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long step0, int nsteps, int G,
+__device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long step0, int nsteps,
                         unsigned char *smem, const float *stab) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const unsigned rank = CL > 1 ? cluster_rank() : 0u;
     const int n0 = v.net_off[b], N = v.net_off[b + 1] - n0;
     const int nt = v.n_stypes, M = N * nt;
     const long long sbase = v.row_ptr[n0];
-    const int r_lo = pl.split[rank], nrows = pl.split[rank + 1] - r_lo;
-    const NeuronLayout L = make_nlayout(N, nt, HAS2, nrows);
+    const int r_lo = pl.split[rank], nown = pl.split[rank + 1] - r_lo;
+    const NeuronLayout L = make_nlayout(nown, N, M, HAS2);
     float *y0 = (float *)(smem + L.y0), *ys = (float *)(smem + L.ys), *acc = (float *)(smem + L.acc);
-    float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext);
-    float *isyn = (float *)(smem + L.isyn), *vst = (float *)(smem + L.vst);
+    float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext), *inp = (float *)(smem + L.inp);
+    float *vst = (float *)(smem + L.vst);
     float2 *cur1 = (float2 *)(smem + L.cur1), *acc1 = (float2 *)(smem + L.acc1), *fin1 = (float2 *)(smem + L.fin1);
     float4 *cur2 = HAS2 ? (float4 *)(smem + L.cur2) : nullptr;
     float4 *acc2 = HAS2 ? (float4 *)(smem + L.acc2) : nullptr;
     float4 *fin2 = HAS2 ? (float4 *)(smem + L.fin2) : nullptr;
     int *tmp = (int *)(smem + L.tmp);
-    RowChunks rc = carve_rows(smem + L.syn, nrows, pl.chunks[rank], HAS2);
+    Items it = carve_items(smem + L.syn, nown, pl.K, pl.n1[rank], pl.n2[rank], HAS2);
 
     float *gV = v.state + n0;
     float *gr = v.state + 4 * v.N + sbase;
@@ -103,21 +126,23 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     const float *gw = v.weight + sbase;
     const uint32_t *gcode = v.syn_code + sbase;
 
-    for (int i = tid; i < N; i += nthr) {
-        const float V = gV[i];
-        y0[i] = V;
-        vst[i] = V;  // stage-0 potential, parity 0
+    for (int j = tid; j < N; j += nthr) vst[j] = gV[j];  // stage-0 potentials, parity 0
+    for (int i = tid; i < nown; i += nthr) {
+        const int gi = r_lo + i;
 #pragma unroll
-        for (int x = 1; x < 4; ++x) {
-            const float y = gV[(long long)x * v.N + i];
-            y0[x * N + i] = y;
-            ys[x * N + i] = y;
+        for (int x = 0; x < 4; ++x) {
+            const float y = gV[(long long)x * v.N + gi];
+            y0[x * nown + i] = y;
+            ys[x * nown + i] = y;
         }
-        const float *p = v.nparams + (long long)v.neuron_type[n0 + i] * PSST_NEURON_NPARAM;
-        prm[NP_C * N + i] = 1.0f / p[NP_C];
+        const float *p = v.nparams + (long long)v.neuron_type[n0 + gi] * PSST_NEURON_NPARAM;
+        prm[NP_C * nown + i] = 1.0f / p[NP_C];
 #pragma unroll
-        for (int x = 1; x < PSST_NEURON_NPARAM; ++x) prm[x * N + i] = p[x];
+        for (int x = 1; x < PSST_NEURON_NPARAM; ++x) prm[x * nown + i] = p[x];
+        inp[i] = v.i_const[n0 + gi];
+        inp[nown + i] = v.pulse_amp ? v.pulse_amp[n0 + gi] : 0.0f;
     }
+    const long long pon = v.pulse_on[b], poff = v.pulse_off[b];
     for (int k = tid; k < M; k += nthr) {
         fin1[k] = make_float2(0.0f, 1.0f);
         if (HAS2) {
@@ -125,77 +150,48 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
             fin2[k] = make_float4(0.0f, 0.0f, 1.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
         }
     }
-    load_rows<HAS2>(rc, v, n0, sbase, r_lo, gr, gs, gw, gcode, stab, tmp);  // ends with __syncthreads
+    load_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gw, gcode, stab, tmp);  // ends with __syncthreads
     if (CL > 1) cluster_sync();
 
     const float dt = v.dt;
-    // coefficient pairs are taken by the threads after the neuron threads
-    int tq = tid - N % nthr;
+    // gate-map pairs are taken by the threads after the owned-neuron threads
+    int tq = tid - nown % nthr;
     if (tq < 0) tq += nthr;
 
-    for (int it = 0; it < nsteps; ++it) {
-        const long long step = step0 + it;
-        for (int i = tid; i < N; i += nthr) iext[i] = input_current(v, b, (long long)n0 + i, step);
-#define PSST_STAGE(ST)                                                                                     \
-    {                                                                                                      \
-        const float *vcur = vst + (ST & 1) * N;                                                            \
-        float *vnxt = vst + ((ST + 1) & 1) * N;                                                            \
-        float *isy = isyn + (ST & 1) * N;                                                                  \
-        const SmemCoef cf{ST == 0 ? fin1 : cur1, ST == 0 ? fin2 : cur2};                                   \
-        sphase<ST, HAS2>(rc, vcur + r_lo, cf, G, IsynOut<CL>{isy, r_lo, rank});                            \
-        if (CL > 1) cluster_sync();                                                                        \
-        else __syncthreads();                                                                              \
-        for (int i = tid; i < N; i += nthr) {                                                              \
-            const float vn = neuron_update<ST>(i, N, vcur[i], y0, acc, ys, prm, iext[i], isy[i], dt);      \
-            vnxt[i] = vn;                                                                                  \
-            if (ST == 3 && rank == 0 && v.rec_stride > 0 && ((step + 1) % v.rec_stride) == 0) {            \
-                const long long frame = (step + 1) / v.rec_stride - 1;                                     \
-                v.rec[(frame % v.rec_cap) * v.N + n0 + i] = vn;                                            \
-            }                                                                                              \
-        }                                                                                                  \
-        for (int p = tq; p < M; p += nthr) {                                                               \
-            float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);                                                   \
-            float4 &c2 = HAS2 ? cur2[p] : d4;                                                              \
-            float4 &a2 = HAS2 ? acc2[p] : d4;                                                              \
-            float4 &f2 = HAS2 ? fin2[p] : d4;                                                              \
-            coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], fin1[p], c2, a2, \
-                                  f2);                                                                     \
-        }                                                                                                  \
-        __syncthreads();                                                                                   \
-    }
-        PSST_STAGE(0)
-        PSST_STAGE(1)
-        PSST_STAGE(2)
-        PSST_STAGE(3)
-#undef PSST_STAGE
+    for (int itn = 0; itn < nsteps; ++itn) {
+        const long long step = step0 + itn;
+        const bool in_pulse = step >= pon && step < poff;
+        for (int i = tid; i < nown; i += nthr)
+            iext[i] = input_current(v, inp[i], inp[nown + i], in_pulse, (long long)n0 + r_lo + i, step);
+        // iext is read in the N-phase, after the S-phase barrier
+        stage<0, CL, HAS2>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+                           acc1, fin1, cur2, acc2, fin2, stab);
+        stage<1, CL, HAS2>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+                           acc1, fin1, cur2, acc2, fin2, stab);
+        stage<2, CL, HAS2>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+                           acc1, fin1, cur2, acc2, fin2, stab);
+        stage<3, CL, HAS2>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+                           acc1, fin1, cur2, acc2, fin2, stab);
     }
 
-    // write back: own synapses with the last step's gate map; neurons by rank 0
-    struct Fin {
-        const float2 *f1;
-        const float4 *f2;
-        __device__ __forceinline__ float2 r(int i) const { return f1[i]; }
-        __device__ __forceinline__ float4 s(int i) const { return f2[i]; }
-    } fin{fin1, fin2};
-    store_rows<HAS2>(rc, v, n0, sbase, r_lo, gr, gs, gcode, stab, fin);
-    if (rank == 0) {
-        bool bad = false;
-        for (int i = tid; i < N; i += nthr) {
+    // write back: owned synapses with the last step's gate map, owned neurons
+    store_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gcode, stab, SmemCoef{fin1, fin2});
+    bool bad = false;
+    for (int i = tid; i < nown; i += nthr) {
 #pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                const float y = y0[x * N + i];
-                bad |= !isfinite(y);
-                gV[(long long)x * v.N + i] = y;
-            }
+        for (int x = 0; x < 4; ++x) {
+            const float y = y0[x * nown + i];
+            bad |= !isfinite(y);
+            gV[(long long)x * v.N + r_lo + i] = y;
         }
-        if (bad) set_error(v.err, PSST_ERR_NONFINITE);
     }
+    if (bad) set_error(v.err, PSST_ERR_NONFINITE);
     if (CL > 1) cluster_sync();  // no CTA leaves while a peer may still write into it
 }
 
 template <int CL>
 __global__ void __launch_bounds__(1024) net_kernel(NetView v, const int *list, const NetPlan *plans,
-                                                   long long step0, int nsteps, int G) {
+                                                   long long step0, int nsteps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float stab[PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM];
     for (int i = threadIdx.x; i < v.n_stypes * PSST_SYN_NPARAM; i += blockDim.x) {
@@ -205,14 +201,14 @@ __global__ void __launch_bounds__(1024) net_kernel(NetView v, const int *list, c
     }
     __syncthreads();
     const int b = list[blockIdx.x / CL];
-    if (v.net_flags[b] & NET_HAS2) run_net<CL, true>(v, b, plans[b], step0, nsteps, G, smem, stab);
-    else run_net<CL, false>(v, b, plans[b], step0, nsteps, G, smem, stab);
+    if (v.net_flags[b] & NET_HAS2) run_net<CL, true>(v, b, plans[b], step0, nsteps, smem, stab);
+    else run_net<CL, false>(v, b, plans[b], step0, nsteps, smem, stab);
 }
 
 template <int CL>
 cudaError_t launch_cl(const NetView &v, const ClassLaunch &c, long long step0, int nsteps, cudaStream_t stream) {
     if (CL == 1) {
-        net_kernel<1><<<c.n_nets, c.block, c.smem, stream>>>(v, c.list, c.plans, step0, nsteps, c.G);
+        net_kernel<1><<<c.n_nets, c.block, c.smem, stream>>>(v, c.list, c.plans, step0, nsteps);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -227,16 +223,12 @@ cudaError_t launch_cl(const NetView &v, const ClassLaunch &c, long long step0, i
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, net_kernel<CL>, v, c.list, c.plans, step0, nsteps, c.G);
+    return cudaLaunchKernelEx(&cfg, net_kernel<CL>, v, c.list, c.plans, step0, nsteps);
 }
 
 }  // namespace
 
-int cta_max_smem(int device) {
-    int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return -1;
-    return v - (int)(PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM * sizeof(float) + 64);
-}
+int cta_static_smem() { return (int)(PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM * sizeof(float)); }
 
 cudaError_t cta_prepare(int cl, int max_smem) {
     const void *k = cl == 1 ? (const void *)net_kernel<1> : cl == 2 ? (const void *)net_kernel<2>

@@ -53,7 +53,8 @@ struct GridView {
     float4 *c2;                  // [2][N * n_stypes] gate maps (s), second-order networks only
     unsigned *bar;               // [2] barrier arrival counter and generation
     const int *row_split;        // [gridDim.x + 1] first row owned by each CTA
-    const int *chunks;           // [gridDim.x] synapse chunks of each CTA's rows
+    const int *items;            // [2][gridDim.x] first- and second-order work items of each CTA
+    int K;                       // 4-synapse chunks per work item
     unsigned long long timeout_ns;  // limit of one barrier wait
 };
 
@@ -64,26 +65,29 @@ enum { SP_KIND = 0, SP_A, SP_B, SP_K3, SP_K4, SP_KD, SP_E, SP_VP, SP_KP };
 #define PSST_MAX_CL 4
 
 // Per-network plan of the CTA/cluster kernel: the rows owned by each CTA of
-// the network's cluster and their number of 4-wide synapse chunks.
+// the network's cluster, the work-item size K (4-synapse chunks per item)
+// and each CTA's number of first- and second-order items.
 struct NetPlan {
     int split[PSST_MAX_CL + 1];
-    int chunks[PSST_MAX_CL];
+    int K;
+    int n1[PSST_MAX_CL];
+    int n2[PSST_MAX_CL];
 };
 
-// Shared-memory layout of the neuron part (all N neurons of the network, or
-// a grid CTA's own neurons) followed by the synapse chunks of the CTA's own
-// rows.  Computed the same way on host (sizing) and device (addressing).
-// Offsets in bytes, 16-aligned.
+// Shared-memory layout of one CTA: its own neurons (n_own), the stage
+// potential of every neuron it needs (n_all), the gate maps of m
+// (neuron, type) pairs, then the synapse work items.  Computed the same way
+// on host (sizing) and device (addressing).  Offsets in bytes, 16-aligned.
 struct NeuronLayout {
-    int cur2, acc2, fin2;  // float4 [N*nt]: s-maps (second order only)
-    int cur1, acc1, fin1;  // float2 [N*nt]: r-maps
-    int y0, ys, acc;       // float [4N]: step-start state, stage m/h/n, RK4 k-sum
-    int prm;               // float [9N]: 1/C, gNa, gK, gL, ENa, EK, EL, gKL, EKL
-    int iext;              // float [N]
-    int isyn;              // float [2][N]: synaptic current, by stage parity
-    int vst;               // float [2][N]: stage potential, by stage parity
-    int tmp;               // int [nrows+1]: scan scratch
-    int syn;               // start of the synapse chunks
+    int cur2, acc2, fin2;  // float4 [m]: s-maps (second order only)
+    int cur1, acc1, fin1;  // float2 [m]: r-maps
+    int y0, ys, acc;       // float [4][n_own]: step-start state, stage m/h/n, RK4 k-sum
+    int prm;               // float [9][n_own]: 1/C, gNa, gK, gL, ENa, EK, EL, gKL, EKL
+    int iext;              // float [n_own]
+    int inp;               // float [2][n_own]: constant current, pulse amplitude
+    int vst;               // float [2][n_all]: stage potential, by stage parity
+    int tmp;               // int [2][n_own + 1]: scan scratch
+    int syn;               // start of the synapse items
 };
 
 __host__ __device__ inline int lay_take(int &o, long long bytes) {
@@ -92,24 +96,25 @@ __host__ __device__ inline int lay_take(int &o, long long bytes) {
     return at;
 }
 
-__host__ __device__ inline NeuronLayout make_nlayout(int N, int nt, bool has2, int nrows) {
+__host__ __device__ inline NeuronLayout make_nlayout(int n_own, int n_all, int m, bool has2) {
     NeuronLayout L;
     int o = 0;
-    const long long M = (long long)N * nt;
-    L.cur2 = has2 ? lay_take(o, 16 * M) : -1;
-    L.acc2 = has2 ? lay_take(o, 16 * M) : -1;
-    L.fin2 = has2 ? lay_take(o, 16 * M) : -1;
-    L.cur1 = lay_take(o, 8 * M);
-    L.acc1 = lay_take(o, 8 * M);
-    L.fin1 = lay_take(o, 8 * M);
-    L.y0 = lay_take(o, 16LL * N);
-    L.ys = lay_take(o, 16LL * N);
-    L.acc = lay_take(o, 16LL * N);
-    L.prm = lay_take(o, 36LL * N);
-    L.iext = lay_take(o, 4LL * N);
-    L.isyn = lay_take(o, 8LL * N);
-    L.vst = lay_take(o, 8LL * N);
-    L.tmp = lay_take(o, 4LL * (nrows + 1));
+    L.cur2 = has2 ? lay_take(o, 16LL * m) : -1;
+    L.acc2 = has2 ? lay_take(o, 16LL * m) : -1;
+    L.fin2 = has2 ? lay_take(o, 16LL * m) : -1;
+    L.cur1 = lay_take(o, 8LL * m);
+    L.acc1 = lay_take(o, 8LL * m);
+    L.fin1 = lay_take(o, 8LL * m);
+    // the stage potentials sit at the same offset in every CTA of a cluster
+    // (peers write into them through distributed shared memory)
+    L.vst = lay_take(o, 8LL * n_all);
+    L.y0 = lay_take(o, 16LL * n_own);
+    L.ys = lay_take(o, 16LL * n_own);
+    L.acc = lay_take(o, 16LL * n_own);
+    L.prm = lay_take(o, 36LL * n_own);
+    L.iext = lay_take(o, 4LL * n_own);
+    L.inp = lay_take(o, 8LL * n_own);
+    L.tmp = lay_take(o, 8LL * (n_own + 1));
     L.syn = o;
     return L;
 }
@@ -168,10 +173,13 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
     return c0;
 }
 
-// External current of global neuron gi (network b) during global step k.
-__device__ __forceinline__ float input_current(const NetView &v, int b, long long gi, long long k) {
-    float I = v.i_const[gi];
-    if (v.pulse_amp && k >= v.pulse_on[b] && k < v.pulse_off[b]) I += v.pulse_amp[gi];
+// External current of global neuron gi during global step k, given its
+// constant current, its pulse amplitude and whether step k lies inside its
+// network's pulse window.
+__device__ __forceinline__ float input_current(const NetView &v, float i_const, float pulse_amp, bool in_pulse,
+                                               long long gi, long long k) {
+    float I = i_const;
+    if (in_pulse) I += pulse_amp;
     if (v.noise_thresh) {
         const uint32_t x = philox_word0((uint32_t)k, (uint32_t)((unsigned long long)k >> 32),
                                         (uint32_t)gi, 0u, (uint32_t)v.noise_seed,

@@ -77,27 +77,59 @@ struct GlobalCoef {
     __device__ __forceinline__ float4 s(int i) const { return __ldcg(t2 + i); }
 };
 
-struct LocalOut {
-    float *isyn;
-    __device__ __forceinline__ void operator()(int row, float x) const { isyn[row] = x; }
-};
+template <int ST, bool HAS2>
+__device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, const Items &it, int lo, int N,
+                                           int nt, int M, int tq, long long step, float dt, float *vst, float *y0,
+                                           float *acc, float *ys, const float *prm, const float *iext,
+                                           float2 *cur1, float2 *acc1, float4 *cur2, float4 *acc2,
+                                           const float *stab) {
+    const int tid = threadIdx.x, nthr = blockDim.x, Mloc = N * nt;
+    const float *vcur = vst + (ST & 1) * N;
+    float *vnxt = vst + ((ST + 1) & 1) * N;
+    sphase<ST, HAS2>(it, GlobalCoef{g.c1 + (size_t)(ST & 1) * M, HAS2 ? g.c2 + (size_t)(ST & 1) * M : nullptr});
+    __syncthreads();
+    for (int i = tid; i < N; i += nthr) {
+        const float V = vcur[i];
+        const float isyn = row_current<HAS2>(it, i, V);
+        const float vn = neuron_update<ST>(i, N, V, y0, acc, ys, prm, iext[i], isyn, dt);
+        vnxt[i] = vn;
+        if (ST == 3 && v.rec_stride > 0 && ((step + 1) % v.rec_stride) == 0) {
+            const long long frame = (step + 1) / v.rec_stride - 1;
+            v.rec[(frame % v.rec_cap) * v.N + lo + i] = vn;
+        }
+    }
+    // gate maps of the own pairs: local copy for the next stage, and the
+    // table every CTA reads at the next stage
+    float2 *o1 = g.c1 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt;
+    float4 *o2 = HAS2 ? g.c2 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt : nullptr;
+    for (int p = tq; p < Mloc; p += nthr) {
+        float2 f1;
+        float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;
+        float4 &c2 = HAS2 ? cur2[p] : d4;
+        float4 &a2 = HAS2 ? acc2[p] : d4;
+        coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
+        o1[p] = ST == 3 ? f1 : cur1[p];
+        if (HAS2) o2[p] = ST == 3 ? f2 : cur2[p];
+    }
+    return grid_barrier(g.bar, g.timeout_ns, v.err);
+}
 
 template <bool HAS2>
-__device__ void grid_run(const NetView &v, const GridView &g, long long step0, int nsteps, int G,
-                         unsigned char *smem, const float *stab) {
+__device__ void grid_run(const NetView &v, const GridView &g, long long step0, int nsteps, unsigned char *smem,
+                         const float *stab) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lo = g.row_split[blockIdx.x], N = g.row_split[blockIdx.x + 1] - lo;
     const int nt = v.n_stypes, Mloc = N * nt;
     const int M = (int)(v.N * nt);
-    const NeuronLayout L = make_nlayout(N, nt, HAS2, N);
+    const NeuronLayout L = make_nlayout(N, N, Mloc, HAS2);
     float *y0 = (float *)(smem + L.y0), *ys = (float *)(smem + L.ys), *acc = (float *)(smem + L.acc);
-    float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext);
-    float *isyn = (float *)(smem + L.isyn), *vst = (float *)(smem + L.vst);
+    float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext), *inp = (float *)(smem + L.inp);
+    float *vst = (float *)(smem + L.vst);
     float2 *cur1 = (float2 *)(smem + L.cur1), *acc1 = (float2 *)(smem + L.acc1);
     float4 *cur2 = HAS2 ? (float4 *)(smem + L.cur2) : nullptr;
     float4 *acc2 = HAS2 ? (float4 *)(smem + L.acc2) : nullptr;
     int *tmp = (int *)(smem + L.tmp);
-    RowChunks rc = carve_rows(smem + L.syn, N, g.chunks[blockIdx.x], HAS2);
+    Items it = carve_items(smem + L.syn, N, g.K, g.items[blockIdx.x], g.items[gridDim.x + blockIdx.x], HAS2);
 
     float *gV = v.state + lo;
     float *gr = v.state + 4 * v.N;
@@ -105,10 +137,9 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
 
     for (int i = tid; i < N; i += nthr) {
         const float V = gV[i];
-        y0[i] = V;
         vst[i] = V;
 #pragma unroll
-        for (int x = 1; x < 4; ++x) {
+        for (int x = 0; x < 4; ++x) {
             const float y = gV[(long long)x * v.N + i];
             y0[x * N + i] = y;
             ys[x * N + i] = y;
@@ -117,7 +148,10 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         prm[NP_C * N + i] = 1.0f / p[NP_C];
 #pragma unroll
         for (int x = 1; x < PSST_NEURON_NPARAM; ++x) prm[x * N + i] = p[x];
+        inp[i] = v.i_const[lo + i];
+        inp[N + i] = v.pulse_amp ? v.pulse_amp[lo + i] : 0.0f;
     }
+    const long long pon = v.pulse_on[0], poff = v.pulse_off[0];
     // identity step-end maps of the own pairs in table 0 (read by stage 0)
     for (int p = tid; p < Mloc; p += nthr) {
         const int gi = lo * nt + p;
@@ -127,53 +161,32 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
             g.c2[gi] = make_float4(0.0f, 0.0f, 1.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
         }
     }
-    load_rows<HAS2>(rc, v, 0, 0, lo, gr, gs, v.weight, v.syn_code, stab, tmp);
+    load_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.weight, v.syn_code, stab, tmp);
     bool ok = grid_barrier(g.bar, g.timeout_ns, v.err);
 
     const float dt = v.dt;
     int tq = tid - N % nthr;
     if (tq < 0) tq += nthr;
-    for (int it = 0; ok && it < nsteps; ++it) {
-        const long long step = step0 + it;
-        for (int i = tid; i < N; i += nthr) iext[i] = input_current(v, 0, (long long)lo + i, step);
-#define PSST_GSTAGE(ST)                                                                                    \
-    if (ok) {                                                                                              \
-        const float *vcur = vst + (ST & 1) * N;                                                            \
-        float *vnxt = vst + ((ST + 1) & 1) * N;                                                            \
-        const GlobalCoef cf{g.c1 + (size_t)(ST & 1) * M, HAS2 ? g.c2 + (size_t)(ST & 1) * M : nullptr};    \
-        sphase<ST, HAS2>(rc, vcur, cf, G, LocalOut{isyn});                                                 \
-        __syncthreads();                                                                                   \
-        for (int i = tid; i < N; i += nthr) {                                                              \
-            const float vn = neuron_update<ST>(i, N, vcur[i], y0, acc, ys, prm, iext[i], isyn[i], dt);     \
-            vnxt[i] = vn;                                                                                  \
-            if (ST == 3 && v.rec_stride > 0 && ((step + 1) % v.rec_stride) == 0) {                         \
-                const long long frame = (step + 1) / v.rec_stride - 1;                                     \
-                v.rec[(frame % v.rec_cap) * v.N + lo + i] = vn;                                            \
-            }                                                                                              \
-        }                                                                                                  \
-        float2 *o1 = g.c1 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt;                                  \
-        float4 *o2 = HAS2 ? g.c2 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt : nullptr;                 \
-        for (int p = tq; p < Mloc; p += nthr) {                                                            \
-            float2 f1;                                                                                     \
-            float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;                                          \
-            float4 &c2 = HAS2 ? cur2[p] : d4;                                                              \
-            float4 &a2 = HAS2 ? acc2[p] : d4;                                                              \
-            coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2); \
-            o1[p] = ST == 3 ? f1 : cur1[p];                                                                \
-            if (HAS2) o2[p] = ST == 3 ? f2 : cur2[p];                                                      \
-        }                                                                                                  \
-        ok = grid_barrier(g.bar, g.timeout_ns, v.err);                                                     \
-    }
-        PSST_GSTAGE(0)
-        PSST_GSTAGE(1)
-        PSST_GSTAGE(2)
-        PSST_GSTAGE(3)
-#undef PSST_GSTAGE
+    for (int itn = 0; ok && itn < nsteps; ++itn) {
+        const long long step = step0 + itn;
+        const bool in_pulse = step >= pon && step < poff;
+        for (int i = tid; i < N; i += nthr)
+            iext[i] = input_current(v, inp[i], inp[N + i], in_pulse, (long long)lo + i, step);
+        ok = grid_stage<0, HAS2>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1, acc1,
+                                 cur2, acc2, stab);
+        if (ok)
+            ok = grid_stage<1, HAS2>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1, acc1,
+                                     cur2, acc2, stab);
+        if (ok)
+            ok = grid_stage<2, HAS2>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1, acc1,
+                                     cur2, acc2, stab);
+        if (ok)
+            ok = grid_stage<3, HAS2>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1, acc1,
+                                     cur2, acc2, stab);
     }
     if (!ok) return;  // error recorded; global state keeps its value from before the call
 
-    const GlobalCoef fin{g.c1, HAS2 ? g.c2 : nullptr};
-    store_rows<HAS2>(rc, v, 0, 0, lo, gr, gs, v.syn_code, stab, fin);
+    store_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.syn_code, stab, GlobalCoef{g.c1, HAS2 ? g.c2 : nullptr});
     bool bad = false;
     for (int i = tid; i < N; i += nthr) {
 #pragma unroll
@@ -186,8 +199,7 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
     if (bad) set_error(v.err, PSST_ERR_NONFINITE);
 }
 
-__global__ void __launch_bounds__(1024, 1) grid_kernel(NetView v, GridView g, long long step0, int nsteps,
-                                                        int G) {
+__global__ void __launch_bounds__(1024, 1) grid_kernel(NetView v, GridView g, long long step0, int nsteps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float stab[PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM];
     for (int i = threadIdx.x; i < v.n_stypes * PSST_SYN_NPARAM; i += blockDim.x) {
@@ -196,8 +208,8 @@ __global__ void __launch_bounds__(1024, 1) grid_kernel(NetView v, GridView g, lo
         stab[i] = x;
     }
     __syncthreads();
-    if (v.net_flags[0] & NET_HAS2) grid_run<true>(v, g, step0, nsteps, G, smem, stab);
-    else grid_run<false>(v, g, step0, nsteps, G, smem, stab);
+    if (v.net_flags[0] & NET_HAS2) grid_run<true>(v, g, step0, nsteps, smem, stab);
+    else grid_run<false>(v, g, step0, nsteps, smem, stab);
 }
 
 }  // namespace
@@ -209,10 +221,10 @@ cudaError_t grid_occupancy(int block, int smem, int *blocks_per_sm) {
 }
 
 cudaError_t grid_launch(const NetView &v, const GridView &g, long long step0, int nsteps, int grid, int block,
-                        int G, int smem, cudaStream_t stream) {
+                        int smem, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(g.bar, 0, 2 * sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
-    void *args[] = {(void *)&v, (void *)&g, (void *)&step0, (void *)&nsteps, (void *)&G};
+    void *args[] = {(void *)&v, (void *)&g, (void *)&step0, (void *)&nsteps};
     return cudaLaunchCooperativeKernel((const void *)grid_kernel, dim3(grid), dim3(block), args, (size_t)smem,
                                        stream);
 }

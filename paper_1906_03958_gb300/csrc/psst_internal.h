@@ -11,19 +11,19 @@ namespace psst {
 struct ClassLaunch {
     int cl;               // CTAs per network (1, 2 or 4)
     int n_nets;           // networks in the class
-    int block, G, smem;   // CTA size, lanes per CSR row, dynamic shared memory
+    int block, smem;      // CTA size, dynamic shared memory
     const int *list;      // [n_nets] device: network indices, largest first
     const NetPlan *plans; // [all nets] device
 };
 
 // CTA/cluster batched kernel (psst_cta.cu).
-int cta_max_smem(int device);
+int cta_static_smem();
 cudaError_t cta_prepare(int cl, int max_smem);
 cudaError_t cta_launch(const NetView &v, const ClassLaunch &c, long long step0, int nsteps, cudaStream_t stream);
 
 // Grid-wide single-network kernel (psst_grid.cu).
 cudaError_t grid_occupancy(int block, int smem, int *blocks_per_sm);
 cudaError_t grid_launch(const NetView &v, const GridView &g, long long step0, int nsteps, int grid, int block,
-                        int G, int smem, cudaStream_t stream);
+                        int smem, cudaStream_t stream);
 
 }  // namespace psst

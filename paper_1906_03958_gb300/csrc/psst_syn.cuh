@@ -1,61 +1,75 @@
-// Synapses of a block of CSR rows held in shared memory in a padded,
-// 4-wide chunk layout, and the S-phase (synaptic current of every owned
-// row at one RK4 stage) over that layout.  Shared by the CTA/cluster kernel
-// and the grid-wide kernel.
+// Synapses of a block of CSR rows held in shared memory as fixed-size work
+// items, the S-phase over them, and the per-neuron / per-gate-map stage
+// updates.  Shared by the CTA/cluster kernel and the grid-wide kernel.
 //
-// Layout.  Each row's synapses are split into its first-order gates and its
-// second-order (r, s) pairs; each part is padded to a multiple of 4 with
-// inert entries (w = 0, gate 0, coefficient index 0).  Chunk c holds 4
-// synapses as float4 r, float4 w, float4 wE (= w * E of its type),
-// ushort4 id (coefficient index pre * n_types + type) and, second order only,
-// float4 s.  Row i owns chunks [cb[i], cm[i]) (first order) and
-// [cm[i], cb[i+1]) (second order).
+// Work items.  Each row's synapses are split into its first-order gates and
+// its second-order (r, s) pairs.  Each part is cut into items of K chunks of
+// 4 synapses (the last item of a row padded with inert entries: w = 0,
+// gate 0, coefficient index 0).  All rows' first-order items form list 1,
+// all second-order items list 2.  A list of n items is stored slot-major:
+// chunk j of item t sits at j * n + t, so the lanes of a warp read
+// consecutive 16-byte slots.  Per chunk: float4 r, w, wE (= w * E of its
+// type), ushort4 coefficient index (pre * n_types + type), and float4 s for
+// list 2.  Row i owns items [ib1[i], ib1[i+1]) of list 1 and
+// [ib2[i], ib2[i+1]) of list 2.
 //
-// Current.  I_syn,i = sum_k w_k G_k (V_i - E_k) = V_i A_i - B_i with
-// A_i = sum_k w_k G_k and B_i = sum_k (w_k E_k) G_k, accumulated per lane and
-// summed over the row's G lanes by a shuffle tree (fixed order).
+// S-phase.  One thread per item accumulates A = sum w G and B = sum wE G
+// over its K chunks and stores them; after a barrier the thread of neuron i
+// adds its row's item partials in item order and forms
+// I_syn,i = V_i A_i - B_i.  The summation order is fixed by the layout, so
+// results are bitwise reproducible.
 #pragma once
 
 #include "psst_device.cuh"
 
 namespace psst {
 
-struct RowChunks {
-    int nrows;
-    int *cb;       // [nrows+1]
-    int *cm;       // [nrows]
-    float4 *r, *s, *w, *we;
+struct Items {
+    int nrows, K, n1, n2;
+    int *ib1, *ib2;           // [nrows+1] item offsets of each row in list 1 / list 2
+    float4 *r, *s, *w, *we;   // [K * (n1 + n2)] chunks, list 1 then list 2 (s: list 2 only)
     ushort4 *id;
+    float *pa, *pb;           // [n1 + n2] item partial sums
 };
 
-// Shared-memory bytes of the synapse part for `chunks` chunks and `nrows` rows.
-__host__ __device__ inline long long syn_smem_bytes(long long chunks, int nrows, bool has2) {
-    const long long per = has2 ? 16 * 4 + 8 : 16 * 3 + 8;
-    return chunks * per + 8LL * nrows + 32;
+// Items of a row part with n synapses.
+__host__ __device__ inline int part_items(int n, int K) { return (n + 4 * K - 1) / (4 * K); }
+
+// Shared-memory bytes of the items of one block of rows.
+__host__ __device__ inline long long items_smem_bytes(int n1, int n2, int K, int nrows, bool has2) {
+    const long long c1 = (long long)K * n1, c2 = (long long)K * n2;
+    long long b = (c1 + c2) * (16 * 3 + 8) + (has2 ? 16 * c2 : 0);
+    b += 8LL * (n1 + n2);          // partials
+    b += 8LL * (nrows + 1) + 64;   // row item offsets + alignment slack
+    return b;
 }
 
-// Number of chunks a row needs (first + second order parts padded to 4).
-__host__ __device__ inline int row_chunks(int n1, int n2) { return (n1 + 3) / 4 + (n2 + 3) / 4; }
-
-// Carve the chunk arrays out of `base` (16-aligned) for `chunks` chunks.
-__device__ inline RowChunks carve_rows(unsigned char *base, int nrows, int chunks, bool has2) {
-    RowChunks rc;
-    rc.nrows = nrows;
+__device__ inline Items carve_items(unsigned char *base, int nrows, int K, int n1, int n2, bool has2) {
+    Items it;
+    it.nrows = nrows;
+    it.K = K;
+    it.n1 = n1;
+    it.n2 = n2;
+    const long long c = (long long)K * (n1 + n2);
     unsigned char *p = base;
-    rc.r = (float4 *)p;
-    p += 16LL * chunks;
-    rc.w = (float4 *)p;
-    p += 16LL * chunks;
-    rc.we = (float4 *)p;
-    p += 16LL * chunks;
-    rc.s = has2 ? (float4 *)p : nullptr;
-    if (has2) p += 16LL * chunks;
-    rc.id = (ushort4 *)p;
-    p += 8LL * chunks;
-    rc.cb = (int *)p;
+    it.r = (float4 *)p;
+    p += 16 * c;
+    it.w = (float4 *)p;
+    p += 16 * c;
+    it.we = (float4 *)p;
+    p += 16 * c;
+    it.s = has2 ? (float4 *)p - (long long)K * n1 : nullptr;  // indexed like the others; list 2 only
+    if (has2) p += 16LL * K * n2;
+    it.id = (ushort4 *)p;
+    p += 8 * c;
+    it.pa = (float *)p;
+    p += 4LL * (n1 + n2);
+    it.pb = (float *)p;
+    p += 4LL * (n1 + n2);
+    it.ib1 = (int *)p;
     p += 4LL * (nrows + 1);
-    rc.cm = (int *)p;
-    return rc;
+    it.ib2 = (int *)p;
+    return it;
 }
 
 // Block-wide exclusive prefix sum of cnt[0..n) into out[0..n] (out[n] = total),
@@ -66,14 +80,14 @@ __device__ inline void block_scan(const int *cnt, int *out, int n) {
         int carry = 0;
         for (int base = 0; base < n; base += 32) {
             const int i = base + lane;
-            const int v = i < n ? cnt[i] : 0;
-            int x = v;
+            const int x0 = i < n ? cnt[i] : 0;
+            int x = x0;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, x, o);
                 if (lane >= o) x += y;
             }
-            if (i < n) out[i] = carry + x - v;
+            if (i < n) out[i] = carry + x - x0;
             carry += __shfl_sync(0xffffffffu, x, 31);
         }
         if (lane == 0) out[n] = carry;
@@ -81,80 +95,90 @@ __device__ inline void block_scan(const int *cnt, int *out, int n) {
     __syncthreads();
 }
 
-// Fill the chunk layout for rows [row0, row0 + nrows) of a network from the
-// global CSR arrays (synapse k of the network at offset k - sbase).  `tmp`
-// is scratch shared memory of nrows + 1 ints.  `stab` is the synapse-type
-// table (kind at SP_KIND, E at SP_E).
+// Slot of the m-th synapse of a row part that starts at item `ib` of a list
+// with n items (chunk index * 4 + lane within the chunk).
+__device__ __forceinline__ long long item_slot(int ib, int m, int K, int n, int base_chunk) {
+    const int t = ib + m / (4 * K);
+    const int j = (m % (4 * K)) >> 2;
+    return ((long long)base_chunk + (long long)j * n + t) * 4 + (m & 3);
+}
+
+__device__ __forceinline__ bool second_order(const float *stab, uint32_t code) {
+    return stab[(code >> 24) * 9 + SP_KIND] != 0.0f;
+}
+
+// Fill the items of rows [row0, row0 + nrows) of a network from the global
+// CSR arrays (synapse k of the network at offset k - sbase; rows of the
+// network start at global row row_g0).  tmp: shared scratch of 2 (nrows + 1)
+// ints.  stab: synapse-type table.
 template <bool HAS2>
-__device__ void load_rows(RowChunks &rc, const NetView &v, long long row_g0, long long sbase, int row0,
-                          const float *gr, const float *gs, const float *gw, const uint32_t *gcode,
-                          const float *stab, int *tmp) {
-    const int tid = threadIdx.x, nthr = blockDim.x, nrows = rc.nrows;
-    // per-row counts of first/second-order synapses
+__device__ void load_items(Items &it, const NetView &v, long long row_g0, long long sbase, int row0,
+                           const float *gr, const float *gs, const float *gw, const uint32_t *gcode,
+                           const float *stab, int *tmp) {
+    const int tid = threadIdx.x, nthr = blockDim.x, nrows = it.nrows, K = it.K;
+    int *c1 = tmp, *c2 = tmp + nrows + 1;
     for (int i = tid; i < nrows; i += nthr) {
         const long long k0 = v.row_ptr[row_g0 + row0 + i] - sbase, k1 = v.row_ptr[row_g0 + row0 + i + 1] - sbase;
         int n2 = 0;
         if (HAS2)
-            for (long long k = k0; k < k1; ++k) n2 += stab[(gcode[k] >> 24) * 9 + SP_KIND] != 0.0f;
-        const int n1 = (int)(k1 - k0) - n2;
-        tmp[i] = row_chunks(n1, n2);
-        rc.cm[i] = (n1 + 3) / 4;  // first-order chunk count, offset fixed below
+            for (long long k = k0; k < k1; ++k) n2 += second_order(stab, gcode[k]);
+        c1[i] = part_items((int)(k1 - k0) - n2, K);
+        c2[i] = part_items(n2, K);
     }
     __syncthreads();
-    block_scan(tmp, rc.cb, nrows);
-    const int chunks = rc.cb[nrows];
-    for (int c = tid; c < chunks; c += nthr) {
+    block_scan(c1, it.ib1, nrows);
+    block_scan(c2, it.ib2, nrows);
+    const long long chunks = (long long)K * (it.n1 + it.n2);
+    for (long long c = tid; c < chunks; c += nthr) {
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        rc.r[c] = z;
-        rc.w[c] = z;
-        rc.we[c] = z;
-        if (HAS2) rc.s[c] = z;
-        rc.id[c] = make_ushort4(0, 0, 0, 0);
+        it.r[c] = z;
+        it.w[c] = z;
+        it.we[c] = z;
+        if (HAS2 && c >= (long long)K * it.n1) it.s[c] = z;
+        it.id[c] = make_ushort4(0, 0, 0, 0);
     }
-    for (int i = tid; i < nrows; i += nthr) rc.cm[i] += rc.cb[i];
     __syncthreads();
+    float *R = (float *)it.r, *W = (float *)it.w, *WE = (float *)it.we, *Sg = (float *)it.s;
+    unsigned short *ID = (unsigned short *)it.id;
     for (int i = tid; i < nrows; i += nthr) {
         const long long k0 = v.row_ptr[row_g0 + row0 + i] - sbase, k1 = v.row_ptr[row_g0 + row0 + i + 1] - sbase;
-        int p1 = rc.cb[i] * 4, p2 = rc.cm[i] * 4;
-        float *R = (float *)rc.r, *W = (float *)rc.w, *WE = (float *)rc.we, *Sg = (float *)rc.s;
-        unsigned short *ID = (unsigned short *)rc.id;
+        int m1 = 0, m2 = 0;
         for (long long k = k0; k < k1; ++k) {
             const uint32_t code = gcode[k];
-            const int tau = (int)(code >> 24);
-            const bool second = HAS2 && stab[tau * 9 + SP_KIND] != 0.0f;
-            const int p = second ? p2++ : p1++;
+            const bool sec = HAS2 && second_order(stab, code);
+            const long long p = sec ? item_slot(it.ib2[i], m2++, K, it.n2, K * it.n1)
+                                    : item_slot(it.ib1[i], m1++, K, it.n1, 0);
             const float w = gw[k];
             R[p] = gr[k];
             W[p] = w;
-            WE[p] = w * stab[tau * 9 + SP_E];
+            WE[p] = w * stab[(code >> 24) * 9 + SP_E];
             ID[p] = (unsigned short)(code & 0xFFFFFFu);
-            if (HAS2) Sg[p] = second ? gs[k] : 0.0f;
+            if (HAS2 && sec) Sg[p] = gs[k];
         }
     }
     __syncthreads();
 }
 
 // Write the owned synapses back to the global CSR arrays, applying the last
-// step's gate map (fin1: r-map, fin2: s-map), in the same slot order as
-// load_rows.  fin tables are indexed by the coefficient index.
+// step's gate map (fin.r: r-map, fin.s: s-map, by coefficient index).
 template <bool HAS2, class Fin>
-__device__ void store_rows(const RowChunks &rc, const NetView &v, long long row_g0, long long sbase, int row0,
-                           float *gr, float *gs, const uint32_t *gcode, const float *stab, const Fin &fin) {
-    const int tid = threadIdx.x, nthr = blockDim.x, nrows = rc.nrows;
-    for (int i = tid; i < nrows; i += nthr) {
+__device__ void store_items(const Items &it, const NetView &v, long long row_g0, long long sbase, int row0,
+                            float *gr, float *gs, const uint32_t *gcode, const float *stab, const Fin &fin) {
+    const int tid = threadIdx.x, nthr = blockDim.x, K = it.K;
+    const float *R = (const float *)it.r, *Sg = (const float *)it.s;
+    for (int i = tid; i < it.nrows; i += nthr) {
         const long long k0 = v.row_ptr[row_g0 + row0 + i] - sbase, k1 = v.row_ptr[row_g0 + row0 + i + 1] - sbase;
-        int p1 = rc.cb[i] * 4, p2 = rc.cm[i] * 4;
-        const float *R = (const float *)rc.r, *Sg = (const float *)rc.s;
+        int m1 = 0, m2 = 0;
         for (long long k = k0; k < k1; ++k) {
             const uint32_t code = gcode[k];
-            const int tau = (int)(code >> 24);
             const int ci = (int)(code & 0xFFFFFFu);
-            const bool second = HAS2 && stab[tau * 9 + SP_KIND] != 0.0f;
-            const int p = second ? p2++ : p1++;
+            const bool sec = HAS2 && second_order(stab, code);
+            const long long p = sec ? item_slot(it.ib2[i], m2++, K, it.n2, K * it.n1)
+                                    : item_slot(it.ib1[i], m1++, K, it.n1, 0);
             const float r0 = R[p];
             const float2 F = fin.r(ci);
             gr[k] = fmaf(F.y, r0, F.x);
-            if (HAS2 && second) {
+            if (HAS2 && sec) {
                 const float4 F2 = fin.s(ci);
                 gs[k] = fmaf(F2.z, Sg[p], fmaf(F2.y, r0, F2.x));
             }
@@ -163,8 +187,8 @@ __device__ void store_rows(const RowChunks &rc, const NetView &v, long long row_
 }
 
 // One synapse of the current stage: gate value from the affine map, then
-// accumulate A += w G, B += wE G.  ST == 0 applies the previous step's final
-// map and stores the new step-start gate.
+// accumulate A += w G, B += wE G.  At the step's first stage the previous
+// step's final map is applied and the new step-start gate stored.
 template <bool FIRST_STAGE>
 __device__ __forceinline__ void syn1(float &r, float w, float we, float2 F, float &A, float &B) {
     const float g = fmaf(F.y, r, F.x);
@@ -188,55 +212,65 @@ __device__ __forceinline__ void syn2(float &r, float &s, float w, float we, floa
     B = fmaf(we, g, B);
 }
 
-// S-phase over the owned rows: lanes of a G-lane group stride the row's
-// chunks; row sums go to out(row, value).  Coef supplies r(ci) (float2
-// affine r-map of this stage) and s(ci) (float4 s-map, w = Kd).
-template <int ST, bool HAS2, class Coef, class Out>
-__device__ __forceinline__ void sphase(const RowChunks &rc, const float *Vrow, const Coef &cf, int G,
-                                       const Out &out) {
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int ngroups = nthr / G, gid = tid / G, gl = tid % G;
-    const int nrows = rc.nrows;
-    for (int base = 0; base < nrows; base += ngroups) {
-        const int row = base + gid;
+// S-phase: every item's partial sums (A, B) at stage ST.  Coef supplies
+// r(ci) (float2 r-map) and s(ci) (float4 s-map, w = Kd).
+template <int ST, bool HAS2, class Coef>
+__device__ __forceinline__ void sphase(const Items &it, const Coef &cf) {
+    const int tid = threadIdx.x, nthr = blockDim.x, K = it.K, n1 = it.n1;
+    for (int t = tid; t < n1; t += nthr) {
         float A = 0.0f, B = 0.0f;
-        if (row < nrows) {
-            const int c0 = rc.cb[row], cmid = rc.cm[row];
-            for (int c = c0 + gl; c < cmid; c += G) {
-                float4 r = rc.r[c];
-                const float4 w = rc.w[c], we = rc.we[c];
-                const ushort4 id = rc.id[c];
-                syn1<ST == 0>(r.x, w.x, we.x, cf.r(id.x), A, B);
-                syn1<ST == 0>(r.y, w.y, we.y, cf.r(id.y), A, B);
-                syn1<ST == 0>(r.z, w.z, we.z, cf.r(id.z), A, B);
-                syn1<ST == 0>(r.w, w.w, we.w, cf.r(id.w), A, B);
-                if (ST == 0) rc.r[c] = r;
-            }
-            if (HAS2) {
-                const int c1 = rc.cb[row + 1];
-                for (int c = cmid + gl; c < c1; c += G) {
-                    float4 r = rc.r[c], s = rc.s[c];
-                    const float4 w = rc.w[c], we = rc.we[c];
-                    const ushort4 id = rc.id[c];
-                    syn2<ST == 0>(r.x, s.x, w.x, we.x, cf.r(id.x), cf.s(id.x), A, B);
-                    syn2<ST == 0>(r.y, s.y, w.y, we.y, cf.r(id.y), cf.s(id.y), A, B);
-                    syn2<ST == 0>(r.z, s.z, w.z, we.z, cf.r(id.z), cf.s(id.z), A, B);
-                    syn2<ST == 0>(r.w, s.w, w.w, we.w, cf.r(id.w), cf.s(id.w), A, B);
-                    if (ST == 0) {
-                        rc.r[c] = r;
-                        rc.s[c] = s;
-                    }
+        for (int j = 0; j < K; ++j) {
+            const int c = j * n1 + t;
+            float4 r = it.r[c];
+            const float4 w = it.w[c], we = it.we[c];
+            const ushort4 id = it.id[c];
+            syn1<ST == 0>(r.x, w.x, we.x, cf.r(id.x), A, B);
+            syn1<ST == 0>(r.y, w.y, we.y, cf.r(id.y), A, B);
+            syn1<ST == 0>(r.z, w.z, we.z, cf.r(id.z), A, B);
+            syn1<ST == 0>(r.w, w.w, we.w, cf.r(id.w), A, B);
+            if (ST == 0) it.r[c] = r;
+        }
+        it.pa[t] = A;
+        it.pb[t] = B;
+    }
+    if (HAS2) {
+        const int n2 = it.n2, base = K * n1;
+        for (int t = tid; t < n2; t += nthr) {
+            float A = 0.0f, B = 0.0f;
+            for (int j = 0; j < K; ++j) {
+                const int c = base + j * n2 + t;
+                float4 r = it.r[c], s = it.s[c];
+                const float4 w = it.w[c], we = it.we[c];
+                const ushort4 id = it.id[c];
+                syn2<ST == 0>(r.x, s.x, w.x, we.x, cf.r(id.x), cf.s(id.x), A, B);
+                syn2<ST == 0>(r.y, s.y, w.y, we.y, cf.r(id.y), cf.s(id.y), A, B);
+                syn2<ST == 0>(r.z, s.z, w.z, we.z, cf.r(id.z), cf.s(id.z), A, B);
+                syn2<ST == 0>(r.w, s.w, w.w, we.w, cf.r(id.w), cf.s(id.w), A, B);
+                if (ST == 0) {
+                    it.r[c] = r;
+                    it.s[c] = s;
                 }
             }
+            it.pa[n1 + t] = A;
+            it.pb[n1 + t] = B;
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-            if (off < G) {
-                A += __shfl_xor_sync(0xffffffffu, A, off);
-                B += __shfl_xor_sync(0xffffffffu, B, off);
-            }
-        if (row < nrows && gl == 0) out(row, fmaf(Vrow[row], A, -B));
     }
+}
+
+// Synaptic current of owned row i from its items' partials (fixed order).
+template <bool HAS2>
+__device__ __forceinline__ float row_current(const Items &it, int i, float V) {
+    float A = 0.0f, B = 0.0f;
+    for (int t = it.ib1[i]; t < it.ib1[i + 1]; ++t) {
+        A += it.pa[t];
+        B += it.pb[t];
+    }
+    if (HAS2)
+        for (int t = it.ib2[i]; t < it.ib2[i + 1]; ++t) {
+            A += it.pa[it.n1 + t];
+            B += it.pb[it.n1 + t];
+        }
+    return fmaf(V, A, -B);
 }
 
 // Gate-map update of one (presynaptic neuron j, synapse type tau) pair at
@@ -286,31 +320,32 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, float dt, 
     }
 }
 
-// Right-hand side and stage update of neuron i at stage ST.  y0/acc/ys hold
-// [4][N] (ys rows 1..3 = stage m, h, n); V is the stage potential; returns
-// the potential of the next stage (ST < 3) or of the new step start.
+// Right-hand side and stage update of owned neuron i at stage ST.
+// y0/acc/ys hold [4][n] (ys rows 1..3 = stage m, h, n); V is the stage
+// potential; returns the potential of the next stage (ST < 3) or of the new
+// step start.
 template <int ST>
-__device__ __forceinline__ float neuron_update(int i, int N, float V, float *y0, float *acc, float *ys,
+__device__ __forceinline__ float neuron_update(int i, int n, float V, float *y0, float *acc, float *ys,
                                                const float *prm, float iext, float isyn, float dt) {
     constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
     const float cnext = (ST == 2) ? dt : 0.5f * dt;
     const float dt6 = dt * (1.0f / 6.0f);
-    const float m = ys[N + i], h = ys[2 * N + i], n = ys[3 * N + i];
+    const float m = ys[n + i], h = ys[2 * n + i], nn = ys[3 * n + i];
     const Rates q = hh_rates(V);
-    const float m3h = m * m * m * h, n2 = n * n, n4 = n2 * n2;
-    const float iion = prm[NP_GNA * N + i] * m3h * (V - prm[NP_ENA * N + i]) +
-                       prm[NP_GK * N + i] * n4 * (V - prm[NP_EK * N + i]) +
-                       prm[NP_GL * N + i] * (V - prm[NP_EL * N + i]) +
-                       prm[NP_GKL * N + i] * (V - prm[NP_EKL * N + i]);
+    const float m3h = m * m * m * h, n2 = nn * nn, n4 = n2 * n2;
+    const float iion = prm[NP_GNA * n + i] * m3h * (V - prm[NP_ENA * n + i]) +
+                       prm[NP_GK * n + i] * n4 * (V - prm[NP_EK * n + i]) +
+                       prm[NP_GL * n + i] * (V - prm[NP_EL * n + i]) +
+                       prm[NP_GKL * n + i] * (V - prm[NP_EKL * n + i]);
     float d[4];
-    d[0] = (iext - iion - isyn) * prm[NP_C * N + i];  // prm row 0 holds 1/C
+    d[0] = (iext - iion - isyn) * prm[NP_C * n + i];  // prm row 0 holds 1/C
     d[1] = q.am * (1.0f - m) - q.bm * m;
     d[2] = q.ah * (1.0f - h) - q.bh * h;
-    d[3] = q.an * (1.0f - n) - q.bn * n;
+    d[3] = q.an * (1.0f - nn) - q.bn * nn;
     float vnext = 0.0f;
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
-        const int ix = x * N + i;
+        const int ix = x * n + i;
         const float ac = (ST == 0) ? d[x] : fmaf(WGT, d[x], acc[ix]);
         float yn;
         if (ST < 3) {

@@ -45,13 +45,13 @@ class NetworkDesc(C.Structure):
                 ("noise_seed", C.c_uint64), ("noise_thresh", C.c_uint32),
                 ("noise_amp", C.c_float), ("dt", C.c_float), ("init_state", C.c_void_p),
                 ("rec_stride", C.c_int32), ("rec_capacity", C.c_int64), ("mode", C.c_int32),
-                ("block_threads", C.c_int32), ("row_group", C.c_int32), ("device", C.c_int32)]
+                ("block_threads", C.c_int32), ("item_chunks", C.c_int32), ("device", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [("n_nets", C.c_int32), ("n_neurons", C.c_int64), ("n_synapses", C.c_int64),
                 ("steps_done", C.c_int64), ("rec_frames", C.c_int64), ("mode", C.c_int32),
-                ("block_threads", C.c_int32), ("row_group", C.c_int32), ("grid_ctas", C.c_int32),
+                ("block_threads", C.c_int32), ("item_chunks", C.c_int32), ("grid_ctas", C.c_int32),
                 ("smem_bytes", C.c_int32), ("n_single_cta_nets", C.c_int32),
                 ("n_cluster_nets", C.c_int32), ("n_launch_classes", C.c_int32),
                 ("kernel_launches", C.c_int32)]
@@ -120,7 +120,7 @@ class Network:
     """A batch of networks resident on one GPU (``psst_create_network``)."""
 
     def __init__(self, spec, init_state=None, rec_stride: int = 0, rec_capacity: int = 0,
-                 mode: int = MODE_AUTO, block_threads: int = 0, row_group: int = 0,
+                 mode: int = MODE_AUTO, block_threads: int = 0, item_chunks: int = 0,
                  device: int | None = None):
         lib = load()
         keep = dict(
@@ -145,7 +145,7 @@ class Network:
             noise_seed=int(spec.noise_seed), noise_thresh=int(spec.noise_thresh),
             noise_amp=float(spec.noise_amp), dt=float(spec.dt), init_state=ptr("init"),
             rec_stride=int(rec_stride), rec_capacity=int(rec_capacity), mode=int(mode),
-            block_threads=int(block_threads), row_group=int(row_group), device=int(device))
+            block_threads=int(block_threads), item_chunks=int(item_chunks), device=int(device))
         h = C.c_void_p()
         _check(lib.psst_create_network(C.byref(d), C.byref(h)))
         self._h = h

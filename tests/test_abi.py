@@ -79,7 +79,7 @@ def _desc(spec, **kw):
     ("n_syn_types", 9, b"n_syn_types"),
     ("noise_thresh", (1 << 24) + 1, b"noise_thresh"),
     ("block_threads", 100, b"block_threads"),
-    ("row_group", 3, b"row_group"),
+    ("item_chunks", 65, b"item_chunks"),
     ("rec_stride", -1, b"rec_stride"),
 ])
 def test_invalid_descriptor_rejected_on_host(lib, field, value, needle):

@@ -52,7 +52,7 @@ def test_grid_equals_cta_mode_bitwise():
     y0 = oracle.rest_state(spec).astype(np.float32)
     out = []
     for mode in (psst.MODE_CTA, psst.MODE_GRID):
-        with _net(spec, init_state=y0, mode=mode, block_threads=256, row_group=16,
+        with _net(spec, init_state=y0, mode=mode, block_threads=256, item_chunks=2,
                   rec_stride=5, rec_capacity=100) as net:
             net.set_step(9950)
             net.integrate(300)

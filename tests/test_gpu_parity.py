@@ -136,7 +136,7 @@ def test_batched_equals_alone_bitwise():
     for blk in range(2):
         parts += [y[4 * n + blk * s:4 * n + (blk + 1) * s] for y, n, s in zip(y0s, Ns, Ss)]
     yb = np.concatenate(parts)
-    kw = dict(block_threads=256, row_group=8)
+    kw = dict(block_threads=256, item_chunks=3)
     with _net(both, init_state=yb, **kw) as nb:
         nb.integrate(500)
         nb.status()
@@ -177,13 +177,13 @@ def test_ragged_batch_single_step():
         assert step_error(got, y64, N, S) <= STEP_TOL
 
 
-@pytest.mark.parametrize("block,G", [(32, 32), (128, 4), (1024, 16), (64, 1)])
+@pytest.mark.parametrize("block,G", [(32, 1), (128, 4), (1024, 16), (64, 64), (256, 7)])
 def test_launch_shapes(block, G):
     spec = ng.antennal_lobe(seed=5)
     N, S = spec.n_neurons, spec.n_synapses
     (step, y32), = _states_along_oracle(spec, [10050], step0=9990)
     y64, _ = oracle.integrate(spec, y32.astype(np.float64), 1, step0=step)
-    got = _gpu_one_step(spec, y32, step, block_threads=block, row_group=G)
+    got = _gpu_one_step(spec, y32, step, block_threads=block, item_chunks=G)
     assert step_error(got, y64, N, S) <= STEP_TOL
 
 
