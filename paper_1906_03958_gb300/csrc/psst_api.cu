@@ -336,7 +336,8 @@ int setup_grid(psst_net *h, const psst_network_desc *d, const SmemCaps &caps, bo
     h->K = K;
     h->smem = need;
     int per_sm = 0;
-    e = psst::grid_occupancy(h->block, need, &per_sm);
+    // the kernel attribute is an upper bound shared by every handle's launches
+    e = psst::grid_occupancy(h->block, caps.max_dyn, &per_sm);
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid occupancy");
     if (per_sm < 1) return fail(PSST_ERR_UNSUPPORTED, "grid mode: a CTA of %d threads does not fit an SM", h->block);
     h->grid = parts;
