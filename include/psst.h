@@ -183,6 +183,69 @@ const char *psst_error_string(int code);
 /* Message of the last failing call on this thread ("" if none). */
 const char *psst_last_error(void);
 
+/*
+ * Integration without device allocation.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc themselves or let a library do it -- code that
+ * must keep every device byte inside an allocator it does not control (a
+ * framework's memory pool, a memory-capped or sandboxed process), or code
+ * that only receives buffers from its caller.  They pass their own device
+ * arrays in the layout below, and the call allocates nothing: the grid-wide
+ * kernel's extra memory (gate-map tables, barrier words, per-CTA plan) is
+ * one fixed array of PSST_NOALLOC_SCRATCH_BYTES in device global memory,
+ * compiled into the library.  Every GPU that loads the library holds that
+ * array until the process exits.
+ *
+ * psst_integrate_grid_noalloc advances the single network *net by n_steps
+ * RK4 steps starting at global step index step0, exactly like
+ * psst_integrate in PSST_MODE_GRID (same kernel; with the same item_chunks
+ * the results are bitwise identical).  It runs on the current device and
+ * `stream`.  Its first call on a device looks up that device's address of
+ * the fixed array (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Each call synchronises `stream` once, after planning and
+ * before the integration launch, and otherwise returns without waiting.
+ * Every call uses the same array and finds it as the last call left it; the
+ * call clears what must start at zero.  Two calls whose GPU work overlaps
+ * (different streams without ordering, or different threads) race on the
+ * array and give wrong results.
+ *
+ * Limits: n_neurons * n_syn_types < 65536 (the gate-map tables then always
+ * fit the array); larger networks return PSST_ERR_UNSUPPORTED, as does a
+ * network whose per-CTA share does not fit shared memory.  Errors are
+ * reported by return code only (psst_last_error is not updated):
+ * INVALID_ARG for a NULL pointer or a bad size/field, UNSUPPORTED for the
+ * limits above, CUDA for a failing runtime call.  Device-side failures
+ * (TIMEOUT, NONFINITE) are written to *err (the caller zeroes it).
+ */
+#define PSST_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+typedef struct {
+    int64_t n_neurons, n_synapses;
+    int32_t n_syn_types;            /* 1..PSST_MAX_SYN_TYPES */
+    int32_t item_chunks;            /* 4-synapse chunks per work item, 0 = chosen by the call */
+    const int64_t *row_ptr;         /* device [N+1], CSR by postsynaptic neuron */
+    const uint32_t *syn_code;       /* device [S]: (syn_type << 24) | (pre * n_syn_types + syn_type) */
+    const float *weight;            /* device [S] */
+    const int32_t *neuron_type;     /* device [N] */
+    const float *neuron_params;     /* device [n_neuron_types * PSST_NEURON_NPARAM] */
+    const float *syn_params;        /* device [n_syn_types * PSST_SYN_NPARAM] */
+    const float *i_const;           /* device [N] */
+    const float *pulse_amp;         /* device [N] or NULL */
+    int64_t pulse_on, pulse_off;    /* pulse window in steps */
+    uint64_t noise_seed;
+    uint32_t noise_thresh;
+    float noise_amp;
+    float dt;
+    float *state;                   /* device [4N+2S], read and overwritten */
+    float *rec;                     /* device [rec_capacity][N] or NULL */
+    int32_t rec_stride;
+    int64_t rec_capacity;
+    int *err;                       /* device error word, written on device failure */
+} psst_device_network;
+
+int psst_integrate_grid_noalloc(const psst_device_network *net, int64_t step0, int64_t n_steps, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

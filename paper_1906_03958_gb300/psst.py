@@ -26,7 +26,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOU
 EXPORTED = ("psst_create_network", "psst_integrate", "psst_status", "psst_get_state",
             "psst_set_state", "psst_set_step", "psst_read_record", "psst_query",
             "psst_destroy_network", "psst_error_string", "psst_last_error",
-            "psst_set_barrier_timeout")
+            "psst_set_barrier_timeout", "psst_integrate_grid_noalloc")
 
 
 class PsstError(RuntimeError):
@@ -46,6 +46,18 @@ class NetworkDesc(C.Structure):
                 ("noise_amp", C.c_float), ("dt", C.c_float), ("init_state", C.c_void_p),
                 ("rec_stride", C.c_int32), ("rec_capacity", C.c_int64), ("mode", C.c_int32),
                 ("block_threads", C.c_int32), ("item_chunks", C.c_int32), ("device", C.c_int32)]
+
+
+class DeviceNetwork(C.Structure):
+    """psst_device_network: one network in caller-owned device arrays."""
+    _fields_ = [("n_neurons", C.c_int64), ("n_synapses", C.c_int64), ("n_syn_types", C.c_int32),
+                ("item_chunks", C.c_int32), ("row_ptr", C.c_void_p), ("syn_code", C.c_void_p),
+                ("weight", C.c_void_p), ("neuron_type", C.c_void_p), ("neuron_params", C.c_void_p),
+                ("syn_params", C.c_void_p), ("i_const", C.c_void_p), ("pulse_amp", C.c_void_p),
+                ("pulse_on", C.c_int64), ("pulse_off", C.c_int64), ("noise_seed", C.c_uint64),
+                ("noise_thresh", C.c_uint32), ("noise_amp", C.c_float), ("dt", C.c_float),
+                ("state", C.c_void_p), ("rec", C.c_void_p), ("rec_stride", C.c_int32),
+                ("rec_capacity", C.c_int64), ("err", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -85,6 +97,7 @@ def load(build_if_missing: bool = False):
         lib.psst_set_state.argtypes = [P, P, SZ, I32, P]
         lib.psst_set_step.argtypes = [P, I64]
         lib.psst_set_barrier_timeout.argtypes = [P, I64]
+        lib.psst_integrate_grid_noalloc.argtypes = [C.POINTER(DeviceNetwork), I64, I64, P]
         lib.psst_read_record.argtypes = [P, P, SZ, C.POINTER(C.c_int64), I32, P]
         lib.psst_query.argtypes = [P, C.POINTER(Info)]
         lib.psst_destroy_network.argtypes = [P]
@@ -110,6 +123,14 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def integrate_grid_noalloc(net: DeviceNetwork, step0: int, n_steps: int, stream=None):
+    """psst_integrate_grid_noalloc: integrate a network held in the
+    caller's device arrays without any device allocation."""
+    rc = load().psst_integrate_grid_noalloc(C.byref(net), int(step0), int(n_steps), _stream_handle(stream))
+    if rc != OK:
+        raise PsstError(rc, "psst_integrate_grid_noalloc failed (see psst.h for the cases of this code)")
 
 
 def _arr(a, dtype):
