@@ -6,7 +6,8 @@ float64, built with gcc) through ctypes and shares no code with the CUDA
 library: it reads the same seeded input arrays (any object with the
 ``NetworkSpec`` attributes) and widens them to float64.
 
-Pinned functions and their pins live in ``tests/test_oracle_pins.py``.  The
+Pinned functions and their pins live in ``tests/test_oracle_pins.py`` and
+``tests/test_oracle_adjoint.py``.  The
 Philox generator is pinned only statistically (no published known-answer
 vector is available here): its parity with the published generator is
 unpinned; its parity with the CUDA side is bit-exact by test.
@@ -68,6 +69,13 @@ def lib():
             _lib.orc_noise_event.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int64]
             _lib.orc_rates.argtypes = [C.c_double, P]
             _lib.orc_steady_gates.argtypes = [C.c_double, P]
+            _lib.orc_vjp.argtypes = [C.POINTER(_Net), P, P, P, P, P]
+            _lib.orc_linear_adjoint.restype = C.c_int
+            _lib.orc_linear_adjoint.argtypes = [C.c_int64, P, P, C.c_double, C.c_int64, P]
+            _lib.orc_adjoint.restype = C.c_int
+            _lib.orc_adjoint.argtypes = [C.POINTER(_Net), P, C.c_int64, C.c_int64, C.c_int64, P, P, P, P,
+                                         C.c_int64]
+            _lib.orc_rates_deriv.argtypes = [C.c_double, P]
             _lib.orc_transmitter.restype = C.c_double
             _lib.orc_transmitter.argtypes = [C.c_double, C.c_double, C.c_double]
         return _lib
@@ -156,6 +164,54 @@ def linear_integrate(A, y0, h: float, nsteps: int, order: int = 4) -> np.ndarray
     if lib().orc_linear_integrate(len(y), _ptr(A), _ptr(y), float(h), int(nsteps), int(order)):
         raise MemoryError("oracle linear integrate")
     return y
+
+
+class _Grads(C.Structure):
+    _fields_ = [("gw", C.c_void_p), ("gnp", C.c_void_p)]
+
+
+def vjp(spec, y, v, step: int = 0):
+    """(J(y)^T v, dL/dw contribution, dL/dnparams contribution) at state y."""
+    net = as_net(spec)
+    y = np.ascontiguousarray(y, np.float64)
+    v = np.ascontiguousarray(v, np.float64)
+    iext = input_current(net, step)
+    u = np.zeros(net.dim, np.float64)
+    gw = np.zeros(net.S, np.float64)
+    gnp = np.zeros(net.nparams.size, np.float64)
+    g = _Grads(_ptr(gw), _ptr(gnp))
+    lib().orc_vjp(C.byref(net.c), _ptr(iext), _ptr(y), _ptr(v), _ptr(u), C.addressof(g))
+    return u, gw, gnp.reshape(-1, 9)
+
+
+def linear_adjoint(A, y0, h: float, nsteps: int, lam_T) -> np.ndarray:
+    A = np.ascontiguousarray(A, np.float64)
+    y0 = np.ascontiguousarray(y0, np.float64)
+    lam = np.array(lam_T, np.float64, copy=True)
+    if lib().orc_linear_adjoint(len(y0), _ptr(A), _ptr(y0), float(h), int(nsteps), _ptr(lam)):
+        raise MemoryError("oracle linear adjoint")
+    return lam
+
+
+def adjoint(spec, y0, nsteps: int, dLdV, rec_stride: int, step0: int = 0, ckpt: int = 100):
+    """Gradient of L = sum_f sum_i dLdV[f, i] V_i(frame f) over the RK4
+    trajectory; returns (dL/dy0, dL/dw, dL/dnparams[n_types, 9])."""
+    net = as_net(spec)
+    y0 = np.ascontiguousarray(y0, np.float64)
+    dLdV = np.ascontiguousarray(dLdV, np.float64)
+    gy = np.zeros(net.dim, np.float64)
+    gw = np.zeros(net.S, np.float64)
+    gnp = np.zeros(net.nparams.size, np.float64)
+    if lib().orc_adjoint(C.byref(net.c), _ptr(y0), int(step0), int(nsteps), int(rec_stride), _ptr(dLdV),
+                         _ptr(gy), _ptr(gw), _ptr(gnp), int(ckpt)):
+        raise MemoryError("oracle adjoint")
+    return gy, gw, gnp.reshape(-1, 9)
+
+
+def rates_deriv(V: float) -> np.ndarray:
+    out = np.zeros(6, np.float64)
+    lib().orc_rates_deriv(float(V), _ptr(out))
+    return out
 
 
 def philox(ctr, key) -> np.ndarray:

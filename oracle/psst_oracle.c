@@ -16,7 +16,12 @@
  *     dt and F the classic fourth-order Runge-Kutta map (Sec. "Brain
  *     simulations ...", RK4 paragraph) or forward Euler (Eq. euler);
  *   - the Philox4x32-10 counter-based generator of Salmon et al., SC'11,
- *     used for shot-noise input.
+ *     used for shot-noise input;
+ *   - the discrete adjoint (transpose) of the RK4 map over the full
+ *     per-synapse state, with the Jacobian-transpose products of the
+ *     right-hand side derived by hand, giving gradients of a voltage-trace
+ *     functional with respect to the initial state, the weights and the
+ *     neuron-type parameters (checkpointed every K steps, recomputed).
  *
  * The paper gives the HH model only by name and state vector; the rate
  * functions and constants are the textbook squid-axon set in the -65 mV
@@ -278,4 +283,272 @@ int64_t orc_integrate(const orc_net *net, double *y, int64_t step0, int64_t nste
     }
     free(work);
     return frames;
+}
+
+/* ------------------------------------------------ discrete adjoint of RK4 */
+
+/* d/du of u / (1 - exp(-u)); its limit at 0 is 1/2.  The Bernoulli series
+   1/2 + u/6 - u^3/180 + u^5/5040 is used for |u| < 1e-2, where the closed
+   form cancels. */
+static double ratio_u_deriv(double u)
+{
+    if (fabs(u) < 1e-2) {
+        double u2 = u * u;
+        return 0.5 + u / 6.0 - u * u2 / 180.0 + u * u2 * u2 / 5040.0;
+    }
+    double e = exp(-u), den = -expm1(-u);
+    return (den - u * e) / (den * den);
+}
+
+/* derivatives d/dV of alpha_m, beta_m, alpha_h, beta_h, alpha_n, beta_n */
+void orc_rates_deriv(double V, double out[6])
+{
+    double r[6];
+    orc_rates(V, r);
+    out[0] = 0.1 * ratio_u_deriv((V + 40.0) / 10.0);
+    out[1] = -r[1] / 18.0;
+    out[2] = -r[2] / 20.0;
+    out[3] = r[3] * (1.0 - r[3]) / 10.0;
+    out[4] = 0.01 * ratio_u_deriv((V + 55.0) / 10.0);
+    out[5] = -r[5] / 80.0;
+}
+
+/* Gradient accumulators of one adjoint run. */
+typedef struct {
+    double *gw;   /* [S] d/d weight */
+    double *gnp;  /* [n_ntypes * P_NCOL] d/d neuron-type parameters */
+} orc_grads;
+
+/* u = J(y)^T v for the network right-hand side at state y (input iext), and
+   params += (df/dtheta)^T v for the weights and the neuron-type parameters.
+   Hand-derived from orc_rhs, term by term. */
+void orc_vjp(const orc_net *net, const double *iext, const double *y, const double *v, double *u, orc_grads *g)
+{
+    const int64_t N = net->N, S = net->S;
+    const double *V = y, *m = y + N, *h = y + 2 * N, *n = y + 3 * N;
+    const double *r = y + 4 * N, *s = y + 4 * N + S;
+    const double *vV = v, *vm = v + N, *vh = v + 2 * N, *vn = v + 3 * N;
+    const double *vr = v + 4 * N, *vs = v + 4 * N + S;
+    double *uV = u, *um = u + N, *uh = u + 2 * N, *un = u + 3 * N;
+    double *ur = u + 4 * N, *us = u + 4 * N + S;
+
+    for (int64_t i = 0; i < 4 * N + 2 * S; ++i) u[i] = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        const double *p = net->nparams + (int64_t)net->ntype[i] * P_NCOL;
+        double *gp = g ? g->gnp + (int64_t)net->ntype[i] * P_NCOL : NULL;
+        const double q = vV[i] / p[P_C];  /* adjoint of dV/dt scaled by 1/C */
+        double a[6], da[6];
+        orc_rates(V[i], a);
+        orc_rates_deriv(V[i], da);
+        const double m3h = m[i] * m[i] * m[i] * h[i], n4 = n[i] * n[i] * n[i] * n[i];
+        /* synaptic terms of the row: current, its V-derivative, weights, gates */
+        double isyn = 0.0, gsum = 0.0;
+        for (int64_t k = net->row_ptr[i]; k < net->row_ptr[i + 1]; ++k) {
+            const double *sq = net->sparams + (int64_t)net->stype[k] * Q_NCOL;
+            const double E = sq[Q_E];
+            double G, dG;  /* gate and its derivative w.r.t. the variable it reads */
+            if (sq[Q_KIND] == 0.0) {
+                G = r[k];
+                dG = 1.0;
+                ur[k] += -q * net->w[k] * dG * (V[i] - E);
+            } else {
+                const double s4 = s[k] * s[k] * s[k] * s[k];
+                G = s4 / (s4 + sq[Q_KD]);
+                dG = 4.0 * s[k] * s[k] * s[k] * sq[Q_KD] / ((s4 + sq[Q_KD]) * (s4 + sq[Q_KD]));
+                us[k] += -q * net->w[k] * dG * (V[i] - E);
+            }
+            isyn += net->w[k] * G * (V[i] - E);
+            gsum += net->w[k] * G;
+            if (g) g->gw[k] += -q * G * (V[i] - E);
+        }
+        const double iion = p[P_GNA] * m3h * (V[i] - p[P_ENA]) + p[P_GK] * n4 * (V[i] - p[P_EK]) +
+                            p[P_GL] * (V[i] - p[P_EL]) + p[P_GKL] * (V[i] - p[P_EKL]);
+        const double diion = p[P_GNA] * m3h + p[P_GK] * n4 + p[P_GL] + p[P_GKL];
+        uV[i] += q * (-diion - gsum);
+        uV[i] += vm[i] * (da[0] * (1.0 - m[i]) - da[1] * m[i]);
+        uV[i] += vh[i] * (da[2] * (1.0 - h[i]) - da[3] * h[i]);
+        uV[i] += vn[i] * (da[4] * (1.0 - n[i]) - da[5] * n[i]);
+        um[i] += q * (-p[P_GNA] * 3.0 * m[i] * m[i] * h[i] * (V[i] - p[P_ENA])) - vm[i] * (a[0] + a[1]);
+        uh[i] += q * (-p[P_GNA] * m[i] * m[i] * m[i] * (V[i] - p[P_ENA])) - vh[i] * (a[2] + a[3]);
+        un[i] += q * (-p[P_GK] * 4.0 * n[i] * n[i] * n[i] * (V[i] - p[P_EK])) - vn[i] * (a[4] + a[5]);
+        if (gp) {
+            const double fV = (iext[i] - iion - isyn) / p[P_C];
+            gp[P_C] += -q * fV;
+            gp[P_GNA] += -q * m3h * (V[i] - p[P_ENA]);
+            gp[P_GK] += -q * n4 * (V[i] - p[P_EK]);
+            gp[P_GL] += -q * (V[i] - p[P_EL]);
+            gp[P_GKL] += -q * (V[i] - p[P_EKL]);
+            gp[P_ENA] += q * p[P_GNA] * m3h;
+            gp[P_EK] += q * p[P_GK] * n4;
+            gp[P_EL] += q * p[P_GL];
+            gp[P_EKL] += q * p[P_GKL];
+        }
+    }
+    /* gate equations: own-variable terms and the presynaptic voltage */
+    for (int64_t k = 0; k < S; ++k) {
+        const double *sq = net->sparams + (int64_t)net->stype[k] * Q_NCOL;
+        const int64_t j = net->pre[k];
+        const double T = orc_transmitter(V[j], sq[Q_VP], sq[Q_KP]);
+        const double dT = T * (1.0 - T) / sq[Q_KP];
+        ur[k] += -vr[k] * (sq[Q_A] * T + sq[Q_B]);
+        uV[j] += vr[k] * sq[Q_A] * dT * (1.0 - r[k]);
+        if (sq[Q_KIND] != 0.0) {
+            ur[k] += vs[k] * sq[Q_K3];
+            us[k] += -vs[k] * sq[Q_K4];
+        }
+    }
+}
+
+typedef void (*vjp_fn)(void *ctx, const double *y, const double *v, double *u);
+
+/* Reverse of one classic RK4 step from y_n (Hager 2000; Sandu 2006): on
+   entry lam holds the adjoint of y_{n+1}, on exit that of y_n.  With
+   k_s = f(Y_s), the stage adjoints are
+     kb4 = h/6 lam,           Yb4 = J(Y4)^T kb4
+     kb3 = h/3 lam + h Yb4,   Yb3 = J(Y3)^T kb3
+     kb2 = h/3 lam + h/2 Yb3, Yb2 = J(Y2)^T kb2
+     kb1 = h/6 lam + h/2 Yb2, Yb1 = J(Y1)^T kb1
+   and lam_n = lam + Yb1 + Yb2 + Yb3 + Yb4.  The vjp callback also adds the
+   parameter terms (df/dtheta)^T kb_s. */
+static void rk4_adjoint_step(int64_t d, double hstep, rhs_fn f, vjp_fn g, void *ctx, const double *y,
+                             double *lam, double *work)
+{
+    double *Y1 = work, *Y2 = work + d, *Y3 = work + 2 * d, *Y4 = work + 3 * d;
+    double *k = work + 4 * d, *kb = work + 5 * d, *Yb = work + 6 * d, *Ysum = work + 7 * d;
+    for (int64_t i = 0; i < d; ++i) Y1[i] = y[i];
+    f(ctx, Y1, k);
+    for (int64_t i = 0; i < d; ++i) Y2[i] = y[i] + 0.5 * hstep * k[i];
+    f(ctx, Y2, k);
+    for (int64_t i = 0; i < d; ++i) Y3[i] = y[i] + 0.5 * hstep * k[i];
+    f(ctx, Y3, k);
+    for (int64_t i = 0; i < d; ++i) Y4[i] = y[i] + hstep * k[i];
+
+    for (int64_t i = 0; i < d; ++i) kb[i] = hstep / 6.0 * lam[i];
+    g(ctx, Y4, kb, Yb);
+    for (int64_t i = 0; i < d; ++i) Ysum[i] = Yb[i];
+    for (int64_t i = 0; i < d; ++i) kb[i] = hstep / 3.0 * lam[i] + hstep * Yb[i];
+    g(ctx, Y3, kb, Yb);
+    for (int64_t i = 0; i < d; ++i) Ysum[i] += Yb[i];
+    for (int64_t i = 0; i < d; ++i) kb[i] = hstep / 3.0 * lam[i] + 0.5 * hstep * Yb[i];
+    g(ctx, Y2, kb, Yb);
+    for (int64_t i = 0; i < d; ++i) Ysum[i] += Yb[i];
+    for (int64_t i = 0; i < d; ++i) kb[i] = hstep / 6.0 * lam[i] + 0.5 * hstep * Yb[i];
+    g(ctx, Y1, kb, Yb);
+    for (int64_t i = 0; i < d; ++i) lam[i] += Ysum[i] + Yb[i];
+}
+
+static void lin_vjp(void *c, const double *y, const double *v, double *u)
+{
+    const lin_ctx *L = (const lin_ctx *)c;
+    (void)y;
+    for (int64_t j = 0; j < L->d; ++j) {
+        double acc = 0.0;
+        for (int64_t i = 0; i < L->d; ++i) acc += L->A[i * L->d + j] * v[i];
+        u[j] = acc;
+    }
+}
+
+/* Adjoint of nsteps RK4 steps of dy/dt = A y: lam (adjoint of y at the end)
+   is carried back to the adjoint of the initial state. */
+int orc_linear_adjoint(int64_t d, const double *A, const double *y0, double h, int64_t nsteps, double *lam)
+{
+    double *traj = (double *)malloc(sizeof(double) * (size_t)d * (size_t)(nsteps + 1));
+    double *work = (double *)malloc(sizeof(double) * 8 * (size_t)d);
+    if (!traj || !work) { free(traj); free(work); return -1; }
+    lin_ctx c = {d, A};
+    memcpy(traj, y0, sizeof(double) * (size_t)d);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        memcpy(traj + (k + 1) * d, traj + k * d, sizeof(double) * (size_t)d);
+        rk4_step(d, h, lin_rhs, &c, traj + (k + 1) * d, work);
+    }
+    for (int64_t k = nsteps - 1; k >= 0; --k)
+        rk4_adjoint_step(d, h, lin_rhs, lin_vjp, &c, traj + k * d, lam, work);
+    free(traj);
+    free(work);
+    return 0;
+}
+
+typedef struct { const orc_net *net; const double *iext; orc_grads *g; } net_adj_ctx;
+
+static void net_rhs_adj(void *c, const double *y, double *dy)
+{
+    const net_adj_ctx *nc = (const net_adj_ctx *)c;
+    orc_rhs(nc->net, nc->iext, y, dy);
+}
+
+static void net_vjp(void *c, const double *y, const double *v, double *u)
+{
+    const net_adj_ctx *nc = (const net_adj_ctx *)c;
+    orc_vjp(nc->net, nc->iext, y, v, u, nc->g);
+}
+
+/* Gradient of the linear functional L = sum_f sum_i dLdV[f][i] V_i(frame f)
+   over the RK4 trajectory of nsteps steps from y0 (first step at global
+   index step0; frame f is the state after global step k with
+   k % rec_stride == 0, in order).  Outputs the adjoint of y0 (grad_y0[dim]),
+   dL/dw (grad_w[S]) and dL/d(neuron-type parameters) (grad_np, row per
+   type).  Memory: states are kept every `ckpt` steps and each segment is
+   recomputed.  Returns 0, or -1 on allocation failure. */
+int orc_adjoint(const orc_net *net, const double *y0, int64_t step0, int64_t nsteps, int64_t rec_stride,
+                const double *dLdV, double *grad_y0, double *grad_w, double *grad_np, int64_t ckpt)
+{
+    const int64_t d = 4 * net->N + 2 * net->S;
+    if (ckpt < 1) ckpt = 1;
+    const int64_t nck = (nsteps + ckpt - 1) / ckpt + 1;
+    double *cks = (double *)malloc(sizeof(double) * (size_t)d * (size_t)nck);
+    double *seg = (double *)malloc(sizeof(double) * (size_t)d * (size_t)(ckpt + 1));
+    double *work = (double *)malloc(sizeof(double) * (8 * (size_t)d + 2 * (size_t)net->N));
+    if (!cks || !seg || !work) { free(cks); free(seg); free(work); return -1; }
+    double *iext = work + 8 * d;
+    orc_grads g = {grad_w, grad_np};
+    net_ctx fc = {net, iext};
+    net_adj_ctx ac = {net, iext, &g};
+
+    /* forward: checkpoints every ckpt steps */
+    memcpy(cks, y0, sizeof(double) * (size_t)d);
+    {
+        double *y = seg;
+        memcpy(y, y0, sizeof(double) * (size_t)d);
+        for (int64_t k = 0; k < nsteps; ++k) {
+            orc_input(net, step0 + k, iext);
+            rk4_step(d, net->dt, net_rhs, &fc, y, work);
+            if ((k + 1) % ckpt == 0) memcpy(cks + ((k + 1) / ckpt) * d, y, sizeof(double) * (size_t)d);
+        }
+    }
+    /* frames: global steps k in (step0, step0 + nsteps] with k % rec_stride == 0 */
+    int64_t nframes = 0;
+    if (rec_stride > 0)
+        for (int64_t k = step0 + 1; k <= step0 + nsteps; ++k) nframes += (k % rec_stride) == 0;
+    int64_t frame = nframes - 1;
+
+    double *lam = grad_y0;
+    for (int64_t i = 0; i < d; ++i) lam[i] = 0.0;
+    /* the last state may itself be a frame */
+    if (rec_stride > 0 && (step0 + nsteps) % rec_stride == 0 && frame >= 0) {
+        for (int64_t i = 0; i < net->N; ++i) lam[i] += dLdV[frame * net->N + i];
+        --frame;
+    }
+    for (int64_t c = (nsteps - 1) / ckpt; c >= 0; --c) {
+        const int64_t k0 = c * ckpt, k1 = (k0 + ckpt < nsteps) ? k0 + ckpt : nsteps;
+        /* recompute the segment's step states */
+        memcpy(seg, cks + c * d, sizeof(double) * (size_t)d);
+        for (int64_t k = k0; k < k1 - 1; ++k) {
+            memcpy(seg + (k - k0 + 1) * d, seg + (k - k0) * d, sizeof(double) * (size_t)d);
+            orc_input(net, step0 + k, iext);
+            rk4_step(d, net->dt, net_rhs, &fc, seg + (k - k0 + 1) * d, work);
+        }
+        for (int64_t k = k1 - 1; k >= k0; --k) {
+            orc_input(net, step0 + k, iext);
+            rk4_adjoint_step(d, net->dt, net_rhs_adj, net_vjp, &ac, seg + (k - k0) * d, lam, work);
+            /* state y_{step0+k} is a frame when its global index qualifies */
+            if (rec_stride > 0 && k > 0 && (step0 + k) % rec_stride == 0 && frame >= 0) {
+                for (int64_t i = 0; i < net->N; ++i) lam[i] += dLdV[frame * net->N + i];
+                --frame;
+            }
+        }
+    }
+    free(cks);
+    free(seg);
+    free(work);
+    return 0;
 }

@@ -1,5 +1,6 @@
 """Plants plausible mistakes in a copy of the oracle (CPU only) and checks
-that the pins in test_oracle_pins.py catch every one of them.
+that the pins in test_oracle_pins.py and test_oracle_adjoint.py catch every
+one of them.
 
 The Philox round structure is deliberately absent: it is pinned only
 statistically, so its parity with the published generator is unpinned.
@@ -18,19 +19,30 @@ MUTANTS = [
     ("Y[i] = y[i] + h * k3[i];", "Y[i] = y[i] + 0.5 * h * k3[i];"),        # RK4 node
     ("- q[Q_B] * r[k];", "+ q[Q_B] * r[k];"),                              # sign
     ("G * (V[i] - q[Q_E]);", "G * (V[j] - q[Q_E]);"),                      # index
-    ("orc_transmitter(V[j],", "orc_transmitter(V[i],"),                    # index
-    ("m[i] * m[i] * m[i] * h[i]", "m[i] * m[i] * h[i]"),                   # exponent
+    ("double T = orc_transmitter(V[j], q[Q_VP]", "double T = orc_transmitter(V[i], q[Q_VP]"),  # index
+    ("double iNa = p[P_GNA] * m[i] * m[i] * m[i] * h[i]", "double iNa = p[P_GNA] * m[i] * m[i] * h[i]"),  # exponent
     ("double iL = p[P_GL] * (V[i] - p[P_EL]);", "double iL = 0.0;"),       # dropped term
-    ("s[k] * s[k] * s[k] * s[k];", "s[k] * s[k] * s[k];"),                 # exponent
+    ("s[k] * s[k] * s[k] * s[k];\n                G = s4 / (s4 + q[Q_KD]);",
+     "s[k] * s[k] * s[k];\n                G = s4 / (s4 + q[Q_KD]);"),                  # exponent
     ("- q[Q_K4] * s[k];", "- q[Q_K3] * s[k];"),                            # operand
     ("exp(-(V + 65.0) / 18.0)", "exp(-(V + 65.0) / 20.0)"),                # constant
     ("dh[i] = a[2] * (1.0 - h[i]) - a[3] * h[i];",
      "dh[i] = a[3] * (1.0 - h[i]) - a[2] * h[i];"),                        # swapped
     ("step < net->pulse_off[i]", "step <= net->pulse_off[i]"),             # off by one
     ("- iKL - isyn) / p[P_C];", "- iKL + isyn) / p[P_C];"),                # sign
-    ("(V[i] - p[P_EKL])", "(V[i] - p[P_EK])"),                             # operand
-    ("/ p[P_C];", ";"),                                                    # dropped factor
+    ("double iKL = p[P_GKL] * (V[i] - p[P_EKL]);", "double iKL = p[P_GKL] * (V[i] - p[P_EK]);"),  # operand
+    ("- iKL - isyn) / p[P_C];", "- iKL - isyn);"),                         # dropped factor
     ("(iext[i] - iNa", "(- iNa"),                                          # dropped input
+    # discrete adjoint
+    ("kb[i] = hstep / 3.0 * lam[i] + hstep * Yb[i];",
+     "kb[i] = hstep / 3.0 * lam[i] + 0.5 * hstep * Yb[i];"),               # tableau transpose
+    ("lam[i] += Ysum[i] + Yb[i];", "lam[i] += Ysum[i];"),                  # dropped stage
+    ("uV[i] += q * (-diion - gsum);", "uV[i] += q * (-diion);"),           # dropped term
+    ("uV[j] += vr[k] * sq[Q_A] * dT * (1.0 - r[k]);",
+     "uV[i] += vr[k] * sq[Q_A] * dT * (1.0 - r[k]);"),                     # wrong index
+    ("out[3] = r[3] * (1.0 - r[3]) / 10.0;", "out[3] = r[3] * (1.0 - r[3]) / 20.0;"),  # constant
+    ("gp[P_GK] += -q * n4 * (V[i] - p[P_EK]);", "gp[P_GK] += q * n4 * (V[i] - p[P_EK]);"),  # sign
+    ("if (g) g->gw[k] += -q * G * (V[i] - E);", "if (g) g->gw[k] += -q * (V[i] - E);"),  # dropped factor
 ]
 
 
@@ -48,5 +60,6 @@ def test_pins_catch_planted_mistake(tmp_path, old, new):
     assert text.count(old) == 1, old
     src.write_text(text.replace(old, new))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py"], cwd=tmp_path, capture_output=True, text=True)
+                        "tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py"],
+                       cwd=tmp_path, capture_output=True, text=True)
     assert r.returncode != 0, "mutant survived: " + new + "\n" + r.stdout[-400:]
