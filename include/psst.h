@@ -171,6 +171,34 @@ int psst_set_step(psst_net *h, int64_t step);
 int psst_read_record(const psst_net *h, float *dst, size_t cap_frames, int64_t *n_frames,
                      int dst_on_device, void *stream);
 
+/* Replace the synaptic weights ([S] floats, CSR order) or the neuron-type
+   table ([n_neuron_types * PSST_NEURON_NPARAM] floats) from host or device
+   memory; used by later psst_integrate / psst_adjoint calls (stream-ordered;
+   synchronises when the source is on the host). */
+int psst_set_weights(psst_net *h, const float *w, size_t n, int on_device, void *stream);
+int psst_set_neuron_params(psst_net *h, const float *p, size_t n, int on_device, void *stream);
+
+/* Discrete adjoint of the RK4 map (no counterpart in the paper; the
+   differentiated form).  For the n_steps steps that a psst_integrate call
+   made now would take -- from the current state and step index -- computes
+   the gradient of
+       L = sum_f sum_i dL_dV[f][i] * V_i(frame f)
+   where frame f is the f-th recorded frame of that span (global steps k in
+   (step, step + n_steps] with k % rec_stride == 0; n_frames must equal their
+   count).  Outputs (device arrays, overwritten):
+     grad_w              [S]   dL/dw for every synapse, CSR order;
+     grad_neuron_params  [n_neuron_types * 9]  dL/d(neuron-type table);
+     grad_state0         [4][N] dL/d(V, m, h, n at the start), or NULL.
+   The state and step index are left unchanged.  Memory: reduced states are
+   checkpointed every ckpt_every steps and each segment is recomputed;
+   the handle allocates the storage on first use and grows it as needed.
+   Preconditions: CTA mode; every network fits one CTA for the adjoint; all
+   gates of a (presynaptic neuron, synapse type) pair hold the same value at
+   the start (true from rest), else the device reports PSST_ERR_UNSUPPORTED
+   through psst_status.  Asynchronous on `stream`. */
+int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_frames, int32_t ckpt_every,
+                 float *grad_w, float *grad_neuron_params, float *grad_state0, void *stream);
+
 /* Sizes, progress and the launch configuration. */
 int psst_query(const psst_net *h, psst_info *out);
 

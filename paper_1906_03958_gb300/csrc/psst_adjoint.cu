@@ -1,0 +1,583 @@
+// Discrete adjoint of the RK4 network map (the differentiated form).
+//
+// Gradient of L = sum_f sum_i dL/dV[f][i] V_i(frame f) over n RK4 steps from
+// the current state, with respect to every synaptic weight and every
+// neuron-type parameter, for batches of networks (one CTA per network).
+//
+// Gate state.  When all gates of a (presynaptic neuron j, synapse type tau)
+// pair start from the same value -- as they do from rest -- they stay equal
+// for ever, since their equation depends only on V_j and the type.  The
+// kernel then carries one gate (r, and s for second order) per pair: the
+// same trajectory as the per-synapse model, with state 4N + 2M
+// (M = N * n_types) instead of 4N + 2S.  psst_adjoint checks the
+// precondition on the starting state.
+//
+// Reverse sweep (Hager 2000; Sandu 2006).  For the step y_n -> y_{n+1} with
+// stages Y_s and k_s = f(Y_s):
+//   kb4 = h/6 lam,           Yb4 = J(Y4)^T kb4
+//   kb3 = h/3 lam + h Yb4,   Yb3 = J(Y3)^T kb3
+//   kb2 = h/3 lam + h/2 Yb3, Yb2 = J(Y2)^T kb2
+//   kb1 = h/6 lam + h/2 Yb2, Yb1 = J(Y1)^T kb1
+//   lam_n = lam + Yb1 + Yb2 + Yb3 + Yb4;  theta_bar += sum_s (df/dtheta)^T kb_s.
+// States are checkpointed every `ckpt` steps in a first forward pass; each
+// segment is recomputed forward (step states kept in global memory), then
+// swept backward, recomputing each step's four stages in shared memory.
+//
+// Jacobian-transpose product at a stage (q_i = kbV_i / C_i,
+// A_i = sum_k w_k G_p(k), G_p the pair's gate, I_syn = V A - B):
+//   uV_i = q_i (-dI_ion/dV - A_i) + sum_x kbx_i (alpha_x' (1-x) - beta_x' x)
+//          + sum_tau kbr_(i,tau) a T'(V_i) (1 - r_(i,tau))
+//   um_i = -q_i 3 gNa m^2 h (V - ENa) - kbm_i (alpha_m + beta_m), likewise h, n
+//   ur_p = -C_p [first order] - (a T + b) kbr_p + K3 kbs_p [second order]
+//   us_p = -C_p G'(s_p) - K4 kbs_p               [second order]
+//   with the column sum C_p = sum_{k in p} w_k (q_i V_i - q_i E_k);
+//   dL/dw_k += -q_i G_p (V_i - E_k);  dL/dgNa += -q_i m^3 h (V - ENa), ...
+// The column sums use shared-memory atomics (their order is not fixed); the
+// weight gradients are accumulated with Kahan compensation.
+#include <cuda_runtime.h>
+
+#include "psst_device.cuh"
+#include "psst_internal.h"
+
+namespace psst {
+
+namespace {
+
+constexpr int ADJ_THREADS = 512;
+
+__device__ __forceinline__ float ratio_u_deriv(float u) {
+    // d/du of u / (1 - e^{-u}); Bernoulli series near 0
+    if (fabsf(u) < 0.1f) {
+        const float u2 = u * u;
+        return fmaf(u, fmaf(u2, -1.0f / 180.0f, 1.0f / 6.0f), 0.5f);
+    }
+    const float e = __expf(-u), den = 1.0f - e;
+    return __fdividef(den - u * e, den * den);
+}
+
+struct AdjSmem {
+    // items (row-aligned, K chunks of 4 synapses, slot-major)
+    float4 *w;
+    ushort4 *id;
+    float *pa, *pb;
+    int *ib;           // [N+1] first item of each row
+    unsigned short *irow;  // [n_items] row of each item
+    // per stage s = 0..3 (stored by the forward recompute)
+    float *sV, *sm, *sh, *sn;  // [4][N]
+    float *sr, *ss, *sG;       // [4][M]
+    float *sA, *sfv;           // [4][N]
+    // reduced state y (step start) and running RK4 sums
+    float *y;                  // [4N + 2M]: V, m, h, n, r, s
+    float *acc;                // [4N + 2M]
+    // adjoint
+    float *lam, *yprev, *ysum; // [4N + 2M]
+    float2 *ab;                // [N]: q_i V_i, q_i
+    float *csum;               // [M]
+    float *uV;                 // [N] partial uV
+    double *gp;                // [N][9] neuron parameter gradients
+    float *prm;                // [9][N] (row 0: 1/C)
+    float *iext, *inp;         // [N], [2][N]
+};
+
+__host__ __device__ inline long long adj_smem_bytes(int N, int M, int n_items, int K) {
+    long long b = 0;
+    const long long slots = (long long)K * n_items;
+    b += slots * (16 + 8);              // w, id
+    b += 8LL * n_items + 2LL * n_items + 16;  // pa, pb, irow
+    b += 4LL * (N + 1);
+    b += 4LL * 4 * (6LL * N + 3LL * M);  // stage storage
+    b += 4LL * 5 * (4LL * N + 2LL * M);  // y, acc, lam, yprev, ysum
+    b += 8LL * N + 4LL * M + 4LL * N;     // ab, csum, uV
+    b += 8LL * 9 * N;                    // gp (double)
+    b += 4LL * 9 * N + 4LL * 3 * N;      // prm, iext, inp
+    b += 16 * 32;                        // alignment slack
+    return b;
+}
+
+__device__ inline unsigned char *take(unsigned char *&p, long long bytes) {
+    unsigned char *at = p;
+    p += (bytes + 15) & ~15LL;
+    return at;
+}
+
+struct AdjNet {
+    int b, n0, N, nt, M, K, n_items, R;
+    long long sbase, S;
+};
+
+// ---------------------------------------------------------------- forward
+
+// Forward of one RK4 step of the reduced model from S.y (step `step`),
+// storing the four stages' values; on return S.y holds the next state.
+template <bool STORE>
+__device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, const float *stab, long long step,
+                         float dt) {
+    const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M;
+    float *V = S.y, *m = S.y + N, *h = S.y + 2 * N, *n = S.y + 3 * N, *r = S.y + 4 * N, *s = S.y + 4 * N + M;
+    const bool in_pulse = step >= v.pulse_on[a.b] && step < v.pulse_off[a.b];
+    for (int i = tid; i < N; i += nthr)
+        S.iext[i] = input_current(v, S.inp[i], S.inp[N + i], in_pulse, (long long)a.n0 + i, step);
+    // stage values live in the stage arrays (stage 0 = y)
+    for (int i = tid; i < N; i += nthr) {
+        S.sV[i] = V[i];
+        S.sm[i] = m[i];
+        S.sh[i] = h[i];
+        S.sn[i] = n[i];
+        for (int t = 0; t < nt; ++t) {
+            const int p = i * nt + t;
+            const float *sp = stab + t * 9;
+            S.sr[p] = r[p];
+            S.ss[p] = s[p];
+            const float s2 = s[p] * s[p], s4 = s2 * s2;
+            S.sG[p] = sp[SP_KIND] != 0.0f ? __fdividef(s4, s4 + sp[SP_KD]) : r[p];
+        }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int st = 0; st < 4; ++st) {
+        const float *G = S.sG + st * M;
+        // synaptic sums per item
+        const int K = a.K, ni = a.n_items;
+        for (int it = tid; it < ni; it += nthr) {
+            float A = 0.0f, B = 0.0f;
+            for (int j = 0; j < K; ++j) {
+                const int c = j * ni + it;
+                const float4 w = S.w[c];
+                const ushort4 id = S.id[c];
+                const float g0 = G[id.x], g1 = G[id.y], g2 = G[id.z], g3 = G[id.w];
+                A = fmaf(w.x, g0, A);
+                A = fmaf(w.y, g1, A);
+                A = fmaf(w.z, g2, A);
+                A = fmaf(w.w, g3, A);
+                B = fmaf(w.x * stab[(id.x % nt) * 9 + SP_E], g0, B);
+                B = fmaf(w.y * stab[(id.y % nt) * 9 + SP_E], g1, B);
+                B = fmaf(w.z * stab[(id.z % nt) * 9 + SP_E], g2, B);
+                B = fmaf(w.w * stab[(id.w % nt) * 9 + SP_E], g3, B);
+            }
+            S.pa[it] = A;
+            S.pb[it] = B;
+        }
+        __syncthreads();
+        const float WGT = (st == 0 || st == 3) ? 1.0f : 2.0f;
+        const float cnext = (st == 2) ? dt : 0.5f * dt;
+        const float dt6 = dt * (1.0f / 6.0f);
+        for (int i = tid; i < N; i += nthr) {
+            float A = 0.0f, B = 0.0f;
+            for (int it = S.ib[i]; it < S.ib[i + 1]; ++it) {
+                A += S.pa[it];
+                B += S.pb[it];
+            }
+            const float Vs = S.sV[st * N + i], ms = S.sm[st * N + i], hs = S.sh[st * N + i], ns = S.sn[st * N + i];
+            const Rates q = hh_rates(Vs);
+            const float *P = S.prm;
+            const float m3h = ms * ms * ms * hs, n4 = ns * ns * ns * ns;
+            const float iion = P[NP_GNA * N + i] * m3h * (Vs - P[NP_ENA * N + i]) +
+                               P[NP_GK * N + i] * n4 * (Vs - P[NP_EK * N + i]) +
+                               P[NP_GL * N + i] * (Vs - P[NP_EL * N + i]) +
+                               P[NP_GKL * N + i] * (Vs - P[NP_EKL * N + i]);
+            const float fV = (S.iext[i] - iion - fmaf(Vs, A, -B)) * P[NP_C * N + i];
+            const float d[4] = {fV, q.am * (1.0f - ms) - q.bm * ms, q.ah * (1.0f - hs) - q.bh * hs,
+                                q.an * (1.0f - ns) - q.bn * ns};
+            if (STORE) {
+                S.sA[st * N + i] = A;
+                S.sfv[st * N + i] = fV;
+            }
+            float *stg[4] = {S.sV, S.sm, S.sh, S.sn};
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const int ix = x * N + i;
+                const float ac = (st == 0) ? d[x] : fmaf(WGT, d[x], S.acc[ix]);
+                if (st < 3) {
+                    S.acc[ix] = ac;
+                    stg[x][(st + 1) * N + i] = fmaf(cnext, d[x], S.y[ix]);
+                } else {
+                    S.y[ix] = fmaf(dt6, ac, S.y[ix]);
+                }
+            }
+            // own gate pairs
+            for (int t = 0; t < nt; ++t) {
+                const int p = i * nt + t;
+                const float *sp = stab + t * 9;
+                const float rs = S.sr[st * M + p], ss = S.ss[st * M + p];
+                const float T = transmitter(Vs, sp[SP_VP], sp[SP_KP]);
+                const float dr = sp[SP_A] * T * (1.0f - rs) - sp[SP_B] * rs;
+                const float ds = sp[SP_KIND] != 0.0f ? sp[SP_K3] * rs - sp[SP_K4] * ss : 0.0f;
+                const int ir = 4 * N + p, is = 4 * N + M + p;
+                const float ar = (st == 0) ? dr : fmaf(WGT, dr, S.acc[ir]);
+                const float as = (st == 0) ? ds : fmaf(WGT, ds, S.acc[is]);
+                float rn, sn;
+                if (st < 3) {
+                    S.acc[ir] = ar;
+                    S.acc[is] = as;
+                    rn = fmaf(cnext, dr, S.y[ir]);
+                    sn = fmaf(cnext, ds, S.y[is]);
+                    S.sr[(st + 1) * M + p] = rn;
+                    S.ss[(st + 1) * M + p] = sn;
+                    const float s2 = sn * sn, s4 = s2 * s2;
+                    S.sG[(st + 1) * M + p] = sp[SP_KIND] != 0.0f ? __fdividef(s4, s4 + sp[SP_KD]) : rn;
+                } else {
+                    S.y[ir] = fmaf(dt6, ar, S.y[ir]);
+                    S.y[is] = fmaf(dt6, as, S.y[is]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- reverse
+
+// Reverse of the step whose stages fwd_step<true> just stored: lam holds the
+// adjoint of y_{n+1} on entry and of y_n on exit (before the frame term).
+__device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, float dt, float2 *gslot) {
+    const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M, K = a.K, ni = a.n_items;
+    const int D = 4 * N + 2 * M;
+    const float cb[4] = {dt / 6.0f, dt / 3.0f, dt / 3.0f, dt / 6.0f};  // h b_s
+    const float ca[4] = {0.5f * dt, 0.5f * dt, dt, 0.0f};             // h a_{s+1,s}
+#pragma unroll 1
+    for (int st = 3; st >= 0; --st) {
+        // A) owners: stage adjoint kb, neuron-local products, parameter gradients
+        for (int i = tid; i < N; i += nthr) {
+            const float Vs = S.sV[st * N + i], ms = S.sm[st * N + i], hs = S.sh[st * N + i], ns = S.sn[st * N + i];
+            float kb[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const int ix = x * N + i;
+                kb[x] = cb[st] * S.lam[ix] + (st < 3 ? ca[st] * S.yprev[ix] : 0.0f);
+            }
+            const float *P = S.prm;
+            const float invC = P[NP_C * N + i];
+            const float q = kb[0] * invC;
+            S.ab[i] = make_float2(q * Vs, q);
+            const Rates rt = hh_rates(Vs);
+            const float dam = 0.1f * ratio_u_deriv((Vs + 40.0f) * 0.1f), dbm = -rt.bm * (1.0f / 18.0f);
+            const float dah = -rt.ah * (1.0f / 20.0f), dbh = rt.bh * (1.0f - rt.bh) * 0.1f;
+            const float dan = 0.01f * ratio_u_deriv((Vs + 55.0f) * 0.1f), dbn = -rt.bn * (1.0f / 80.0f);
+            const float m3h = ms * ms * ms * hs, n4 = ns * ns * ns * ns;
+            const float gNa = P[NP_GNA * N + i], gK = P[NP_GK * N + i], gL = P[NP_GL * N + i], gKL = P[NP_GKL * N + i];
+            const float ENa = P[NP_ENA * N + i], EK = P[NP_EK * N + i], EL = P[NP_EL * N + i], EKL = P[NP_EKL * N + i];
+            const float diion = gNa * m3h + gK * n4 + gL + gKL;
+            float uV = q * (-diion - S.sA[st * N + i]);
+            uV = fmaf(kb[1], dam * (1.0f - ms) - dbm * ms, uV);
+            uV = fmaf(kb[2], dah * (1.0f - hs) - dbh * hs, uV);
+            uV = fmaf(kb[3], dan * (1.0f - ns) - dbn * ns, uV);
+            S.uV[i] = uV;
+            S.yprev[N + i] = -q * gNa * 3.0f * ms * ms * hs * (Vs - ENa) - kb[1] * (rt.am + rt.bm);
+            S.yprev[2 * N + i] = -q * gNa * ms * ms * ms * (Vs - ENa) - kb[2] * (rt.ah + rt.bh);
+            S.yprev[3 * N + i] = -q * gK * 4.0f * ns * ns * ns * (Vs - EK) - kb[3] * (rt.an + rt.bn);
+            double *g = S.gp + 9 * i;
+            g[NP_C] += (double)(-q * S.sfv[st * N + i]);
+            g[NP_GNA] += (double)(-q * m3h * (Vs - ENa));
+            g[NP_GK] += (double)(-q * n4 * (Vs - EK));
+            g[NP_GL] += (double)(-q * (Vs - EL));
+            g[NP_GKL] += (double)(-q * (Vs - EKL));
+            g[NP_ENA] += (double)(q * gNa * m3h);
+            g[NP_EK] += (double)(q * gK * n4);
+            g[NP_EL] += (double)(q * gL);
+            g[NP_EKL] += (double)(q * gKL);
+        }
+        __syncthreads();
+        // B) items: column sums C_p and weight gradients
+        const float *G = S.sG + st * M;
+        for (int it = tid; it < ni; it += nthr) {
+            const float2 abv = S.ab[S.irow[it]];
+            for (int j = 0; j < K; ++j) {
+                const int c = j * ni + it;
+                const float4 w = S.w[c];
+                const ushort4 id = S.id[c];
+                const float wv[4] = {w.x, w.y, w.z, w.w};
+                const int iv[4] = {id.x, id.y, id.z, id.w};
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    const int p = iv[q4];
+                    const float E = stab[(p % nt) * 9 + SP_E];
+                    const float x = fmaf(-E, abv.y, abv.x);  // q V - q E
+                    if (wv[q4] != 0.0f) atomicAdd(&S.csum[p], wv[q4] * x);
+                    // Kahan: slot += -G x
+                    float2 k2 = gslot[c * 4 + q4];
+                    const float yv = -G[p] * x - k2.y;
+                    const float t = k2.x + yv;
+                    k2.y = (t - k2.x) - yv;
+                    k2.x = t;
+                    gslot[c * 4 + q4] = k2;
+                }
+            }
+        }
+        __syncthreads();
+        // C) owners: gate-pair products and the presynaptic voltage term
+        for (int i = tid; i < N; i += nthr) {
+            const float Vs = S.sV[st * N + i];
+            float uV = S.uV[i];
+            for (int t = 0; t < nt; ++t) {
+                const int p = i * nt + t;
+                const float *sp = stab + t * 9;
+                const float C = S.csum[p];
+                S.csum[p] = 0.0f;
+                const int ir = 4 * N + p, is = 4 * N + M + p;
+                const float kbr = cb[st] * S.lam[ir] + (st < 3 ? ca[st] * S.yprev[ir] : 0.0f);
+                const float kbs = cb[st] * S.lam[is] + (st < 3 ? ca[st] * S.yprev[is] : 0.0f);
+                const float rs = S.sr[st * M + p], ss = S.ss[st * M + p];
+                const float T = transmitter(Vs, sp[SP_VP], sp[SP_KP]);
+                const float dT = T * (1.0f - T) * sp[SP_KP];  // table holds 1/Kp
+                float ur = -(sp[SP_A] * T + sp[SP_B]) * kbr, us = 0.0f;
+                if (sp[SP_KIND] != 0.0f) {
+                    const float s2 = ss * ss, s4 = s2 * s2, den = s4 + sp[SP_KD];
+                    const float dG = __fdividef(4.0f * s2 * ss * sp[SP_KD], den * den);
+                    ur = fmaf(sp[SP_K3], kbs, ur);
+                    us = -C * dG - sp[SP_K4] * kbs;
+                } else {
+                    ur -= C;
+                }
+                uV = fmaf(kbr * sp[SP_A] * dT, 1.0f - rs, uV);
+                S.yprev[ir] = ur;
+                S.yprev[is] = us;
+                S.ysum[ir] += ur;
+                S.ysum[is] += us;
+            }
+            S.yprev[i] = uV;
+            S.ysum[i] += uV;
+            S.ysum[N + i] += S.yprev[N + i];
+            S.ysum[2 * N + i] += S.yprev[2 * N + i];
+            S.ysum[3 * N + i] += S.yprev[3 * N + i];
+        }
+        // the next stage's part A reads only owner-written values; its part B
+        // reads ab after the barrier that follows part A
+    }
+    // lam_n = lam + sum of the stage adjoints (owner-only values)
+    for (int i = tid; i < N; i += nthr) {
+        for (int x = 0; x < 4; ++x) {
+            const int ix = x * N + i;
+            S.lam[ix] += S.ysum[ix];
+            S.ysum[ix] = 0.0f;
+        }
+        for (int t = 0; t < nt; ++t) {
+            const int ir = 4 * N + i * nt + t, is = 4 * N + M + i * nt + t;
+            S.lam[ir] += S.ysum[ir];
+            S.lam[is] += S.ysum[is];
+            S.ysum[ir] = 0.0f;
+            S.ysum[is] = 0.0f;
+        }
+    }
+    (void)D;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av, long long step0, int nsteps) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float stab[PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM];
+    __shared__ int s_bad;
+    for (int i = threadIdx.x; i < v.n_stypes * PSST_SYN_NPARAM; i += blockDim.x) {
+        float x = v.sparams[i];
+        if (i % PSST_SYN_NPARAM == SP_KP) x = 1.0f / x;
+        stab[i] = x;
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    AdjNet a;
+    a.b = blockIdx.x;
+    a.n0 = v.net_off[a.b];
+    a.N = v.net_off[a.b + 1] - a.n0;
+    a.nt = v.n_stypes;
+    a.M = a.N * a.nt;
+    a.K = av.K[a.b];
+    a.n_items = av.n_items[a.b];
+    a.R = 4 * a.N + 2 * a.M;
+    a.sbase = v.row_ptr[a.n0];
+    a.S = v.row_ptr[a.n0 + a.N] - a.sbase;
+    const int N = a.N, M = a.M, nt = a.nt, K = a.K, ni = a.n_items;
+
+    AdjSmem S;
+    unsigned char *p = smem;
+    const long long slots = (long long)K * ni;
+    S.w = (float4 *)take(p, 16 * slots);
+    S.id = (ushort4 *)take(p, 8 * slots);
+    S.pa = (float *)take(p, 4LL * ni);
+    S.pb = (float *)take(p, 4LL * ni);
+    S.irow = (unsigned short *)take(p, 2LL * ni);
+    S.ib = (int *)take(p, 4LL * (N + 1));
+    S.sV = (float *)take(p, 16LL * N);
+    S.sm = (float *)take(p, 16LL * N);
+    S.sh = (float *)take(p, 16LL * N);
+    S.sn = (float *)take(p, 16LL * N);
+    S.sr = (float *)take(p, 16LL * M);
+    S.ss = (float *)take(p, 16LL * M);
+    S.sG = (float *)take(p, 16LL * M);
+    S.sA = (float *)take(p, 16LL * N);
+    S.sfv = (float *)take(p, 16LL * N);
+    S.y = (float *)take(p, 4LL * a.R);
+    S.acc = (float *)take(p, 4LL * a.R);
+    S.lam = (float *)take(p, 4LL * a.R);
+    S.yprev = (float *)take(p, 4LL * a.R);
+    S.ysum = (float *)take(p, 4LL * a.R);
+    S.ab = (float2 *)take(p, 8LL * N);
+    S.csum = (float *)take(p, 4LL * M);
+    S.uV = (float *)take(p, 4LL * N);
+    S.gp = (double *)take(p, 72LL * N);
+    S.prm = (float *)take(p, 36LL * N);
+    S.iext = (float *)take(p, 4LL * N);
+    S.inp = (float *)take(p, 8LL * N);
+
+    const long long *rp = v.row_ptr + a.n0;
+    const uint32_t *gcode = v.syn_code + a.sbase;
+    const float *gw = v.weight + a.sbase;
+    const float *gr = v.state + 4 * v.N + a.sbase;
+    const float *gs = v.state + 4 * v.N + v.S + a.sbase;
+
+    // neurons, parameters, inputs; initial reduced state
+    for (int i = tid; i < N; i += nthr) {
+        for (int x = 0; x < 4; ++x) S.y[x * N + i] = v.state[(long long)x * v.N + a.n0 + i];
+        const float *pp = v.nparams + (long long)v.neuron_type[a.n0 + i] * PSST_NEURON_NPARAM;
+        S.prm[NP_C * N + i] = 1.0f / pp[NP_C];
+        for (int x = 1; x < PSST_NEURON_NPARAM; ++x) S.prm[x * N + i] = pp[x];
+        S.inp[i] = v.i_const[a.n0 + i];
+        S.inp[N + i] = v.pulse_amp ? v.pulse_amp[a.n0 + i] : 0.0f;
+        for (int x = 0; x < 9; ++x) S.gp[9 * i + x] = 0.0;
+        S.uV[i] = 0.0f;
+    }
+    for (int q = tid; q < M; q += nthr) {
+        S.y[4 * N + q] = 0.0f;
+        S.y[4 * N + M + q] = 0.0f;
+        S.csum[q] = 0.0f;
+    }
+    for (int q = tid; q < a.R; q += nthr) {
+        S.lam[q] = 0.0f;
+        S.ysum[q] = 0.0f;
+        S.yprev[q] = 0.0f;
+    }
+    // items: row-aligned, each row's synapses in CSR order
+    int *cnt = (int *)S.acc;  // scratch: acc is written before it is read
+    for (int i = tid; i < N; i += nthr) cnt[i] = (int)((rp[i + 1] - rp[i] + 4 * K - 1) / (4 * K));
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int i = 0; i < N; ++i) {
+            S.ib[i] = acc;
+            acc += cnt[i];
+        }
+        S.ib[N] = acc;
+    }
+    __syncthreads();
+    for (long long c = tid; c < slots; c += nthr) {
+        S.w[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        S.id[c] = make_ushort4(0, 0, 0, 0);
+    }
+    for (int i = tid; i < N; i += nthr)
+        for (int it = S.ib[i]; it < S.ib[i + 1]; ++it) S.irow[it] = (unsigned short)i;
+    __syncthreads();
+    float *W = (float *)S.w;
+    unsigned short *ID = (unsigned short *)S.id;
+    for (int i = tid; i < N; i += nthr) {
+        const long long k0 = rp[i] - a.sbase;
+        for (long long k = k0; k < rp[i + 1] - a.sbase; ++k) {
+            const int m = (int)(k - k0);
+            const int t = S.ib[i] + m / (4 * K), j = (m % (4 * K)) >> 2;
+            const long long slot = ((long long)j * ni + t) * 4 + (m & 3);
+            W[slot] = gw[k];
+            const int ci = (int)(gcode[k] & 0xFFFFFFu);
+            ID[slot] = (unsigned short)ci;
+            // pair gate from its synapses (all equal by the precondition)
+            S.y[4 * N + ci] = gr[k];
+            S.y[4 * N + M + ci] = gs[k];
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += nthr) {
+        for (long long k = rp[i] - a.sbase; k < rp[i + 1] - a.sbase; ++k) {
+            const int ci = (int)(gcode[k] & 0xFFFFFFu);
+            if (S.y[4 * N + ci] != gr[k] || S.y[4 * N + M + ci] != gs[k]) s_bad = 1;
+        }
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (tid == 0) set_error(v.err, PSST_ERR_UNSUPPORTED);
+        return;
+    }
+
+    // pass 1: checkpoints every ckpt steps
+    float *ck = av.ckpt + av.ck_off[a.b];
+    float *seg = av.seg + av.seg_off[a.b];
+    float2 *gslot = av.gslot + av.slot_off[a.b];
+    for (long long c = tid; c < slots * 4; c += nthr) gslot[c] = make_float2(0.0f, 0.0f);
+    const int ckpt = av.ckpt_every;
+    const float dt = v.dt;
+    for (int n = 0; n < nsteps; ++n) {
+        if (n % ckpt == 0)
+            for (int q = tid; q < a.R; q += nthr) ck[(long long)(n / ckpt) * a.R + q] = S.y[q];
+        fwd_step<false>(v, a, S, stab, step0 + n, dt);
+    }
+    // frames: global steps k in (step0, step0 + nsteps] with k % stride == 0
+    const int stride = v.rec_stride;
+    int frame = av.n_frames - 1;
+    const float *dl = av.dLdV;
+    if (stride > 0 && (step0 + nsteps) % stride == 0 && frame >= 0) {
+        for (int i = tid; i < N; i += nthr) S.lam[i] += dl[(long long)frame * v.N + a.n0 + i];
+        --frame;
+    }
+    __syncthreads();
+    // pass 2: segments backward
+    const int nseg = (nsteps + ckpt - 1) / ckpt;
+    for (int c = nseg - 1; c >= 0; --c) {
+        const int k0 = c * ckpt, k1 = min(k0 + ckpt, nsteps);
+        for (int q = tid; q < a.R; q += nthr) S.y[q] = ck[(long long)c * a.R + q];
+        __syncthreads();
+        for (int n = k0; n < k1; ++n) {
+            for (int q = tid; q < a.R; q += nthr) seg[(long long)(n - k0) * a.R + q] = S.y[q];
+            if (n + 1 < k1) fwd_step<false>(v, a, S, stab, step0 + n, dt);
+        }
+        __syncthreads();
+        for (int n = k1 - 1; n >= k0; --n) {
+            for (int q = tid; q < a.R; q += nthr) S.y[q] = seg[(long long)(n - k0) * a.R + q];
+            __syncthreads();
+            fwd_step<true>(v, a, S, stab, step0 + n, dt);
+            rev_step(a, S, stab, dt, gslot);
+            if (stride > 0 && n > 0 && (step0 + n) % stride == 0 && frame >= 0) {
+                for (int i = tid; i < N; i += nthr) S.lam[i] += dl[(long long)frame * v.N + a.n0 + i];
+                --frame;
+            }
+            __syncthreads();
+        }
+    }
+    // outputs: weight gradients in CSR order, neuron parameter partials
+    for (int i = tid; i < N; i += nthr) {
+        const long long k0 = rp[i] - a.sbase;
+        for (long long k = k0; k < rp[i + 1] - a.sbase; ++k) {
+            const int m = (int)(k - k0);
+            const int t = S.ib[i] + m / (4 * K), j = (m % (4 * K)) >> 2;
+            const long long slot = ((long long)j * ni + t) * 4 + (m & 3);
+            const float2 g2 = gslot[slot];
+            av.grad_w[a.sbase + k] = g2.x - g2.y;
+        }
+        for (int x = 0; x < 9; ++x) av.gp_neuron[(long long)(a.n0 + i) * 9 + x] = S.gp[9 * i + x];
+        for (int x = 0; x < 4; ++x) av.grad_y0[(long long)x * v.N + a.n0 + i] = S.lam[x * N + i];
+    }
+}
+
+// Sum of the per-neuron parameter gradients into the neuron-type table
+// (fixed order: neuron index).
+__global__ void adj_reduce_types(const int *neuron_type, long long N, const double *gp_neuron, int n_types,
+                                 float *grad_np) {
+    const int t = blockIdx.x, x = threadIdx.x;
+    if (x >= 9) return;
+    double acc = 0.0;
+    for (long long i = 0; i < N; ++i)
+        if (neuron_type[i] == t) acc += gp_neuron[i * 9 + x];
+    grad_np[t * 9 + x] = (float)acc;
+}
+
+}  // namespace
+
+long long adj_smem_need(int N, int nt, int n_items, int K) { return adj_smem_bytes(N, N * nt, n_items, K); }
+
+cudaError_t adj_launch(const NetView &v, const AdjView &av, long long step0, int nsteps, int smem, int n_types,
+                       float *grad_np, cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    adj_kernel<<<v.n_nets, ADJ_THREADS, smem, stream>>>(v, av, step0, nsteps);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    adj_reduce_types<<<n_types, 32, 0, stream>>>(v.neuron_type, v.N, av.gp_neuron, n_types, grad_np);
+    return cudaGetLastError();
+}
+
+}  // namespace psst

@@ -62,6 +62,18 @@ struct psst_net {
     int block = 0, K = 0, smem = 0, grid = 0;
     int n_smem = 0, n_global = 0;
     int launches = 0;
+    int n_ntypes = 0;
+    int max_dyn = 0;
+    // adjoint plan and scratch (allocated on the first psst_adjoint)
+    std::vector<int> adj_K, adj_items;
+    int adj_smem = 0;
+    int *d_adjK = nullptr, *d_adjI = nullptr;
+    long long *d_ckoff = nullptr, *d_segoff = nullptr, *d_slotoff = nullptr;
+    float *adj_ckpt = nullptr, *adj_seg = nullptr, *adj_gy0 = nullptr;
+    float2 *adj_gslot = nullptr;
+    double *adj_gpn = nullptr;
+    long long adj_ck_cap = 0, adj_seg_cap = 0;
+    int adj_ckpt_every = 0;
 
     template <class T>
     cudaError_t alloc(T **p, size_t count) {
@@ -475,6 +487,8 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
     psst_net *h = new psst_net();
     h->device = dev;
     h->mode = mode;
+    h->n_ntypes = d->n_neuron_types;
+    h->max_dyn = caps.max_dyn;
     h->block = d->block_threads;
     NetView &v = h->v;
     v.n_nets = n_nets;
@@ -679,6 +693,135 @@ int psst_read_record(const psst_net *h, float *dst, size_t cap_frames, int64_t *
     if (e == cudaSuccess && !dst_on_device) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "psst_read_record");
     *n_frames = count;
+    return PSST_OK;
+}
+
+int psst_set_weights(psst_net *h, const float *w, size_t n, int on_device, void *stream) {
+    if (!h || !w) return fail(PSST_ERR_INVALID_ARG, "NULL argument");
+    if (n != (size_t)h->v.S) return fail(PSST_ERR_INVALID_ARG, "weights hold %zu values, network has %lld", n, h->v.S);
+    DeviceGuard guard(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync((void *)h->v.weight, w, n * sizeof(float),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? PSST_OK : cuda_fail(e, "psst_set_weights");
+}
+
+int psst_set_neuron_params(psst_net *h, const float *p, size_t n, int on_device, void *stream) {
+    if (!h || !p) return fail(PSST_ERR_INVALID_ARG, "NULL argument");
+    if (n != (size_t)h->n_ntypes * PSST_NEURON_NPARAM)
+        return fail(PSST_ERR_INVALID_ARG, "parameter table holds %zu values, expected %d", n,
+                    h->n_ntypes * PSST_NEURON_NPARAM);
+    DeviceGuard guard(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync((void *)h->v.nparams, p, n * sizeof(float),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? PSST_OK : cuda_fail(e, "psst_set_neuron_params");
+}
+
+int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_frames, int32_t ckpt_every,
+                 float *grad_w, float *grad_neuron_params, float *grad_state0, void *stream) {
+    if (!h || !grad_w || !grad_neuron_params) return fail(PSST_ERR_INVALID_ARG, "NULL argument");
+    if (h->mode != PSST_MODE_CTA) return fail(PSST_ERR_UNSUPPORTED, "the adjoint runs in CTA mode only");
+    if (n_steps < 1 || n_steps > (1LL << 30)) return fail(PSST_ERR_INVALID_ARG, "n_steps must be in 1..2^30");
+    if (ckpt_every < 1) return fail(PSST_ERR_INVALID_ARG, "ckpt_every must be >= 1");
+    const long long stride = h->v.rec_stride, s0 = h->step;
+    long long want = 0;
+    if (stride > 0) want = (s0 + n_steps) / stride - s0 / stride;
+    if (n_frames != want)
+        return fail(PSST_ERR_INVALID_ARG, "dL_dV has %lld frames, the span records %lld", (long long)n_frames, want);
+    if (n_frames > 0 && !dL_dV) return fail(PSST_ERR_INVALID_ARG, "dL_dV is NULL");
+    DeviceGuard guard(h->device);
+    const int n_nets = h->v.n_nets, nt = h->v.n_stypes;
+    cudaError_t e = cudaSuccess;
+    // per-network plan (host copy of the CSR offsets is not kept: read them back once)
+    if (h->adj_K.empty()) {
+        std::vector<int> off((size_t)n_nets + 1);
+        std::vector<long long> rp((size_t)h->v.N + 1);
+        e = cudaMemcpy(off.data(), h->v.net_off, off.size() * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(rp.data(), h->v.row_ptr, rp.size() * sizeof(long long), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint plan");
+        h->adj_K.resize(n_nets);
+        h->adj_items.resize(n_nets);
+        std::vector<long long> slot_off((size_t)n_nets), seg_rows((size_t)n_nets);
+        long long slots = 0;
+        int need = 0;
+        for (int b = 0; b < n_nets; ++b) {
+            const int n0 = off[b], N = off[b + 1] - n0;
+            const long long S = rp[n0 + N] - rp[n0];
+            const int K = (int)std::max(1LL, std::min(8LL, (S / 4 + 511) / 512));
+            int items = 0;
+            for (int i = n0; i < n0 + N; ++i) items += (int)((rp[i + 1] - rp[i] + 4 * K - 1) / (4 * K));
+            if (N >= 65536 || (long long)N * nt >= 65536)
+                return fail(PSST_ERR_UNSUPPORTED, "adjoint: net %d too large (%d neurons)", b, N);
+            const long long bytes = psst::adj_smem_need(N, nt, items, K);
+            if (bytes > h->max_dyn)
+                return fail(PSST_ERR_UNSUPPORTED, "adjoint: net %d needs %lld B of shared memory (max %d)", b, bytes,
+                            h->max_dyn);
+            need = std::max<int>(need, (int)bytes);
+            h->adj_K[b] = K;
+            h->adj_items[b] = items;
+            slot_off[b] = slots;
+            slots += 4LL * K * items;
+        }
+        h->adj_smem = need;
+        e = upload(h, &h->d_adjK, h->adj_K.data(), h->adj_K.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_adjI, h->adj_items.data(), h->adj_items.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_slotoff, slot_off.data(), slot_off.size());
+        if (e == cudaSuccess) e = h->alloc(&h->adj_gslot, (size_t)slots);
+        if (e == cudaSuccess) e = h->alloc(&h->adj_gpn, (size_t)h->v.N * 9);
+        if (e == cudaSuccess) e = h->alloc(&h->adj_gy0, (size_t)h->v.N * 4);
+        if (e == cudaSuccess) e = h->alloc(&h->d_ckoff, (size_t)n_nets);
+        if (e == cudaSuccess) e = h->alloc(&h->d_segoff, (size_t)n_nets);
+        if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint buffers");
+    }
+    // checkpoint and segment storage for this span (grown on demand)
+    {
+        std::vector<int> off((size_t)n_nets + 1);
+        e = cudaMemcpy(off.data(), h->v.net_off, off.size() * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint offsets");
+        const long long nck = (n_steps + ckpt_every - 1) / ckpt_every;
+        std::vector<long long> ck((size_t)n_nets), sg((size_t)n_nets);
+        long long ck_total = 0, seg_total = 0;
+        for (int b = 0; b < n_nets; ++b) {
+            const long long N = off[b + 1] - off[b], R = 4 * N + 2 * N * nt;
+            ck[b] = ck_total;
+            sg[b] = seg_total;
+            ck_total += nck * R;
+            seg_total += (long long)ckpt_every * R;
+        }
+        if (ck_total > h->adj_ck_cap) {
+            e = h->alloc(&h->adj_ckpt, (size_t)ck_total);
+            h->adj_ck_cap = ck_total;
+        }
+        if (e == cudaSuccess && seg_total > h->adj_seg_cap) {
+            e = h->alloc(&h->adj_seg, (size_t)seg_total);
+            h->adj_seg_cap = seg_total;
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_ckoff, ck.data(), ck.size() * sizeof(long long), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_segoff, sg.data(), sg.size() * sizeof(long long), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint storage");
+    }
+    psst::AdjView av{};
+    av.K = h->d_adjK;
+    av.n_items = h->d_adjI;
+    av.ckpt_every = ckpt_every;
+    av.ckpt = h->adj_ckpt;
+    av.ck_off = h->d_ckoff;
+    av.seg = h->adj_seg;
+    av.seg_off = h->d_segoff;
+    av.gslot = h->adj_gslot;
+    av.slot_off = h->d_slotoff;
+    av.dLdV = dL_dV;
+    av.n_frames = (int)n_frames;
+    av.grad_w = grad_w;
+    av.gp_neuron = h->adj_gpn;
+    av.grad_y0 = grad_state0 ? grad_state0 : h->adj_gy0;
+    e = psst::adj_launch(h->v, av, s0, (int)n_steps, h->adj_smem, h->n_ntypes, grad_neuron_params,
+                         (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint launch");
+    h->launches = 2;
     return PSST_OK;
 }
 

@@ -62,6 +62,25 @@ struct GridView {
 enum { NP_C = 0, NP_GNA, NP_GK, NP_GL, NP_ENA, NP_EK, NP_EL, NP_GKL, NP_EKL };
 enum { SP_KIND = 0, SP_A, SP_B, SP_K3, SP_K4, SP_KD, SP_E, SP_VP, SP_KP };
 
+// Device state of one adjoint launch (psst_adjoint): per-network work-item
+// size, checkpoint and segment storage, gradient accumulators, outputs.
+struct AdjView {
+    const int *K;               // [n_nets] chunks per work item
+    const int *n_items;         // [n_nets]
+    int ckpt_every;
+    float *ckpt;                // reduced states every ckpt_every steps
+    const long long *ck_off;    // [n_nets] float offset of each network's checkpoints
+    float *seg;                 // step states of the segment being swept
+    const long long *seg_off;   // [n_nets]
+    float2 *gslot;              // Kahan accumulators of the weight gradients, item-slot order
+    const long long *slot_off;  // [n_nets]
+    const float *dLdV;          // [n_frames][N]
+    int n_frames;
+    float *grad_w;              // [S] output, CSR order
+    double *gp_neuron;          // [N][9] per-neuron parameter gradients
+    float *grad_y0;             // [4][N] output: adjoint of V, m, h, n at the start
+};
+
 #define PSST_MAX_CL 4
 
 // Per-network plan of the CTA/cluster kernel: the rows owned by each CTA of

@@ -311,3 +311,54 @@ def perturbed_params(spec: NetworkSpec, seed: int, rel: float = 0.2) -> NetworkS
     out.neuron_params = tab.astype(np.float32)
     out.name = spec.name + f"[perturbed seed={seed}]"
     return out
+
+
+def differentiated(n_sets: int = 64, seed: int = 5000, n_pn: int = 90, n_ln: int = 30, p: float = 0.5,
+                   w_max=(0.3, 0.6, 0.3), rel: float = 0.2, dt: float = DT):
+    """Parameter sets of the antennal-lobe network with dense weight
+    matrices, for gradients with respect to every entry.
+
+    Every ordered pair (post i, pre j), self pairs included, carries a
+    synapse of the presynaptic neuron's fast type (cholinergic from PNs,
+    GABA_A from LNs) and every (PN post, LN pre) pair a GABA_B synapse; a
+    pair outside the random p-mask has weight 0.  Set q has its own neuron
+    types (2q: PN, 2q+1: LN).  Returns (hidden, start): the hidden parameters
+    theta* (drawn from ``seed``) and the starting point
+    theta0 = theta* (1 + rel U[-1, 1]) (``seed + 1``), as two batches with the
+    same topology, odor pulse and inputs."""
+    rng = np.random.default_rng(seed)
+    n = n_pn + n_ln
+    pn, ln = np.arange(n_pn), np.arange(n_pn, n)
+    parts, on, off = [], [], []
+    tabs = []
+    for q in range(n_sets):
+        post_all = np.repeat(np.arange(n), n)
+        pre_all = np.tile(np.arange(n), n)
+        fast_t = np.where(pre_all < n_pn, 0, 1)
+        w_fast = np.where(rng.random(n * n) < p, rng.uniform(0, 1, n * n), 0.0)
+        w_fast *= np.where(pre_all < n_pn, w_max[0], w_max[1])
+        w_fast[post_all == pre_all] = 0.0
+        bpost = np.repeat(pn, n_ln)
+        bpre = np.tile(ln, n_pn)
+        w_b = np.where(rng.random(bpost.size) < p, rng.uniform(0, w_max[2], bpost.size), 0.0)
+        post = np.concatenate([post_all, bpost])
+        pre = np.concatenate([pre_all, bpre])
+        w = np.concatenate([w_fast, w_b])
+        st = np.concatenate([fast_t, np.full(bpost.size, 2)])
+        rows = _rows_from_edges(n, post, pre, w, st)
+        ntype = np.r_[np.zeros(n_pn), np.ones(n_ln)] + 2 * q
+        i_const = rng.uniform(0.0, 5.0, n)
+        amp = np.zeros(n)
+        stim = rng.permutation(n)[: n // 3]
+        amp[stim] = 10.0 * rng.uniform(0.5, 1.0, stim.size)
+        parts.append(dict(neuron_type=ntype.astype(np.int32), **rows, i_const=i_const.astype(np.float32),
+                          pulse_amp=amp.astype(np.float32)))
+        on.append(int(round(20.0 / dt)))
+        off.append(int(round(150.0 / dt)))
+        tabs.extend([PN, LN])
+    hidden = _concat(parts, neuron_table(*tabs), synapse_table(ACH, GABA_A, GABA_B), on, off, 0, 0, 0.0, dt,
+                     f"differentiated(n_sets={n_sets},seed={seed})")
+    start = perturbed_params(hidden, seed + 1, rel)
+    # a perturbed absent synapse stays absent
+    start.weight = np.where(hidden.weight == 0, 0.0, start.weight).astype(np.float32)
+    return hidden, start

@@ -26,7 +26,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOU
 EXPORTED = ("psst_create_network", "psst_integrate", "psst_status", "psst_get_state",
             "psst_set_state", "psst_set_step", "psst_read_record", "psst_query",
             "psst_destroy_network", "psst_error_string", "psst_last_error",
-            "psst_set_barrier_timeout", "psst_integrate_grid_noalloc")
+            "psst_set_barrier_timeout", "psst_integrate_grid_noalloc", "psst_set_weights",
+            "psst_set_neuron_params", "psst_adjoint")
 
 
 class PsstError(RuntimeError):
@@ -97,6 +98,9 @@ def load(build_if_missing: bool = False):
         lib.psst_set_state.argtypes = [P, P, SZ, I32, P]
         lib.psst_set_step.argtypes = [P, I64]
         lib.psst_set_barrier_timeout.argtypes = [P, I64]
+        lib.psst_set_weights.argtypes = [P, P, SZ, I32, P]
+        lib.psst_set_neuron_params.argtypes = [P, P, SZ, I32, P]
+        lib.psst_adjoint.argtypes = [P, I64, P, I64, C.c_int32, P, P, P, P]
         lib.psst_integrate_grid_noalloc.argtypes = [C.POINTER(DeviceNetwork), I64, I64, P]
         lib.psst_read_record.argtypes = [P, P, SZ, C.POINTER(C.c_int64), I32, P]
         lib.psst_query.argtypes = [P, C.POINTER(Info)]
@@ -176,6 +180,7 @@ class Network:
         self.dim = 4 * self.N + 2 * self.S
         self.rec_stride = rec_stride
         self._cap = int(rec_capacity) if rec_stride > 0 else 0
+        self.n_ntypes = keep["np_"].shape[0]
 
     def __del__(self):
         self.close()
@@ -232,6 +237,39 @@ class Network:
             x = _arr(x, np.float32)
             on_dev, ptr, n = 0, x.ctypes.data, x.size
         _check(load().psst_set_state(self._h, ptr, n, on_dev, _stream_handle(stream)))
+
+    def set_weights(self, w, stream=None):
+        """Synaptic weights [S] from a float32 CUDA tensor or host array."""
+        self._set_table(load().psst_set_weights, w, stream)
+
+    def set_neuron_params(self, p, stream=None):
+        """Neuron-type table [n_types, 9] from a float32 CUDA tensor or host array."""
+        self._set_table(load().psst_set_neuron_params, p, stream)
+
+    def _set_table(self, fn, x, stream):
+        import torch
+        if isinstance(x, torch.Tensor):
+            x = x.detach().contiguous()
+            assert x.dtype == torch.float32
+            _check(fn(self._h, x.data_ptr(), x.numel(), int(x.is_cuda), _stream_handle(stream)))
+        else:
+            x = _arr(x, np.float32)
+            _check(fn(self._h, x.ctypes.data, x.size, 0, _stream_handle(stream)))
+
+    def adjoint(self, n_steps: int, dL_dV, ckpt_every: int = 1000, stream=None):
+        """Gradients (dL/dw [S], dL/dparams [n_types, 9], dL/d(V,m,h,n)_0 [4, N])
+        of L = sum(dL_dV * V(frames)) over the next n_steps steps; dL_dV is a
+        float32 CUDA tensor [frames, N]."""
+        import torch
+        dev = f"cuda:{self.device}"
+        dl = dL_dV.detach().to(device=dev, dtype=torch.float32).contiguous()
+        gw = torch.empty(self.S, dtype=torch.float32, device=dev)
+        gp = torch.empty((self.n_ntypes, 9), dtype=torch.float32, device=dev)
+        gy = torch.empty((4, self.N), dtype=torch.float32, device=dev)
+        _check(load().psst_adjoint(self._h, int(n_steps), dl.data_ptr() if dl.numel() else None,
+                                   dl.shape[0] if dl.dim() == 2 else 0, int(ckpt_every), gw.data_ptr(),
+                                   gp.data_ptr(), gy.data_ptr(), _stream_handle(stream)))
+        return gw, gp, gy
 
     def read_record(self, out=None, stream=None):
         """Recorded V frames [frames, N], oldest first (numpy unless ``out``

@@ -1,0 +1,155 @@
+"""GPU discrete adjoint (psst_adjoint, FP32) against the FP64 oracle's adjoint
+and FP64 central finite differences; the torch.autograd bridge."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1906_03958_gb300 import netgen as ng
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-3
+
+
+def _spec(seed=3, sets=1):
+    hidden, start = ng.differentiated(n_sets=sets, seed=seed, n_pn=12, n_ln=4)
+    for s in (hidden, start):
+        s.pulse_on[:] = 5
+        s.pulse_off[:] = 10_000
+    return hidden, start
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30)
+
+
+def _gpu_adjoint(spec, nsteps, dLdV, stride, ckpt=50, step0=0):
+    import torch
+    from paper_1906_03958_gb300 import psst
+    with psst.Network(spec, rec_stride=stride, rec_capacity=nsteps // stride + 1) as net:
+        net.set_step(step0)
+        gw, gp, gy = net.adjoint(nsteps, torch.from_numpy(dLdV.astype(np.float32)).cuda(), ckpt)
+        net.status()
+        return gw.cpu().numpy(), gp.cpu().numpy(), gy.cpu().numpy()
+
+
+def test_adjoint_matches_oracle_adjoint():
+    _, spec = _spec()
+    rng = np.random.default_rng(0)
+    nsteps, stride = 600, 10
+    g = rng.standard_normal((nsteps // stride, spec.n_neurons))
+    y0 = oracle.rest_state(spec)
+    gy64, gw64, gp64 = oracle.adjoint(spec, y0, nsteps, g, stride, ckpt=100)
+    gw, gp, gy = _gpu_adjoint(spec, nsteps, g, stride)
+    assert _rel(gw, gw64) <= GRAD_TOL
+    assert _rel(gp, gp64) <= GRAD_TOL
+    N = spec.n_neurons
+    assert _rel(gy.ravel(), gy64[:4 * N]) <= GRAD_TOL
+
+
+def test_adjoint_vs_fp64_finite_differences():
+    # 10 random coordinates (weights and conductances), central differences
+    # with h = 1e-6 max(1, |theta|) on the FP64 forward map
+    _, spec = _spec(seed=4)
+    net = oracle.OracleNet(spec)
+    rng = np.random.default_rng(1)
+    nsteps, stride = 500, 5
+    g = rng.standard_normal((nsteps // stride, spec.n_neurons))
+    y0 = oracle.rest_state(net)
+    gw, gp, _ = _gpu_adjoint(spec, nsteps, g, stride)
+
+    def loss():
+        _, rec = oracle.integrate(net, y0, nsteps, rec_stride=stride)
+        return float(np.sum(rec * g))
+
+    def fd(arr, idx):
+        x0 = arr[idx]
+        h = 1e-6 * max(1.0, abs(x0))
+        arr[idx] = x0 + h
+        lp = loss()
+        arr[idx] = x0 - h
+        lm = loss()
+        arr[idx] = x0
+        return (lp - lm) / (2 * h)
+
+    nz = np.nonzero(net.w)[0]
+    coords = [("w", int(k)) for k in rng.choice(nz, 4, replace=False)] + \
+             [("w", int(k)) for k in rng.choice(np.nonzero(net.w == 0)[0], 2, replace=False)]
+    P = net.nparams.reshape(-1, 9)
+    coords += [("p", (0, 1)), ("p", (0, 2)), ("p", (1, 3)), ("p", (1, 7))]
+    scale_w = np.abs(gw).max()
+    for kind, idx in coords:
+        if kind == "w":
+            want, got, scale = fd(net.w, idx), gw[idx], scale_w
+        else:
+            want, got, scale = fd(P, idx), gp[idx], abs(fd(P, idx))
+        assert abs(got - want) <= GRAD_TOL * max(abs(want), 1e-2 * scale), (kind, idx, got, want)
+
+
+def test_adjoint_batch_of_parameter_sets():
+    _, spec = _spec(seed=5, sets=3)
+    rng = np.random.default_rng(2)
+    nsteps, stride = 300, 3
+    g = rng.standard_normal((nsteps // stride, spec.n_neurons))
+    gy64, gw64, gp64 = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, ckpt=64)
+    gw, gp, _ = _gpu_adjoint(spec, nsteps, g, stride, ckpt=64)
+    for b in range(spec.n_nets):
+        s0, s1 = spec.row_ptr[spec.net_neuron_off[b]], spec.row_ptr[spec.net_neuron_off[b + 1]]
+        assert _rel(gw[s0:s1], gw64[s0:s1]) <= GRAD_TOL
+        assert _rel(gp[2 * b:2 * b + 2], gp64[2 * b:2 * b + 2]) <= GRAD_TOL
+
+
+def test_checkpoint_spacing_and_step_offset():
+    _, spec = _spec(seed=6)
+    rng = np.random.default_rng(3)
+    nsteps, stride, step0 = 240, 4, 2
+    frames = (step0 + nsteps) // stride - step0 // stride
+    g = rng.standard_normal((frames, spec.n_neurons))
+    a = _gpu_adjoint(spec, nsteps, g, stride, ckpt=7, step0=step0)
+    b = _gpu_adjoint(spec, nsteps, g, stride, ckpt=240, step0=step0)
+    for x, y in zip(a, b):
+        assert _rel(x, y) <= 1e-5
+    _, gw64, _ = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, step0=step0)
+    assert _rel(a[0], gw64) <= GRAD_TOL
+
+
+def test_nonuniform_gates_are_rejected():
+    from paper_1906_03958_gb300 import psst
+    import torch
+    _, spec = _spec(seed=7)
+    y = oracle.rest_state(spec).astype(np.float32)
+    N = spec.n_neurons
+    y[4 * N + 3] = 0.5  # one gate differs from the other gates of its pair
+    with psst.Network(spec, init_state=y, rec_stride=10, rec_capacity=10) as net:
+        net.adjoint(50, torch.zeros((5, N), device="cuda"), 10)
+        with pytest.raises(psst.PsstError) as ei:
+            net.status()
+        assert ei.value.code == -7
+
+
+def test_autograd_mse_loss():
+    import torch
+    from paper_1906_03958_gb300 import psst
+    from paper_1906_03958_gb300.autograd import trace
+    hidden, start = _spec(seed=8)
+    nsteps = 400
+    N = hidden.n_neurons
+    pn = torch.zeros(N, dtype=torch.bool, device="cuda")
+    pn[:12] = True
+    with psst.Network(hidden, rec_stride=1, rec_capacity=nsteps) as nh:
+        target = trace(nh, torch.from_numpy(hidden.weight).cuda(), torch.from_numpy(hidden.neuron_params).cuda(),
+                       nsteps).detach()
+    with psst.Network(start, rec_stride=1, rec_capacity=nsteps) as net:
+        w = torch.from_numpy(start.weight).cuda().requires_grad_(True)
+        p = torch.from_numpy(start.neuron_params).cuda().requires_grad_(True)
+        v = trace(net, w, p, nsteps)
+        loss = ((v[:, pn] - target[:, pn]) ** 2).mean()
+        loss.backward()
+        assert net.info()["steps_done"] == nsteps
+    dLdV = np.zeros((nsteps, N))
+    diff = (v - target).detach().cpu().numpy()
+    dLdV[:, :12] = 2.0 * diff[:, :12] / (nsteps * 12)
+    _, gw64, gp64 = oracle.adjoint(start, oracle.rest_state(start), nsteps, dLdV, 1)
+    assert _rel(w.grad.cpu().numpy(), gw64) <= GRAD_TOL
+    assert _rel(p.grad.cpu().numpy(), gp64) <= GRAD_TOL
+    assert float(loss.detach()) > 0
