@@ -201,6 +201,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=300)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=20000)
+    ap.add_argument("--ckpt-every", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -313,6 +315,41 @@ def main():
                   "value": al.n_neurons * args.single_steps / (sms / 1e3), "unit": UNIT,
                   "us_per_rk4_step": sms * 1e3 / args.single_steps}
 
+    # ---- differentiated form: adjoint gradient time / forward time
+    adjoint = None
+    if rank == 0 and args.adjoint_steps > 0:
+        from paper_1906_03958_gb300 import netgen as ng
+        hidden, start = ng.differentiated(n_sets=64)
+        T = args.adjoint_steps
+        with psst.Network(start, rec_stride=1, rec_capacity=T) as dn:
+            y0 = dn.get_state().clone()
+            dn.integrate(50)                      # warm-up
+            dn.adjoint(50, torch.zeros((50, start.n_neurons), device="cuda"), 25)
+            torch.cuda.synchronize()
+            dn.set_state(y0)
+            dn.set_step(0)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            dn.integrate(T)
+            e1.record(stream)
+            frames = dn.read_record(out=torch.empty((T, start.n_neurons), device="cuda"))
+            # gradient of a mean-square trace loss over the projection neurons
+            pn = torch.from_numpy(start.neuron_type % 2 == 0).cuda()
+            dldv = torch.where(pn, 2.0 * frames / (T * int(pn.sum())), torch.zeros_like(frames))
+            dn.set_state(y0)
+            dn.set_step(0)
+            torch.cuda.synchronize()
+            e1b = torch.cuda.Event(enable_timing=True)
+            e1b.record(stream)
+            dn.adjoint(T, dldv, args.ckpt_every)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            dn.status()
+            fwd_ms, adj_ms = e0.elapsed_time(e1), e1b.elapsed_time(e2)
+        adjoint = {"workload": f"64 antennal-lobe parameter sets, dense 120x120 W + GABA_B, {T} steps, "
+                               f"checkpoint every {args.ckpt_every}",
+                   "forward_ms": fwd_ms, "adjoint_ms": adj_ms, "ratio": adj_ms / fwd_ms}
+
     # ---- roofline of the dominant kernel (the CTA-resident integrator)
     peaks = measured_peaks()
     smax = peaks.get("sm_max_mhz", 2070.0)
@@ -321,8 +358,8 @@ def main():
     dur = t_local / max(launches, 1)
     roof = {"bound": "alu", "achieved": flops_launch / dur / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": flops_launch / dur / 1e12 / peak_tflops,
-            "traffic": traffic_for("cta_kernel", args.workload),
-            "kernel": "cta_kernel", "peak_source": f"FP32 FMA pipes: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+            "traffic": traffic_for("net_kernel", args.workload),
+            "kernel": "net_kernel (all size classes)", "peak_source": f"FP32 FMA pipes: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                                     f"{smax:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"}
 
     if rank == 0:
@@ -340,7 +377,7 @@ def main():
                           "parallelism": f"replicas x{world}"},
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
-               "single": single, "adjoint_over_forward": None}
+               "single": single, "adjoint_over_forward": adjoint}
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -20,8 +20,8 @@
 //   kb1 = h/6 lam + h/2 Yb2, Yb1 = J(Y1)^T kb1
 //   lam_n = lam + Yb1 + Yb2 + Yb3 + Yb4;  theta_bar += sum_s (df/dtheta)^T kb_s.
 // States are checkpointed every `ckpt` steps in a first forward pass; each
-// segment is recomputed forward (step states kept in global memory), then
-// swept backward, recomputing each step's four stages in shared memory.
+// segment is recomputed forward, keeping every step's four stages in global
+// memory, then swept backward from those stages.
 //
 // Jacobian-transpose product at a stage (q_i = kbV_i / C_i,
 // A_i = sum_k w_k G_p(k), G_p the pair's gate, I_syn = V A - B):
@@ -32,8 +32,9 @@
 //   us_p = -C_p G'(s_p) - K4 kbs_p               [second order]
 //   with the column sum C_p = sum_{k in p} w_k (q_i V_i - q_i E_k);
 //   dL/dw_k += -q_i G_p (V_i - E_k);  dL/dgNa += -q_i m^3 h (V - ENa), ...
-// The column sums use shared-memory atomics (their order is not fixed); the
-// weight gradients are accumulated with Kahan compensation.
+// The column sums use shared-memory atomics (their order is not fixed).  The
+// weight gradients are summed over each step's four stages in one pass, into
+// an FP32 partial per segment, then into an FP64 total.
 #include <cuda_runtime.h>
 
 #include "psst_device.cuh"
@@ -43,7 +44,7 @@ namespace psst {
 
 namespace {
 
-constexpr int ADJ_THREADS = 512;
+constexpr int ADJ_THREADS = 1024;
 
 __device__ __forceinline__ float ratio_u_deriv(float u) {
     // d/du of u / (1 - e^{-u}); Bernoulli series near 0
@@ -71,10 +72,11 @@ struct AdjSmem {
     float *acc;                // [4N + 2M]
     // adjoint
     float *lam, *yprev, *ysum; // [4N + 2M]
-    float2 *ab;                // [N]: q_i V_i, q_i
+    float2 *ab;                // [4][N]: q_i V_i, q_i at each stage
     float *csum;               // [M]
     float *uV;                 // [N] partial uV
     double *gp;                // [N][9] neuron parameter gradients
+    float *Ep;                 // [M] reversal potential of each pair's type
     float *prm;                // [9][N] (row 0: 1/C)
     float *iext, *inp;         // [N], [2][N]
 };
@@ -87,9 +89,10 @@ __host__ __device__ inline long long adj_smem_bytes(int N, int M, int n_items, i
     b += 4LL * (N + 1);
     b += 4LL * 4 * (6LL * N + 3LL * M);  // stage storage
     b += 4LL * 5 * (4LL * N + 2LL * M);  // y, acc, lam, yprev, ysum
-    b += 8LL * N + 4LL * M + 4LL * N;     // ab, csum, uV
+    b += 32LL * N + 4LL * M + 4LL * N;    // ab, csum, uV
     b += 8LL * 9 * N;                    // gp (double)
     b += 4LL * 9 * N + 4LL * 3 * N;      // prm, iext, inp
+    b += 4LL * M;                        // Ep
     b += 16 * 32;                        // alignment slack
     return b;
 }
@@ -149,10 +152,10 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
                 A = fmaf(w.y, g1, A);
                 A = fmaf(w.z, g2, A);
                 A = fmaf(w.w, g3, A);
-                B = fmaf(w.x * stab[(id.x % nt) * 9 + SP_E], g0, B);
-                B = fmaf(w.y * stab[(id.y % nt) * 9 + SP_E], g1, B);
-                B = fmaf(w.z * stab[(id.z % nt) * 9 + SP_E], g2, B);
-                B = fmaf(w.w * stab[(id.w % nt) * 9 + SP_E], g3, B);
+                B = fmaf(w.x * S.Ep[id.x], g0, B);
+                B = fmaf(w.y * S.Ep[id.y], g1, B);
+                B = fmaf(w.z * S.Ep[id.z], g2, B);
+                B = fmaf(w.w * S.Ep[id.w], g3, B);
             }
             S.pa[it] = A;
             S.pb[it] = B;
@@ -229,7 +232,7 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
 
 // Reverse of the step whose stages fwd_step<true> just stored: lam holds the
 // adjoint of y_{n+1} on entry and of y_n on exit (before the frame term).
-__device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, float dt, float2 *gslot) {
+__device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, float dt, float4 *gpart) {
     const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M, K = a.K, ni = a.n_items;
     const int D = 4 * N + 2 * M;
     const float cb[4] = {dt / 6.0f, dt / 3.0f, dt / 3.0f, dt / 6.0f};  // h b_s
@@ -248,7 +251,7 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, f
             const float *P = S.prm;
             const float invC = P[NP_C * N + i];
             const float q = kb[0] * invC;
-            S.ab[i] = make_float2(q * Vs, q);
+            S.ab[st * N + i] = make_float2(q * Vs, q);
             const Rates rt = hh_rates(Vs);
             const float dam = 0.1f * ratio_u_deriv((Vs + 40.0f) * 0.1f), dbm = -rt.bm * (1.0f / 18.0f);
             const float dah = -rt.ah * (1.0f / 20.0f), dbh = rt.bh * (1.0f - rt.bh) * 0.1f;
@@ -277,10 +280,9 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, f
             g[NP_EKL] += (double)(q * gKL);
         }
         __syncthreads();
-        // B) items: column sums C_p and weight gradients
-        const float *G = S.sG + st * M;
+        // B) items: column sums C_p = sum_k w_k (q_i V_i - q_i E_k)
         for (int it = tid; it < ni; it += nthr) {
-            const float2 abv = S.ab[S.irow[it]];
+            const float2 abv = S.ab[st * N + S.irow[it]];
             for (int j = 0; j < K; ++j) {
                 const int c = j * ni + it;
                 const float4 w = S.w[c];
@@ -288,19 +290,8 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, f
                 const float wv[4] = {w.x, w.y, w.z, w.w};
                 const int iv[4] = {id.x, id.y, id.z, id.w};
 #pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    const int p = iv[q4];
-                    const float E = stab[(p % nt) * 9 + SP_E];
-                    const float x = fmaf(-E, abv.y, abv.x);  // q V - q E
-                    if (wv[q4] != 0.0f) atomicAdd(&S.csum[p], wv[q4] * x);
-                    // Kahan: slot += -G x
-                    float2 k2 = gslot[c * 4 + q4];
-                    const float yv = -G[p] * x - k2.y;
-                    const float t = k2.x + yv;
-                    k2.y = (t - k2.x) - yv;
-                    k2.x = t;
-                    gslot[c * 4 + q4] = k2;
-                }
+                for (int q4 = 0; q4 < 4; ++q4)
+                    if (wv[q4] != 0.0f) atomicAdd(&S.csum[iv[q4]], wv[q4] * fmaf(-S.Ep[iv[q4]], abv.y, abv.x));
             }
         }
         __syncthreads();
@@ -342,6 +333,28 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, f
         }
         // the next stage's part A reads only owner-written values; its part B
         // reads ab after the barrier that follows part A
+    }
+    // weight gradients of the step: dL/dw_k += sum_s -G_p^(s) q_i^(s) (V_i^(s) - E_k),
+    // into the per-segment FP32 partial of each item slot
+    for (int c = tid; c < K * ni; c += nthr) {
+        const int i = S.irow[c % ni];
+        const ushort4 id = S.id[c];
+        const int iv[4] = {id.x, id.y, id.z, id.w};
+        float4 g = gpart[c];
+        float gv[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+            const int p = iv[q4];
+            const float E = S.Ep[p];
+            float acc = 0.0f;
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                const float2 abv = S.ab[st * N + i];
+                acc = fmaf(S.sG[st * M + p], fmaf(E, abv.y, -abv.x), acc);
+            }
+            gv[q4] += acc;
+        }
+        gpart[c] = make_float4(gv[0], gv[1], gv[2], gv[3]);
     }
     // lam_n = lam + sum of the stage adjoints (owner-only values)
     for (int i = tid; i < N; i += nthr) {
@@ -410,10 +423,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     S.lam = (float *)take(p, 4LL * a.R);
     S.yprev = (float *)take(p, 4LL * a.R);
     S.ysum = (float *)take(p, 4LL * a.R);
-    S.ab = (float2 *)take(p, 8LL * N);
+    S.ab = (float2 *)take(p, 32LL * N);
     S.csum = (float *)take(p, 4LL * M);
     S.uV = (float *)take(p, 4LL * N);
     S.gp = (double *)take(p, 72LL * N);
+    S.Ep = (float *)take(p, 4LL * M);
     S.prm = (float *)take(p, 36LL * N);
     S.iext = (float *)take(p, 4LL * N);
     S.inp = (float *)take(p, 8LL * N);
@@ -436,6 +450,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         S.uV[i] = 0.0f;
     }
     for (int q = tid; q < M; q += nthr) {
+        S.Ep[q] = stab[(q % nt) * 9 + SP_E];
         S.y[4 * N + q] = 0.0f;
         S.y[4 * N + M + q] = 0.0f;
         S.csum[q] = 0.0f;
@@ -494,11 +509,16 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         return;
     }
 
+    // the four stages' arrays form one contiguous block (sV .. sfv)
+    const int stage_floats = 4 * (6 * N + 3 * M);
+    float4 *stage_blk = (float4 *)S.sV;
     // pass 1: checkpoints every ckpt steps
     float *ck = av.ckpt + av.ck_off[a.b];
     float *seg = av.seg + av.seg_off[a.b];
-    float2 *gslot = av.gslot + av.slot_off[a.b];
-    for (long long c = tid; c < slots * 4; c += nthr) gslot[c] = make_float2(0.0f, 0.0f);
+    float4 *gpart = av.gpart + av.slot_off[a.b] / 4;
+    double *gtot = av.gtot + av.slot_off[a.b];
+    for (long long c = tid; c < slots; c += nthr) gpart[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (long long c = tid; c < slots * 4; c += nthr) gtot[c] = 0.0;
     const int ckpt = av.ckpt_every;
     const float dt = v.dt;
     for (int n = 0; n < nsteps; ++n) {
@@ -521,22 +541,34 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         const int k0 = c * ckpt, k1 = min(k0 + ckpt, nsteps);
         for (int q = tid; q < a.R; q += nthr) S.y[q] = ck[(long long)c * a.R + q];
         __syncthreads();
+        // recompute the segment, keeping every step's four stages in global memory
         for (int n = k0; n < k1; ++n) {
-            for (int q = tid; q < a.R; q += nthr) seg[(long long)(n - k0) * a.R + q] = S.y[q];
-            if (n + 1 < k1) fwd_step<false>(v, a, S, stab, step0 + n, dt);
-        }
-        __syncthreads();
-        for (int n = k1 - 1; n >= k0; --n) {
-            for (int q = tid; q < a.R; q += nthr) S.y[q] = seg[(long long)(n - k0) * a.R + q];
-            __syncthreads();
             fwd_step<true>(v, a, S, stab, step0 + n, dt);
-            rev_step(a, S, stab, dt, gslot);
+            float4 *dst = (float4 *)(seg + (long long)(n - k0) * stage_floats);
+            for (int q = tid; q < stage_floats / 4; q += nthr) dst[q] = stage_blk[q];
+            __syncthreads();
+        }
+        for (int n = k1 - 1; n >= k0; --n) {
+            const float4 *src = (const float4 *)(seg + (long long)(n - k0) * stage_floats);
+            for (int q = tid; q < stage_floats / 4; q += nthr) stage_blk[q] = src[q];
+            __syncthreads();
+            rev_step(a, S, stab, dt, gpart);
             if (stride > 0 && n > 0 && (step0 + n) % stride == 0 && frame >= 0) {
                 for (int i = tid; i < N; i += nthr) S.lam[i] += dl[(long long)frame * v.N + a.n0 + i];
                 --frame;
             }
             __syncthreads();
         }
+        // fold the segment's partial sums into the FP64 totals
+        for (long long q = tid; q < slots; q += nthr) {
+            const float4 g = gpart[q];
+            gtot[4 * q] += g.x;
+            gtot[4 * q + 1] += g.y;
+            gtot[4 * q + 2] += g.z;
+            gtot[4 * q + 3] += g.w;
+            gpart[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        __syncthreads();
     }
     // outputs: weight gradients in CSR order, neuron parameter partials
     for (int i = tid; i < N; i += nthr) {
@@ -545,8 +577,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
             const int m = (int)(k - k0);
             const int t = S.ib[i] + m / (4 * K), j = (m % (4 * K)) >> 2;
             const long long slot = ((long long)j * ni + t) * 4 + (m & 3);
-            const float2 g2 = gslot[slot];
-            av.grad_w[a.sbase + k] = g2.x - g2.y;
+            av.grad_w[a.sbase + k] = (float)gtot[slot];
         }
         for (int x = 0; x < 9; ++x) av.gp_neuron[(long long)(a.n0 + i) * 9 + x] = S.gp[9 * i + x];
         for (int x = 0; x < 4; ++x) av.grad_y0[(long long)x * v.N + a.n0 + i] = S.lam[x * N + i];

@@ -70,7 +70,8 @@ struct psst_net {
     int *d_adjK = nullptr, *d_adjI = nullptr;
     long long *d_ckoff = nullptr, *d_segoff = nullptr, *d_slotoff = nullptr;
     float *adj_ckpt = nullptr, *adj_seg = nullptr, *adj_gy0 = nullptr;
-    float2 *adj_gslot = nullptr;
+    float4 *adj_gpart = nullptr;
+    double *adj_gtot = nullptr;
     double *adj_gpn = nullptr;
     long long adj_ck_cap = 0, adj_seg_cap = 0;
     int adj_ckpt_every = 0;
@@ -750,7 +751,7 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         for (int b = 0; b < n_nets; ++b) {
             const int n0 = off[b], N = off[b + 1] - n0;
             const long long S = rp[n0 + N] - rp[n0];
-            const int K = (int)std::max(1LL, std::min(8LL, (S / 4 + 511) / 512));
+            const int K = (int)std::max(1LL, std::min(8LL, (S / 4 + 1023) / 1024));
             int items = 0;
             for (int i = n0; i < n0 + N; ++i) items += (int)((rp[i + 1] - rp[i] + 4 * K - 1) / (4 * K));
             if (N >= 65536 || (long long)N * nt >= 65536)
@@ -769,7 +770,8 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         e = upload(h, &h->d_adjK, h->adj_K.data(), h->adj_K.size());
         if (e == cudaSuccess) e = upload(h, &h->d_adjI, h->adj_items.data(), h->adj_items.size());
         if (e == cudaSuccess) e = upload(h, &h->d_slotoff, slot_off.data(), slot_off.size());
-        if (e == cudaSuccess) e = h->alloc(&h->adj_gslot, (size_t)slots);
+        if (e == cudaSuccess) e = h->alloc(&h->adj_gpart, (size_t)slots / 4);
+        if (e == cudaSuccess) e = h->alloc(&h->adj_gtot, (size_t)slots);
         if (e == cudaSuccess) e = h->alloc(&h->adj_gpn, (size_t)h->v.N * 9);
         if (e == cudaSuccess) e = h->alloc(&h->adj_gy0, (size_t)h->v.N * 4);
         if (e == cudaSuccess) e = h->alloc(&h->d_ckoff, (size_t)n_nets);
@@ -786,10 +788,11 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         long long ck_total = 0, seg_total = 0;
         for (int b = 0; b < n_nets; ++b) {
             const long long N = off[b + 1] - off[b], R = 4 * N + 2 * N * nt;
+            const long long stage_floats = 4 * (6 * N + 3 * N * nt);  // four stages of one step
             ck[b] = ck_total;
             sg[b] = seg_total;
             ck_total += nck * R;
-            seg_total += (long long)ckpt_every * R;
+            seg_total += (long long)std::min<long long>(ckpt_every, n_steps) * stage_floats;
         }
         if (ck_total > h->adj_ck_cap) {
             e = h->alloc(&h->adj_ckpt, (size_t)ck_total);
@@ -811,7 +814,8 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
     av.ck_off = h->d_ckoff;
     av.seg = h->adj_seg;
     av.seg_off = h->d_segoff;
-    av.gslot = h->adj_gslot;
+    av.gpart = h->adj_gpart;
+    av.gtot = h->adj_gtot;
     av.slot_off = h->d_slotoff;
     av.dLdV = dL_dV;
     av.n_frames = (int)n_frames;

@@ -72,8 +72,9 @@ struct AdjView {
     const long long *ck_off;    // [n_nets] float offset of each network's checkpoints
     float *seg;                 // step states of the segment being swept
     const long long *seg_off;   // [n_nets]
-    float2 *gslot;              // Kahan accumulators of the weight gradients, item-slot order
-    const long long *slot_off;  // [n_nets]
+    float4 *gpart;              // per-segment FP32 partial weight gradients, item-slot order (4 per chunk)
+    double *gtot;               // FP64 totals, item-slot order
+    const long long *slot_off;  // [n_nets] slot offset of each network (multiple of 4)
     const float *dLdV;          // [n_frames][N]
     int n_frames;
     float *grad_w;              // [S] output, CSR order
