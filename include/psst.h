@@ -178,6 +178,15 @@ int psst_read_record(const psst_net *h, float *dst, size_t cap_frames, int64_t *
 int psst_set_weights(psst_net *h, const float *w, size_t n, int on_device, void *stream);
 int psst_set_neuron_params(psst_net *h, const float *p, size_t n, int on_device, void *stream);
 
+/* Record checkpoints for the adjoint: while every > 0, each psst_integrate
+   call (of at most max_steps steps) stores the full state at its start and
+   after every `every` steps, so that psst_adjoint(..., ckpt_every = 0) can
+   differentiate that call's span without its own checkpointing pass.  The
+   recorded span is invalidated by set_state, set_step, set_weights and
+   set_neuron_params.  every = 0 stops recording.  CTA mode only.  The buffer
+   (ceil(max_steps / every) full states) is allocated here. */
+int psst_record_checkpoints(psst_net *h, int32_t every, int64_t max_steps);
+
 /* Discrete adjoint of the RK4 map (no counterpart in the paper; the
    differentiated form).  For the n_steps steps that a psst_integrate call
    made now would take -- from the current state and step index -- computes
@@ -192,6 +201,9 @@ int psst_set_neuron_params(psst_net *h, const float *p, size_t n, int on_device,
    The state and step index are left unchanged.  Memory: reduced states are
    checkpointed every ckpt_every steps and each segment is recomputed;
    the handle allocates the storage on first use and grows it as needed.
+   ckpt_every = 0 differentiates instead the span of the last psst_integrate
+   call, whose checkpoints were recorded (psst_record_checkpoints); n_steps
+   must equal that call's; PSST_ERR_STATE if no such checkpoints exist.
    Preconditions: CTA mode; every network fits one CTA for the adjoint; all
    gates of a (presynaptic neuron, synapse type) pair hold the same value at
    the start (true from rest), else the device reports PSST_ERR_UNSUPPORTED

@@ -16,7 +16,10 @@ class PsstTrace(torch.autograd.Function):
     ``weight`` [S] and ``neuron_params`` [n_types, 9] are float32 CUDA
     tensors written into the network before integrating; gradients flow back
     to both.  The network's state advances by ``n_steps`` (as after
-    psst_integrate)."""
+    psst_integrate).  If the network records checkpoints
+    (``net.record_checkpoints``), backward differentiates the recorded span
+    directly; otherwise it re-runs the adjoint's own checkpointing pass from
+    the saved starting state."""
 
     @staticmethod
     def forward(ctx, weight, neuron_params, net, n_steps: int, ckpt_every: int = 1000):
@@ -42,6 +45,11 @@ class PsstTrace(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_frames):
         net = ctx.net
+        if net.recording_checkpoints:
+            # the forward call recorded its checkpoints: differentiate its span directly
+            gw, gp, _ = net.adjoint(ctx.n, grad_frames.contiguous(), 0)
+            net.status()
+            return gw, gp.reshape(ctx.pshape), None, None, None
         y_end = net.get_state().clone()
         s_end = net.info()["steps_done"]
         net.set_state(ctx.y0)

@@ -375,6 +375,37 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, f
     __syncthreads();
 }
 
+// Reduced state of the network from a full state [V, m, h, n, r, s] of the
+// whole batch: neurons as they are, each pair's gates from its synapses
+// (all equal by the precondition; *bad, if given, is set when they differ).
+__device__ void load_reduced(const NetView &v, const AdjNet &a, const AdjSmem &S, const float *full,
+                             const long long *rp, const uint32_t *gcode, int *bad) {
+    const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, M = a.M;
+    const float *gr = full + 4 * v.N + a.sbase, *gs = full + 4 * v.N + v.S + a.sbase;
+    for (int i = tid; i < N; i += nthr)
+        for (int x = 0; x < 4; ++x) S.y[x * N + i] = full[(long long)x * v.N + a.n0 + i];
+    for (int q = tid; q < M; q += nthr) {
+        S.y[4 * N + q] = 0.0f;
+        S.y[4 * N + M + q] = 0.0f;
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += nthr)
+        for (long long k = rp[i] - a.sbase; k < rp[i + 1] - a.sbase; ++k) {
+            const int ci = (int)(gcode[k] & 0xFFFFFFu);
+            S.y[4 * N + ci] = gr[k];
+            S.y[4 * N + M + ci] = gs[k];
+        }
+    __syncthreads();
+    if (bad) {
+        for (int i = tid; i < N; i += nthr)
+            for (long long k = rp[i] - a.sbase; k < rp[i + 1] - a.sbase; ++k) {
+                const int ci = (int)(gcode[k] & 0xFFFFFFu);
+                if (S.y[4 * N + ci] != gr[k] || S.y[4 * N + M + ci] != gs[k]) *bad = 1;
+            }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av, long long step0, int nsteps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float stab[PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM];
@@ -435,12 +466,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     const long long *rp = v.row_ptr + a.n0;
     const uint32_t *gcode = v.syn_code + a.sbase;
     const float *gw = v.weight + a.sbase;
-    const float *gr = v.state + 4 * v.N + a.sbase;
-    const float *gs = v.state + 4 * v.N + v.S + a.sbase;
 
     // neurons, parameters, inputs; initial reduced state
     for (int i = tid; i < N; i += nthr) {
-        for (int x = 0; x < 4; ++x) S.y[x * N + i] = v.state[(long long)x * v.N + a.n0 + i];
         const float *pp = v.nparams + (long long)v.neuron_type[a.n0 + i] * PSST_NEURON_NPARAM;
         S.prm[NP_C * N + i] = 1.0f / pp[NP_C];
         for (int x = 1; x < PSST_NEURON_NPARAM; ++x) S.prm[x * N + i] = pp[x];
@@ -451,8 +479,6 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     }
     for (int q = tid; q < M; q += nthr) {
         S.Ep[q] = stab[(q % nt) * 9 + SP_E];
-        S.y[4 * N + q] = 0.0f;
-        S.y[4 * N + M + q] = 0.0f;
         S.csum[q] = 0.0f;
     }
     for (int q = tid; q < a.R; q += nthr) {
@@ -489,21 +515,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
             const int t = S.ib[i] + m / (4 * K), j = (m % (4 * K)) >> 2;
             const long long slot = ((long long)j * ni + t) * 4 + (m & 3);
             W[slot] = gw[k];
-            const int ci = (int)(gcode[k] & 0xFFFFFFu);
-            ID[slot] = (unsigned short)ci;
-            // pair gate from its synapses (all equal by the precondition)
-            S.y[4 * N + ci] = gr[k];
-            S.y[4 * N + M + ci] = gs[k];
+            ID[slot] = (unsigned short)(gcode[k] & 0xFFFFFFu);
         }
     }
     __syncthreads();
-    for (int i = tid; i < N; i += nthr) {
-        for (long long k = rp[i] - a.sbase; k < rp[i + 1] - a.sbase; ++k) {
-            const int ci = (int)(gcode[k] & 0xFFFFFFu);
-            if (S.y[4 * N + ci] != gr[k] || S.y[4 * N + M + ci] != gs[k]) s_bad = 1;
-        }
-    }
-    __syncthreads();
+    // starting state (reduced), checked for equal gates within each pair
+    const float *full0 = av.ck_full ? av.ck_full : v.state;
+    load_reduced(v, a, S, full0, rp, gcode, &s_bad);
     if (s_bad) {
         if (tid == 0) set_error(v.err, PSST_ERR_UNSUPPORTED);
         return;
@@ -521,10 +539,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     for (long long c = tid; c < slots * 4; c += nthr) gtot[c] = 0.0;
     const int ckpt = av.ckpt_every;
     const float dt = v.dt;
-    for (int n = 0; n < nsteps; ++n) {
-        if (n % ckpt == 0)
-            for (int q = tid; q < a.R; q += nthr) ck[(long long)(n / ckpt) * a.R + q] = S.y[q];
-        fwd_step<false>(v, a, S, stab, step0 + n, dt);
+    if (!av.ck_full) {
+        for (int n = 0; n < nsteps; ++n) {
+            if (n % ckpt == 0)
+                for (int q = tid; q < a.R; q += nthr) ck[(long long)(n / ckpt) * a.R + q] = S.y[q];
+            fwd_step<false>(v, a, S, stab, step0 + n, dt);
+        }
     }
     // frames: global steps k in (step0, step0 + nsteps] with k % stride == 0
     const int stride = v.rec_stride;
@@ -539,8 +559,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     const int nseg = (nsteps + ckpt - 1) / ckpt;
     for (int c = nseg - 1; c >= 0; --c) {
         const int k0 = c * ckpt, k1 = min(k0 + ckpt, nsteps);
-        for (int q = tid; q < a.R; q += nthr) S.y[q] = ck[(long long)c * a.R + q];
-        __syncthreads();
+        if (av.ck_full) {
+            load_reduced(v, a, S, av.ck_full + (long long)c * av.dim, rp, gcode, nullptr);
+        } else {
+            for (int q = tid; q < a.R; q += nthr) S.y[q] = ck[(long long)c * a.R + q];
+            __syncthreads();
+        }
         // recompute the segment, keeping every step's four stages in global memory
         for (int n = k0; n < k1; ++n) {
             fwd_step<true>(v, a, S, stab, step0 + n, dt);

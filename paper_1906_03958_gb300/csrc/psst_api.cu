@@ -75,6 +75,11 @@ struct psst_net {
     double *adj_gpn = nullptr;
     long long adj_ck_cap = 0, adj_seg_cap = 0;
     int adj_ckpt_every = 0;
+    // checkpoints recorded by psst_integrate for a later psst_adjoint
+    int rec_ck_every = 0;
+    long long rec_ck_cap_steps = 0, rec_ck_start = 0, rec_ck_nsteps = 0;
+    bool rec_ck_valid = false;
+    float *rec_ck = nullptr;
 
     template <class T>
     cudaError_t alloc(T **p, size_t count) {
@@ -586,6 +591,31 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
     return PSST_OK;
 }
 
+namespace {
+
+// Launch the kernels for n_steps steps starting at global step `step0`.
+int launch_steps(psst_net *h, long long step0, long long n_steps, cudaStream_t st) {
+    const long long chunk = 1LL << 30;
+    for (long long done = 0; done < n_steps;) {
+        const int n = (int)std::min<long long>(chunk, n_steps - done);
+        if (h->mode == PSST_MODE_GRID) {
+            cudaError_t e = psst::grid_launch(h->v, h->gv, step0 + done, n, h->grid, h->block, h->smem, st);
+            if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
+            ++h->launches;
+        } else {
+            for (const psst::ClassLaunch &c : h->classes) {
+                cudaError_t e = psst::cta_launch(h->v, c, step0 + done, n, st);
+                if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
+                ++h->launches;
+            }
+        }
+        done += n;
+    }
+    return PSST_OK;
+}
+
+}  // namespace
+
 int psst_integrate(psst_net *h, int64_t n_steps, void *stream) {
     if (!h) return fail(PSST_ERR_INVALID_ARG, "handle is NULL");
     if (n_steps < 0) return fail(PSST_ERR_INVALID_ARG, "n_steps must be >= 0");
@@ -593,23 +623,52 @@ int psst_integrate(psst_net *h, int64_t n_steps, void *stream) {
     if (n_steps == 0) return PSST_OK;
     DeviceGuard guard(h->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const long long chunk = 1LL << 30;
-    for (long long done = 0; done < n_steps;) {
-        const int n = (int)std::min<long long>(chunk, n_steps - done);
-        if (h->mode == PSST_MODE_GRID) {
-            cudaError_t e = psst::grid_launch(h->v, h->gv, h->step + done, n, h->grid, h->block, h->smem, st);
-            if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
-            ++h->launches;
-        } else {
-            for (const psst::ClassLaunch &c : h->classes) {
-                cudaError_t e = psst::cta_launch(h->v, c, h->step + done, n, st);
-                if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
-                ++h->launches;
-            }
-        }
+    if (h->rec_ck_every <= 0) {
+        const int rc = launch_steps(h, h->step, n_steps, st);
+        if (rc) return rc;
+        h->step += n_steps;
+        return PSST_OK;
+    }
+    // recording checkpoints: the state at the start and after every rec_ck_every steps
+    if (n_steps > h->rec_ck_cap_steps)
+        return fail(PSST_ERR_INVALID_ARG, "n_steps %lld exceeds the checkpoint capacity %lld", (long long)n_steps,
+                    h->rec_ck_cap_steps);
+    const size_t dim = (size_t)(4 * h->v.N + 2 * h->v.S);
+    h->rec_ck_valid = false;
+    const long long s0 = h->step;
+    for (long long done = 0, c = 0; done < n_steps; ++c) {
+        cudaError_t e = cudaMemcpyAsync(h->rec_ck + c * dim, h->v.state, dim * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
+        const long long n = std::min<long long>(h->rec_ck_every, n_steps - done);
+        const int rc = launch_steps(h, s0 + done, n, st);
+        if (rc) return rc;
         done += n;
     }
     h->step += n_steps;
+    h->rec_ck_start = s0;
+    h->rec_ck_nsteps = n_steps;
+    h->rec_ck_valid = true;
+    return PSST_OK;
+}
+
+int psst_record_checkpoints(psst_net *h, int32_t every, int64_t max_steps) {
+    if (!h) return fail(PSST_ERR_INVALID_ARG, "handle is NULL");
+    if (every < 0 || (every > 0 && max_steps < 1)) return fail(PSST_ERR_INVALID_ARG, "bad checkpoint spacing");
+    if (h->mode != PSST_MODE_CTA && every > 0) return fail(PSST_ERR_UNSUPPORTED, "checkpoints need CTA mode");
+    h->rec_ck_valid = false;
+    h->rec_ck_every = every;
+    if (every == 0) return PSST_OK;
+    const long long need = ((max_steps + every - 1) / every) * (4 * h->v.N + 2 * h->v.S);
+    if (max_steps > h->rec_ck_cap_steps || !h->rec_ck) {
+        DeviceGuard guard(h->device);
+        cudaError_t e = h->alloc(&h->rec_ck, (size_t)need);
+        if (e != cudaSuccess) {
+            h->rec_ck_every = 0;
+            return cuda_fail(e, "checkpoint buffer");
+        }
+    }
+    h->rec_ck_cap_steps = std::max<long long>(h->rec_ck_cap_steps, max_steps);
     return PSST_OK;
 }
 
@@ -646,6 +705,7 @@ int psst_get_state(const psst_net *h, float *dst, size_t n, int dst_on_device, v
 }
 
 int psst_set_state(psst_net *h, const float *src, size_t n, int src_on_device, void *stream) {
+    if (h) h->rec_ck_valid = false;
     if (!h || !src) return fail(PSST_ERR_INVALID_ARG, "NULL argument");
     const size_t dim = (size_t)(4 * h->v.N + 2 * h->v.S);
     if (n != dim) return fail(PSST_ERR_INVALID_ARG, "src holds %zu floats, state has %zu", n, dim);
@@ -662,6 +722,7 @@ int psst_set_step(psst_net *h, int64_t step) {
     if (step < 0) return fail(PSST_ERR_INVALID_ARG, "step must be >= 0");
     h->step = step;
     h->rec_reset = step;
+    h->rec_ck_valid = false;
     return PSST_OK;
 }
 
@@ -698,6 +759,7 @@ int psst_read_record(const psst_net *h, float *dst, size_t cap_frames, int64_t *
 }
 
 int psst_set_weights(psst_net *h, const float *w, size_t n, int on_device, void *stream) {
+    if (h) h->rec_ck_valid = false;
     if (!h || !w) return fail(PSST_ERR_INVALID_ARG, "NULL argument");
     if (n != (size_t)h->v.S) return fail(PSST_ERR_INVALID_ARG, "weights hold %zu values, network has %lld", n, h->v.S);
     DeviceGuard guard(h->device);
@@ -709,6 +771,7 @@ int psst_set_weights(psst_net *h, const float *w, size_t n, int on_device, void 
 }
 
 int psst_set_neuron_params(psst_net *h, const float *p, size_t n, int on_device, void *stream) {
+    if (h) h->rec_ck_valid = false;
     if (!h || !p) return fail(PSST_ERR_INVALID_ARG, "NULL argument");
     if (n != (size_t)h->n_ntypes * PSST_NEURON_NPARAM)
         return fail(PSST_ERR_INVALID_ARG, "parameter table holds %zu values, expected %d", n,
@@ -726,8 +789,14 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
     if (!h || !grad_w || !grad_neuron_params) return fail(PSST_ERR_INVALID_ARG, "NULL argument");
     if (h->mode != PSST_MODE_CTA) return fail(PSST_ERR_UNSUPPORTED, "the adjoint runs in CTA mode only");
     if (n_steps < 1 || n_steps > (1LL << 30)) return fail(PSST_ERR_INVALID_ARG, "n_steps must be in 1..2^30");
-    if (ckpt_every < 1) return fail(PSST_ERR_INVALID_ARG, "ckpt_every must be >= 1");
-    const long long stride = h->v.rec_stride, s0 = h->step;
+    const bool recorded = ckpt_every == 0;
+    if (recorded) {
+        if (!h->rec_ck_valid || h->rec_ck_nsteps != n_steps)
+            return fail(PSST_ERR_STATE, "no checkpoints of a %lld-step integrate call are recorded", (long long)n_steps);
+        ckpt_every = h->rec_ck_every;
+    }
+    if (ckpt_every < 1) return fail(PSST_ERR_INVALID_ARG, "ckpt_every must be >= 1 (0 = recorded)");
+    const long long stride = h->v.rec_stride, s0 = recorded ? h->rec_ck_start : h->step;
     long long want = 0;
     if (stride > 0) want = (s0 + n_steps) / stride - s0 / stride;
     if (n_frames != want)
@@ -810,6 +879,8 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
     av.K = h->d_adjK;
     av.n_items = h->d_adjI;
     av.ckpt_every = ckpt_every;
+    av.ck_full = recorded ? h->rec_ck : nullptr;
+    av.dim = 4 * h->v.N + 2 * h->v.S;
     av.ckpt = h->adj_ckpt;
     av.ck_off = h->d_ckoff;
     av.seg = h->adj_seg;

@@ -68,7 +68,9 @@ struct AdjView {
     const int *K;               // [n_nets] chunks per work item
     const int *n_items;         // [n_nets]
     int ckpt_every;
-    float *ckpt;                // reduced states every ckpt_every steps
+    const float *ck_full;       // full states [4N+2S] every ckpt_every steps recorded by psst_integrate, or null
+    long long dim;              // 4N + 2S
+    float *ckpt;                // reduced states every ckpt_every steps (when ck_full is null)
     const long long *ck_off;    // [n_nets] float offset of each network's checkpoints
     float *seg;                 // step states of the segment being swept
     const long long *seg_off;   // [n_nets]

@@ -27,7 +27,7 @@ EXPORTED = ("psst_create_network", "psst_integrate", "psst_status", "psst_get_st
             "psst_set_state", "psst_set_step", "psst_read_record", "psst_query",
             "psst_destroy_network", "psst_error_string", "psst_last_error",
             "psst_set_barrier_timeout", "psst_integrate_grid_noalloc", "psst_set_weights",
-            "psst_set_neuron_params", "psst_adjoint")
+            "psst_set_neuron_params", "psst_adjoint", "psst_record_checkpoints")
 
 
 class PsstError(RuntimeError):
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = False):
         lib.psst_set_weights.argtypes = [P, P, SZ, I32, P]
         lib.psst_set_neuron_params.argtypes = [P, P, SZ, I32, P]
         lib.psst_adjoint.argtypes = [P, I64, P, I64, C.c_int32, P, P, P, P]
+        lib.psst_record_checkpoints.argtypes = [P, C.c_int32, I64]
         lib.psst_integrate_grid_noalloc.argtypes = [C.POINTER(DeviceNetwork), I64, I64, P]
         lib.psst_read_record.argtypes = [P, P, SZ, C.POINTER(C.c_int64), I32, P]
         lib.psst_query.argtypes = [P, C.POINTER(Info)]
@@ -181,6 +182,7 @@ class Network:
         self.rec_stride = rec_stride
         self._cap = int(rec_capacity) if rec_stride > 0 else 0
         self.n_ntypes = keep["np_"].shape[0]
+        self.recording_checkpoints = False
 
     def __del__(self):
         self.close()
@@ -255,6 +257,11 @@ class Network:
         else:
             x = _arr(x, np.float32)
             _check(fn(self._h, x.ctypes.data, x.size, 0, _stream_handle(stream)))
+
+    def record_checkpoints(self, every: int, max_steps: int):
+        """Have later integrate calls store checkpoints for adjoint(..., ckpt_every=0)."""
+        _check(load().psst_record_checkpoints(self._h, int(every), int(max_steps)))
+        self.recording_checkpoints = every > 0
 
     def adjoint(self, n_steps: int, dL_dV, ckpt_every: int = 1000, stream=None):
         """Gradients (dL/dw [S], dL/dparams [n_types, 9], dL/d(V,m,h,n)_0 [4, N])

@@ -153,3 +153,44 @@ def test_autograd_mse_loss():
     assert _rel(w.grad.cpu().numpy(), gw64) <= GRAD_TOL
     assert _rel(p.grad.cpu().numpy(), gp64) <= GRAD_TOL
     assert float(loss.detach()) > 0
+
+
+def test_recorded_checkpoints_match_own_checkpoints():
+    import torch
+    from paper_1906_03958_gb300 import psst
+    _, spec = _spec(seed=9, sets=2)
+    rng = np.random.default_rng(4)
+    nsteps, stride, ck = 300, 5, 64
+    g = torch.from_numpy(rng.standard_normal((nsteps // stride, spec.n_neurons)).astype(np.float32)).cuda()
+    with psst.Network(spec, rec_stride=stride, rec_capacity=nsteps // stride) as net:
+        own = net.adjoint(nsteps, g, ck)
+        net.record_checkpoints(ck, nsteps)
+        net.integrate(nsteps)
+        rec = net.adjoint(nsteps, g, 0)
+        net.status()
+        for a, b in zip(own, rec):
+            assert _rel(b.cpu().numpy(), a.cpu().numpy()) <= 1e-5
+        net.set_state(net.get_state())  # invalidates the recorded span
+        with pytest.raises(psst.PsstError) as ei:
+            net.adjoint(nsteps, g, 0)
+        assert ei.value.code == -6
+
+
+def test_autograd_with_recorded_checkpoints():
+    import torch
+    from paper_1906_03958_gb300 import psst
+    from paper_1906_03958_gb300.autograd import trace
+    _, spec = _spec(seed=10)
+    nsteps = 200
+    out = []
+    for record in (False, True):
+        with psst.Network(spec, rec_stride=2, rec_capacity=nsteps // 2) as net:
+            if record:
+                net.record_checkpoints(50, nsteps)
+            w = torch.from_numpy(spec.weight).cuda().requires_grad_(True)
+            p = torch.from_numpy(spec.neuron_params).cuda().requires_grad_(True)
+            v = trace(net, w, p, nsteps, ckpt_every=50)
+            (v ** 2).mean().backward()
+            out.append((w.grad.cpu().numpy(), p.grad.cpu().numpy()))
+    assert _rel(out[1][0], out[0][0]) <= 1e-5
+    assert _rel(out[1][1], out[0][1]) <= 1e-5
