@@ -184,7 +184,25 @@ def make_workload(name: str, rank: int):
             "antennal lobe: 90 PN + 30 LN, ACh/GABA_A/GABA_B, 1000 ms, dt 0.01 ms", 100000
     if name == "plain20":
         return ng.plain20(seed=1001 + rank), "plain: 20 HH neurons, p=0.5, 100 ms, dt 0.01 ms", 10000
+    if name == "sparse_large":
+        return ng.sparse_large(seed=1003 + rank), \
+            "large sparse: 8000 E + 2000 I HH neurons, p=0.02 (~2M synapses), Philox shot noise, 500 ms", 50000
+    if name == "differentiated":
+        return ng.differentiated(n_sets=64, seed=5000 + 64 * rank)[1], \
+            "differentiated forward: 64 antennal-lobe parameter sets, dense 120x120 W + GABA_B, 200 ms", 20000
     raise SystemExit(f"unknown workload {name}")
+
+
+def reduce_over_ranks(t_local: float, neurons_local: float, device):
+    """Job-wide timing under weak scaling: the slowest rank's time and the
+    neurons of all ranks (no collective touches the integration itself)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    n = torch.tensor([neurons_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
 
 
 def main():
@@ -202,6 +220,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=20000)
+    ap.add_argument("--sparse-steps", type=int, default=2000)
     ap.add_argument("--ckpt-every", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -264,13 +283,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     t_local = ms / 1e3
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_local], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        n = torch.tensor([float(spec.n_neurons)], device="cuda")
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        total_neurons = float(n.item())
+        t_max, total_neurons = reduce_over_ranks(t_local, float(spec.n_neurons), "cuda")
     else:
         t_max, total_neurons = t_local, float(spec.n_neurons)
     value = total_neurons * args.chunk * args.steps / t_max
@@ -314,6 +327,28 @@ def main():
         single = {"workload": "antennal lobe, 120 neurons, one network per launch",
                   "value": al.n_neurons * args.single_steps / (sms / 1e3), "unit": UNIT,
                   "us_per_rk4_step": sms * 1e3 / args.single_steps}
+
+    # ---- the large sparse network (one network over the whole GPU)
+    sparse = None
+    if rank == 0 and args.sparse_steps > 0:
+        from paper_1906_03958_gb300 import netgen as ng
+        sp = ng.sparse_large()
+        with psst.Network(sp) as sn:
+            sn.integrate(200)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sn.integrate(args.sparse_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sn.status()
+            sinfo = sn.info()
+            sms = e0.elapsed_time(e1)
+        sparse = {"workload": "10,000 HH neurons (8k E, 2k I), p=0.02, ~2M synapses, Philox shot noise, "
+                              f"grid mode over {sinfo['grid_ctas']} CTAs",
+                  "value": sp.n_neurons * args.sparse_steps / (sms / 1e3), "unit": UNIT,
+                  "us_per_rk4_step": sms * 1e3 / args.sparse_steps,
+                  "synapse_steps_per_s": sp.n_synapses * args.sparse_steps / (sms / 1e3)}
 
     # ---- differentiated form: adjoint gradient time / forward time
     adjoint = None
@@ -376,7 +411,7 @@ def main():
                           "parallelism": f"replicas x{world}"},
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
-               "single": single, "adjoint_over_forward": adjoint}
+               "single": single, "sparse_large": sparse, "adjoint_over_forward": adjoint}
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
