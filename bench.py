@@ -221,6 +221,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=20000)
     ap.add_argument("--sparse-steps", type=int, default=2000)
+    ap.add_argument("--autotune", type=int, default=200, help="trial steps per shape (0 = off)")
+    ap.add_argument("--graph", type=int, default=1, help="CUDA-graph replay of the launch sequence")
     ap.add_argument("--ckpt-every", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -261,6 +263,10 @@ def main():
     psst.load()
     frames = args.chunk // args.rec_stride if args.rec_stride else 0
     net = psst.Network(spec, rec_stride=args.rec_stride, rec_capacity=max(frames, 1))
+    if args.autotune > 0:
+        net.autotune(args.autotune)       # per size class CTA size (setup, not timed)
+    if args.graph:
+        net.set_graph_mode(True)          # replay the class launches through a CUDA graph
     info = net.info()
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -408,6 +414,7 @@ def main():
                           "grid_ctas": info["grid_ctas"], "smem_bytes": info["smem_bytes"],
                           "single_cta_nets": info["n_single_cta_nets"], "cluster_nets": info["n_cluster_nets"],
                           "launch_classes": info["n_launch_classes"],
+                          "autotune_trial_steps": args.autotune, "cuda_graph": bool(args.graph),
                           "parallelism": f"replicas x{world}"},
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,

@@ -148,6 +148,22 @@ int psst_integrate(psst_net *h, int64_t n_steps, void *stream);
    exercise the error path without a hang). */
 int psst_set_barrier_timeout(psst_net *h, int64_t timeout_ns);
 
+/* Replay psst_integrate's launch sequence through a CUDA graph (the
+   paper's Sec. "Circumventing memory constraints" item 3: run a compiled
+   static graph instead of issuing operations eagerly).  While enabled, the
+   first call for a given n_steps captures the launches into a graph; later
+   calls with the same n_steps replay it with the step index updated.
+   Results are bitwise identical to direct launches.  Not combined with
+   checkpoint recording (those calls launch directly). */
+int psst_set_graph_mode(psst_net *h, int enable);
+
+/* Autotuner: for each size class of a CTA-mode handle, time trial_steps
+   steps with the class's largest CTA size and its halves (from a copy of
+   the state, recording off; the state is restored) and keep the fastest.
+   The summation order does not depend on the CTA size, so results stay
+   bitwise identical.  Synchronises `stream`.  Grid mode: no-op. */
+int psst_autotune(psst_net *h, int64_t trial_steps, void *stream);
+
 /* Synchronise `stream` and return the device error word (0 if none), then
    clear it. */
 int psst_status(psst_net *h, void *stream);

@@ -80,6 +80,21 @@ struct psst_net {
     long long rec_ck_cap_steps = 0, rec_ck_start = 0, rec_ck_nsteps = 0;
     bool rec_ck_valid = false;
     float *rec_ck = nullptr;
+    // CUDA-graph replay of one integrate chunk
+    bool graph_mode = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_nsteps = 0;
+    int graph_launches = 0;
+    float *tune_buf = nullptr;  // state copy for autotuning trials
+
+    void drop_graph() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        graph_exec = nullptr;
+        graph = nullptr;
+        graph_nsteps = 0;
+    }
 
     template <class T>
     cudaError_t alloc(T **p, size_t count) {
@@ -90,6 +105,7 @@ struct psst_net {
         return e;
     }
     void release() {
+        drop_graph();
         for (void *p : allocs) cudaFree(p);
         allocs.clear();
     }
@@ -614,7 +630,142 @@ int launch_steps(psst_net *h, long long step0, long long n_steps, cudaStream_t s
     return PSST_OK;
 }
 
+// Kernel nodes take the global step index as an argument: net_kernel's 4th
+// (v, list, plans, step0, nsteps), grid_kernel's 3rd (v, g, step0, nsteps).
+int patch_step0(psst_net *h, long long step0) {
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetNodes(h->graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n) e = cudaGraphGetNodes(h->graph, nodes.data(), &n);
+    long long chunk_base = 0;
+    const long long chunk = 1LL << 30;
+    int k = 0;
+    for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[i], &t);
+        if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams p;
+        e = cudaGraphKernelNodeGetParams(nodes[i], &p);
+        if (e != cudaSuccess) break;
+        const int idx = h->mode == PSST_MODE_GRID ? 2 : 3;
+        const int nargs = h->mode == PSST_MODE_GRID ? 4 : 5;
+        // launches of one chunk share step0; chunks follow in capture order
+        const int per_chunk = h->mode == PSST_MODE_GRID ? 1 : (int)h->classes.size();
+        chunk_base = (long long)(k / per_chunk) * chunk;
+        long long s = step0 + chunk_base;
+        void *args[5];
+        for (int q = 0; q < nargs; ++q) args[q] = p.kernelParams[q];
+        args[idx] = &s;
+        p.kernelParams = args;
+        e = cudaGraphExecKernelNodeSetParams(h->graph_exec, nodes[i], &p);
+        ++k;
+    }
+    return e == cudaSuccess ? PSST_OK : cuda_fail(e, "graph update");
+}
+
+// Integrate through a CUDA graph of the launch sequence: captured once per
+// step count, then replayed with the step index patched into its kernels.
+int replay_steps(psst_net *h, long long step0, long long n_steps, cudaStream_t st) {
+    if (!h->graph_exec || h->graph_nsteps != n_steps) {
+        h->drop_graph();
+        cudaStream_t cs;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "graph stream");
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        int rc = PSST_OK;
+        if (e == cudaSuccess) rc = launch_steps(h, step0, n_steps, cs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(e, "graph capture");
+        }
+        h->graph = g;
+        h->graph_nsteps = n_steps;
+        h->graph_launches = h->launches;
+    } else {
+        const int rc = patch_step0(h, step0);
+        if (rc) return rc;
+    }
+    h->launches = h->graph_launches;
+    const cudaError_t e = cudaGraphLaunch(h->graph_exec, st);
+    return e == cudaSuccess ? PSST_OK : cuda_fail(e, "graph launch");
+}
+
 }  // namespace
+
+int psst_set_graph_mode(psst_net *h, int enable) {
+    if (!h) return fail(PSST_ERR_INVALID_ARG, "handle is NULL");
+    DeviceGuard guard(h->device);
+    h->graph_mode = enable != 0;
+    if (!enable) h->drop_graph();
+    return PSST_OK;
+}
+
+int psst_autotune(psst_net *h, int64_t trial_steps, void *stream) {
+    if (!h) return fail(PSST_ERR_INVALID_ARG, "handle is NULL");
+    if (trial_steps < 1) return fail(PSST_ERR_INVALID_ARG, "trial_steps must be >= 1");
+    if (h->mode != PSST_MODE_CTA) return PSST_OK;  // grid mode has one shape per device
+    DeviceGuard guard(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t dim = (size_t)(4 * h->v.N + 2 * h->v.S);
+    cudaError_t e = cudaSuccess;
+    if (!h->tune_buf) e = h->alloc(&h->tune_buf, dim);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->tune_buf, h->v.state, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    // the record ring may be written by trial steps: trials run with recording off
+    const int stride = h->v.rec_stride;
+    h->v.rec_stride = 0;
+    for (size_t ci = 0; e == cudaSuccess && ci < h->classes.size(); ++ci) {
+        psst::ClassLaunch &c = h->classes[ci];
+        // the class's CTAs per SM are fixed by its shared memory and its
+        // largest CTA keeps 1024 threads per SM (64 registers each); the
+        // trials try that size and its halves
+        const int base = c.block;
+        float best = 1e30f;
+        int best_block = base;
+        for (int b = base; b >= 64 && b >= base / 4; b /= 2) {
+            if (b % 32) continue;
+            psst::ClassLaunch t = c;
+            t.block = b;
+            const int n = (int)std::min<long long>(trial_steps, 1 << 20);
+            e = psst::cta_launch(h->v, t, 0, n, st);  // warm-up
+            if (e != cudaSuccess) {
+                cudaGetLastError();  // a shape that cannot launch is skipped
+                e = cudaSuccess;
+                continue;
+            }
+            cudaEventRecord(ev0, st);
+            e = psst::cta_launch(h->v, t, 0, n, st);
+            cudaEventRecord(ev1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                best_block = b;
+            }
+        }
+        c.block = best_block;
+    }
+    h->v.rec_stride = stride;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->v.state, h->tune_buf, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    h->drop_graph();
+    if (!h->classes.empty()) h->block = h->classes.back().block;
+    return e == cudaSuccess ? PSST_OK : cuda_fail(e, "psst_autotune");
+}
 
 int psst_integrate(psst_net *h, int64_t n_steps, void *stream) {
     if (!h) return fail(PSST_ERR_INVALID_ARG, "handle is NULL");
@@ -624,7 +775,7 @@ int psst_integrate(psst_net *h, int64_t n_steps, void *stream) {
     DeviceGuard guard(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (h->rec_ck_every <= 0) {
-        const int rc = launch_steps(h, h->step, n_steps, st);
+        const int rc = h->graph_mode ? replay_steps(h, h->step, n_steps, st) : launch_steps(h, h->step, n_steps, st);
         if (rc) return rc;
         h->step += n_steps;
         return PSST_OK;

@@ -27,7 +27,8 @@ EXPORTED = ("psst_create_network", "psst_integrate", "psst_status", "psst_get_st
             "psst_set_state", "psst_set_step", "psst_read_record", "psst_query",
             "psst_destroy_network", "psst_error_string", "psst_last_error",
             "psst_set_barrier_timeout", "psst_integrate_grid_noalloc", "psst_set_weights",
-            "psst_set_neuron_params", "psst_adjoint", "psst_record_checkpoints")
+            "psst_set_neuron_params", "psst_adjoint", "psst_record_checkpoints",
+            "psst_set_graph_mode", "psst_autotune")
 
 
 class PsstError(RuntimeError):
@@ -102,6 +103,8 @@ def load(build_if_missing: bool = False):
         lib.psst_set_neuron_params.argtypes = [P, P, SZ, I32, P]
         lib.psst_adjoint.argtypes = [P, I64, P, I64, C.c_int32, P, P, P, P]
         lib.psst_record_checkpoints.argtypes = [P, C.c_int32, I64]
+        lib.psst_set_graph_mode.argtypes = [P, I32]
+        lib.psst_autotune.argtypes = [P, I64, P]
         lib.psst_integrate_grid_noalloc.argtypes = [C.POINTER(DeviceNetwork), I64, I64, P]
         lib.psst_read_record.argtypes = [P, P, SZ, C.POINTER(C.c_int64), I32, P]
         lib.psst_query.argtypes = [P, C.POINTER(Info)]
@@ -208,6 +211,14 @@ class Network:
 
     def set_step(self, step: int):
         _check(load().psst_set_step(self._h, int(step)))
+
+    def set_graph_mode(self, enable: bool = True):
+        """Replay the integrate launch sequence through a captured CUDA graph."""
+        _check(load().psst_set_graph_mode(self._h, int(bool(enable))))
+
+    def autotune(self, trial_steps: int = 200, stream=None):
+        """Pick each size class's CTA size by timed trials (results unchanged)."""
+        _check(load().psst_autotune(self._h, int(trial_steps), _stream_handle(stream)))
 
     def set_barrier_timeout(self, ns: int):
         _check(load().psst_set_barrier_timeout(self._h, int(ns)))

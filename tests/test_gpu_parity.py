@@ -284,3 +284,30 @@ def test_nonfinite_state_is_reported():
             net.status()
         assert ei.value.code == -4
         net.status()  # cleared after being read
+
+
+def test_graph_replay_bitwise_equal_to_direct_launches():
+    spec = ng.concat_specs([ng.antennal_lobe(seed=51), ng.antennal_lobe(seed=52, n_pn=30, n_ln=10)])
+    y0 = oracle.rest_state(spec).astype(np.float32)
+    with _net(spec, init_state=y0, rec_stride=10, rec_capacity=100) as a, \
+            _net(spec, init_state=y0, rec_stride=10, rec_capacity=100) as b:
+        a.set_step(9950), b.set_step(9950)
+        b.set_graph_mode(True)
+        a.integrate(300)
+        for _ in range(3):
+            b.integrate(100)  # captured once, replayed twice with new step indices
+        a.status(), b.status()
+        np.testing.assert_array_equal(a.get_state_numpy(), b.get_state_numpy())
+        np.testing.assert_array_equal(a.read_record(), b.read_record())
+
+
+def test_autotune_keeps_results_bitwise():
+    spec = ng.batched(n_nets=24, base_seed=700, n_min=20, n_max=300)
+    y0 = oracle.rest_state(spec).astype(np.float32)
+    with _net(spec, init_state=y0, item_chunks=2) as a, _net(spec, init_state=y0, item_chunks=2) as b:
+        b.autotune(50)
+        np.testing.assert_array_equal(b.get_state_numpy(), y0)  # state restored
+        a.integrate(200)
+        b.integrate(200)
+        a.status(), b.status()
+        np.testing.assert_array_equal(a.get_state_numpy(), b.get_state_numpy())
