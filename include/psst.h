@@ -108,6 +108,9 @@ typedef struct {
     int32_t block_threads;         /* CTA size (multiple of 32, <= 1024), 0 = tuned */
     int32_t item_chunks;           /* 4-synapse chunks per work item of the synaptic sum (1..64), 0 = tuned */
     int32_t device;                /* CUDA device ordinal, -1 = current device */
+    int32_t gate_mode;             /* 0: one gate per (presynaptic neuron, type) pair whenever all
+                                      its synapses' gates are equal (bitwise-identical results,
+                                      less work), else one per synapse; 1: always one per synapse */
 } psst_network_desc;
 
 typedef struct {

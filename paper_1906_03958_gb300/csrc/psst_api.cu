@@ -50,8 +50,25 @@ void rest_gates(double V, double out[3]) {
 
 }  // namespace
 
+struct SmemCaps {
+    int max_dyn;   // largest dynamic shared memory of one CTA
+    int per_sm;    // shared memory of one SM
+    int per_cta;   // per-CTA overhead: static shared memory + reserved
+};
+
+// What the CTA-mode planner needs, kept so that it can run again when the
+// gate uniformity of a network changes (psst_set_state).
+struct PlanInput {
+    int n_nets = 0, nt = 0, user_K = 0, user_block = 0;
+    bool force_synapse_gates = false;
+    std::vector<int> net_off, n1, n2;
+    std::vector<long long> net_syn;
+    std::vector<uint8_t> flags;  // NET_HAS2 | NET_PAIR per network
+};
+
 struct psst_net {
     int device = 0;
+    PlanInput pin;
     NetView v{};
     psst::GridView gv{};
     std::vector<psst::ClassLaunch> classes;  // CTA mode: one launch per size class
@@ -64,6 +81,7 @@ struct psst_net {
     int launches = 0;
     int n_ntypes = 0;
     int max_dyn = 0;
+    SmemCaps caps{};
     // adjoint plan and scratch (allocated on the first psst_adjoint)
     std::vector<int> adj_K, adj_items;
     int adj_smem = 0;
@@ -87,6 +105,7 @@ struct psst_net {
     long long graph_nsteps = 0;
     int graph_launches = 0;
     float *tune_buf = nullptr;  // state copy for autotuning trials
+    uint8_t *d_check = nullptr; // per-network result of the pair-uniformity check
 
     void drop_graph() {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -205,6 +224,7 @@ int validate(const psst_network_desc *d) {
             if (!std::isfinite(d->init_state[i])) return fail(PSST_ERR_INVALID_ARG, "init_state[%lld] not finite", i);
     }
     if (d->mode < PSST_MODE_AUTO || d->mode > PSST_MODE_GRID) return fail(PSST_ERR_INVALID_ARG, "unknown mode");
+    if (d->gate_mode < 0 || d->gate_mode > 1) return fail(PSST_ERR_INVALID_ARG, "gate_mode must be 0 or 1");
     return PSST_OK;
 }
 
@@ -246,11 +266,6 @@ void balanced_split(const std::vector<double> &cost, int parts, std::vector<int>
     }
 }
 
-struct SmemCaps {
-    int max_dyn;   // largest dynamic shared memory of one CTA
-    int per_sm;    // shared memory of one SM
-    int per_cta;   // per-CTA overhead: static shared memory + reserved
-};
 
 int smem_caps(int dev, SmemCaps *c) {
     int optin = 0, per_sm = 0, reserved = 0;
@@ -304,22 +319,24 @@ void make_shares(const int *n1, const int *n2, int n, int parts, int user_K, std
 }
 
 // Dynamic shared memory of one CTA of a network of N neurons in CTA mode.
-long long cta_share_bytes(int N, int nt, bool has2, const Share &s, int K) {
-    const psst::NeuronLayout L = psst::make_nlayout(s.r1 - s.r0, N, N * nt, has2);
-    return L.syn + psst::items_smem_bytes(s.items1, s.items2, K, s.r1 - s.r0, has2);
+long long cta_share_bytes(int N, int nt, bool has2, bool pair, const Share &s, int K) {
+    const psst::NeuronLayout L = psst::make_nlayout(s.r1 - s.r0, N, N * nt, has2, pair);
+    return L.syn + (pair ? psst::items_smem_bytes_pair(s.items1, s.items2, K, s.r1 - s.r0)
+                         : psst::items_smem_bytes(s.items1, s.items2, K, s.r1 - s.r0, has2));
 }
 
 // Smallest cluster size (1, 2, 4) whose CTAs all fit; 0 if none.
-int plan_network(const psst_network_desc *d, int b, const std::vector<int> &n1, const std::vector<int> &n2,
-                 bool has2, const SmemCaps &caps, psst::NetPlan *pl, long long *need) {
-    const int n0 = d->net_neuron_off[b], N = d->net_neuron_off[b + 1] - n0, nt = d->n_syn_types;
+int plan_network(const PlanInput &in, int b, const SmemCaps &caps, psst::NetPlan *pl, long long *need) {
+    const int n0 = in.net_off[b], N = in.net_off[b + 1] - n0, nt = in.nt;
+    const bool has2 = in.flags[b] & psst::NET_HAS2, pair = in.flags[b] & psst::NET_PAIR;
+    const std::vector<int> &n1 = in.n1, &n2 = in.n2;
     for (int cl = 1; cl <= PSST_MAX_CL; cl *= 2) {
         if (cl > 1 && N < 2 * cl) break;
         std::vector<Share> sh;
         int K = 1;
-        make_shares(n1.data() + n0, n2.data() + n0, N, cl, d->item_chunks, sh, &K);
+        make_shares(n1.data() + n0, n2.data() + n0, N, cl, in.user_K, sh, &K);
         long long worst = 0;
-        for (int q = 0; q < cl; ++q) worst = std::max(worst, cta_share_bytes(N, nt, has2, sh[q], K));
+        for (int q = 0; q < cl; ++q) worst = std::max(worst, cta_share_bytes(N, nt, has2, pair, sh[q], K));
         if (worst <= caps.max_dyn) {
             std::memset(pl, 0, sizeof *pl);
             pl->K = K;
@@ -334,6 +351,32 @@ int plan_network(const psst_network_desc *d, int b, const std::vector<int> &n1, 
         }
     }
     return 0;
+}
+
+// Per network: do all gates of each (presynaptic neuron, type) pair hold the
+// same value in the state y ([V, m, h, n, r, s], host memory; NULL = rest,
+// all gates 0)?
+std::vector<uint8_t> uniform_pairs(const float *y, const PlanInput &in, const int64_t *row_ptr, const int32_t *pre,
+                                   const int32_t *syn_type, long long N, long long S) {
+    std::vector<uint8_t> ok((size_t)in.n_nets, 1);
+    if (!y) return ok;
+    const float *r = y + 4 * N, *s = y + 4 * N + S;
+    for (int b = 0; b < in.n_nets; ++b) {
+        const int n0 = in.net_off[b], nb = in.net_off[b + 1] - n0;
+        std::vector<float> rr((size_t)nb * in.nt), ss((size_t)nb * in.nt);
+        std::vector<uint8_t> seen((size_t)nb * in.nt, 0);
+        for (long long k = row_ptr[n0]; k < row_ptr[n0 + nb] && ok[b]; ++k) {
+            const size_t p = (size_t)pre[k] * in.nt + syn_type[k];
+            if (!seen[p]) {
+                seen[p] = 1;
+                rr[p] = r[k];
+                ss[p] = s[k];
+            } else if (std::memcmp(&rr[p], &r[k], 4) || std::memcmp(&ss[p], &s[k], 4)) {
+                ok[b] = 0;
+            }
+        }
+    }
+    return ok;
 }
 
 // Grid mode: one contiguous block of rows per CTA with balanced cost, the
@@ -392,21 +435,24 @@ int setup_grid(psst_net *h, const psst_network_desc *d, const SmemCaps &caps, bo
 
 // CTA mode: each network's cluster size and work items, size classes by
 // cluster size x CTAs per SM, launch lists (largest networks first).
-int setup_cta(psst_net *h, const psst_network_desc *d, const SmemCaps &caps, const std::vector<int> &n1,
-              const std::vector<int> &n2, const std::vector<uint8_t> &has2, cudaError_t *err) {
-    const int n_nets = d->n_nets, nt = d->n_syn_types;
+int setup_cta(psst_net *h, const SmemCaps &caps, cudaError_t *err) {
+    const PlanInput &in = h->pin;
+    const int n_nets = in.n_nets, nt = in.nt;
+    const std::vector<int> &n1 = in.n1, &n2 = in.n2;
+    h->classes.clear();
+    h->n_smem = h->n_global = 0;
     std::vector<psst::NetPlan> plans((size_t)n_nets);
     std::vector<int> cl_of((size_t)n_nets), per_sm((size_t)n_nets);
     std::vector<long long> need((size_t)n_nets);
     std::vector<double> cost((size_t)n_nets);
     for (int b = 0; b < n_nets; ++b) {
-        const int n0 = d->net_neuron_off[b], N = d->net_neuron_off[b + 1] - n0;
+        const int n0 = in.net_off[b], N = in.net_off[b + 1] - n0;
         if ((long long)N * nt >= 65536)
             return fail(PSST_ERR_UNSUPPORTED, "net %d: %d neurons x %d synapse types must stay below 65536", b, N, nt);
-        const int cl = plan_network(d, b, n1, n2, has2[b], caps, &plans[b], &need[b]);
+        const int cl = plan_network(in, b, caps, &plans[b], &need[b]);
         if (!cl)
             return fail(PSST_ERR_UNSUPPORTED, "net %d (%d neurons, %lld synapses) does not fit %d CTAs", b, N,
-                        (long long)(d->row_ptr[n0 + N] - d->row_ptr[n0]), PSST_MAX_CL);
+                        in.net_syn[b], PSST_MAX_CL);
         cl_of[b] = cl;
         per_sm[b] = (int)std::max(1LL, std::min(4LL, (long long)caps.per_sm / (need[b] + caps.per_cta)));
         double c = 0;
@@ -428,7 +474,7 @@ int setup_cta(psst_net *h, const psst_network_desc *d, const SmemCaps &caps, con
             long long mx = 0;
             for (int b : list) mx = std::max(mx, need[b]);
             c.smem = (int)mx;
-            c.block = d->block_threads ? d->block_threads : ((1024 / k) / 32) * 32;
+            c.block = in.user_block ? in.user_block : ((1024 / k) / 32) * 32;
             ranges.push_back({(int)all_lists.size(), (int)list.size()});
             all_lists.insert(all_lists.end(), list.begin(), list.end());
             h->classes.push_back(c);
@@ -492,14 +538,31 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
     rc = smem_caps(dev, &caps);
     if (rc) return rc;
 
-    std::vector<int> n1, n2;
+    PlanInput pin;
+    pin.n_nets = n_nets;
+    pin.nt = nt;
+    pin.user_K = d->item_chunks;
+    pin.user_block = d->block_threads;
+    pin.force_synapse_gates = d->gate_mode == 1;
+    pin.net_off.assign(d->net_neuron_off, d->net_neuron_off + n_nets + 1);
+    pin.net_syn.resize(n_nets);
+    for (int b = 0; b < n_nets; ++b)
+        pin.net_syn[b] = d->row_ptr[d->net_neuron_off[b + 1]] - d->row_ptr[d->net_neuron_off[b]];
     std::vector<uint8_t> has2;
-    row_counts(d, n1, n2, has2);
+    row_counts(d, pin.n1, pin.n2, has2);
+    const std::vector<int> &n1 = pin.n1, &n2 = pin.n2;
+    pin.flags.assign(n_nets, 0);
+    {
+        const std::vector<uint8_t> uni = uniform_pairs(d->init_state, pin, d->row_ptr, d->pre, d->syn_type, N, S);
+        for (int b = 0; b < n_nets; ++b)
+            pin.flags[b] = (has2[b] ? psst::NET_HAS2 : 0) |
+                           (uni[b] && !pin.force_synapse_gates ? psst::NET_PAIR : 0);
+    }
     bool all_fit = true;
     for (int b = 0; b < n_nets && all_fit; ++b) {
         psst::NetPlan pl;
         long long need = 0;
-        all_fit = plan_network(d, b, n1, n2, has2[b], caps, &pl, &need) != 0;
+        all_fit = plan_network(pin, b, caps, &pl, &need) != 0;
     }
     int mode = d->mode;
     if (mode == PSST_MODE_AUTO) mode = all_fit ? PSST_MODE_CTA : PSST_MODE_GRID;
@@ -509,6 +572,7 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
     psst_net *h = new psst_net();
     h->device = dev;
     h->mode = mode;
+    h->pin = pin;
     h->n_ntypes = d->n_neuron_types;
     h->max_dyn = caps.max_dyn;
     h->block = d->block_threads;
@@ -554,7 +618,7 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
         if (d->pulse_amp) UP(p_pa, d->pulse_amp, N);
         UP(p_on, pon.data(), n_nets);
         UP(p_offp, poff.data(), n_nets);
-        UP(p_fl, has2.data(), n_nets);
+        UP(p_fl, pin.flags.data(), n_nets);
         v.net_off = p_off;
         v.row_ptr = p_rp;
         v.syn_code = p_code;
@@ -596,8 +660,8 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
         delete h;
         return cuda_fail(e, "psst_create_network");
     }
-    rc = mode == PSST_MODE_GRID ? setup_grid(h, d, caps, has2[0] != 0, n1, n2, &e)
-                                : setup_cta(h, d, caps, n1, n2, has2, &e);
+    h->caps = caps;
+    rc = mode == PSST_MODE_GRID ? setup_grid(h, d, caps, has2[0] != 0, n1, n2, &e) : setup_cta(h, caps, &e);
     if (rc) {
         h->release();
         delete h;
@@ -697,6 +761,41 @@ int replay_steps(psst_net *h, long long step0, long long n_steps, cudaStream_t s
     h->launches = h->graph_launches;
     const cudaError_t e = cudaGraphLaunch(h->graph_exec, st);
     return e == cudaSuccess ? PSST_OK : cuda_fail(e, "graph launch");
+}
+
+// After the state was replaced: which networks now have equal gates within
+// every (presynaptic neuron, type) pair?  When that changes, the CTA-mode
+// plan (per-pair or per-synapse layout) is rebuilt.
+int recheck_pairs(psst_net *h, cudaStream_t st) {
+    if (h->mode != PSST_MODE_CTA || h->pin.force_synapse_gates) return PSST_OK;
+    const int n_nets = h->pin.n_nets;
+    if (!h->d_check) {
+        cudaError_t e = h->alloc(&h->d_check, (size_t)n_nets);
+        if (e != cudaSuccess) return cuda_fail(e, "pair check buffer");
+    }
+    int max_m = 0;
+    for (int b = 0; b < n_nets; ++b) max_m = std::max(max_m, (h->pin.net_off[b + 1] - h->pin.net_off[b]) * h->pin.nt);
+    std::vector<uint8_t> ok((size_t)n_nets, 0);
+    if (4LL * max_m <= 200 * 1024) {
+        cudaError_t e = psst::pair_check(h->v, h->d_check, 4 * max_m, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ok.data(), h->d_check, (size_t)n_nets, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "pair check");
+    }
+    bool changed = false;
+    for (int b = 0; b < n_nets; ++b) {
+        const uint8_t f = (uint8_t)((h->pin.flags[b] & psst::NET_HAS2) | (ok[b] ? psst::NET_PAIR : 0));
+        changed |= f != h->pin.flags[b];
+        h->pin.flags[b] = f;
+    }
+    if (!changed) return PSST_OK;
+    cudaError_t e = cudaMemcpy((void *)h->v.net_flags, h->pin.flags.data(), (size_t)n_nets, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "flags");
+    h->drop_graph();
+    const int blk = h->block;
+    const int rc = setup_cta(h, h->caps, &e);
+    (void)blk;
+    return rc;
 }
 
 }  // namespace
@@ -865,7 +964,8 @@ int psst_set_state(psst_net *h, const float *src, size_t n, int src_on_device, v
     cudaError_t e = cudaMemcpyAsync(h->v.state, src, dim * sizeof(float),
                                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !src_on_device) e = cudaStreamSynchronize(st);
-    return e == cudaSuccess ? PSST_OK : cuda_fail(e, "psst_set_state");
+    if (e != cudaSuccess) return cuda_fail(e, "psst_set_state");
+    return recheck_pairs(h, st);
 }
 
 int psst_set_step(psst_net *h, int64_t step) {

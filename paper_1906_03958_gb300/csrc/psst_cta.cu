@@ -64,16 +64,18 @@ struct SmemCoef {
     __device__ __forceinline__ float4 s(int i) const { return t2[i]; }
 };
 
-template <int ST, int CL, bool HAS2>
+template <int ST, int CL, bool HAS2, bool PAIR>
 __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0, int N, int nt, int r_lo, int nown,
                                       unsigned rank, int tq, long long step, float dt, float *vst, float *y0,
                                       float *acc, float *ys, const float *prm, const float *iext, float2 *cur1,
                                       float2 *acc1, float2 *fin1, float4 *cur2, float4 *acc2, float4 *fin2,
-                                      const float *stab) {
+                                      float *pst, const float *stab) {
     const int tid = threadIdx.x, nthr = blockDim.x, M = N * nt;
     const float *vcur = vst + (ST & 1) * N;
     float *vnxt = vst + ((ST + 1) & 1) * N;
-    sphase<ST, HAS2>(it, SmemCoef{ST == 0 ? fin1 : cur1, ST == 0 ? fin2 : cur2});
+    float *r0p = pst, *s0p = pst + M, *Gt = pst + 2 * M;
+    if (PAIR) sphase_pair(it, Gt, HAS2);
+    else sphase<ST, HAS2>(it, SmemCoef{ST == 0 ? fin1 : cur1, ST == 0 ? fin2 : cur2});
     __syncthreads();
     for (int i = tid; i < nown; i += nthr) {
         const float V = vcur[r_lo + i];
@@ -95,12 +97,24 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
         float4 &a2 = HAS2 ? acc2[p] : d4;
         float4 &f2 = HAS2 ? fin2[p] : d4;
         coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], fin1[p], c2, a2, f2);
+        if (PAIR) {
+            // the pair's gate for the next stage (same operations as the per-synapse path)
+            const bool sec = HAS2 && stab[(p % nt) * 9 + SP_KIND] != 0.0f;
+            if (ST < 3) {
+                Gt[p] = pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]);
+            } else {
+                const float r0 = r0p[p], s0 = s0p[p];
+                Gt[p] = pair_gate(sec, fin1[p], f2, r0, s0);
+                r0p[p] = fmaf(fin1[p].y, r0, fin1[p].x);
+                if (sec) s0p[p] = fmaf(f2.z, s0, fmaf(f2.y, r0, f2.x));
+            }
+        }
     }
     if (CL > 1) cluster_sync();
     else __syncthreads();
 }
 
-template <int CL, bool HAS2>
+template <int CL, bool HAS2, bool PAIR>
 __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long step0, int nsteps,
                         unsigned char *smem, const float *stab) {
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -109,7 +123,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     const int nt = v.n_stypes, M = N * nt;
     const long long sbase = v.row_ptr[n0];
     const int r_lo = pl.split[rank], nown = pl.split[rank + 1] - r_lo;
-    const NeuronLayout L = make_nlayout(nown, N, M, HAS2);
+    const NeuronLayout L = make_nlayout(nown, N, M, HAS2, PAIR);
     float *y0 = (float *)(smem + L.y0), *ys = (float *)(smem + L.ys), *acc = (float *)(smem + L.acc);
     float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext), *inp = (float *)(smem + L.inp);
     float *vst = (float *)(smem + L.vst);
@@ -118,7 +132,9 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     float4 *acc2 = HAS2 ? (float4 *)(smem + L.acc2) : nullptr;
     float4 *fin2 = HAS2 ? (float4 *)(smem + L.fin2) : nullptr;
     int *tmp = (int *)(smem + L.tmp);
-    Items it = carve_items(smem + L.syn, nown, pl.K, pl.n1[rank], pl.n2[rank], HAS2);
+    float *pst = PAIR ? (float *)(smem + L.pair) : nullptr;
+    Items it = PAIR ? carve_items_pair(smem + L.syn, nown, pl.K, pl.n1[rank], pl.n2[rank])
+                    : carve_items(smem + L.syn, nown, pl.K, pl.n1[rank], pl.n2[rank], HAS2);
 
     float *gV = v.state + n0;
     float *gr = v.state + 4 * v.N + sbase;
@@ -150,7 +166,26 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
             fin2[k] = make_float4(0.0f, 0.0f, 1.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
         }
     }
-    load_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gw, gcode, stab, tmp);  // ends with __syncthreads
+    if (PAIR) {
+        // pair state from the network's synapses (all gates of a pair are equal)
+        for (int p = tid; p < 2 * M; p += nthr) pst[p] = 0.0f;
+        __syncthreads();
+        const int S = (int)(v.row_ptr[n0 + N] - sbase);
+        for (int k = tid; k < S; k += nthr) {
+            const int ci = (int)(gcode[k] & 0xFFFFFFu);
+            pst[ci] = gr[k];
+            if (HAS2 && second_order(stab, gcode[k])) pst[M + ci] = gs[k];
+        }
+        __syncthreads();
+        for (int p = tid; p < M; p += nthr) {
+            const bool sec = HAS2 && stab[(p % nt) * 9 + SP_KIND] != 0.0f;
+            pst[2 * M + p] = pair_gate(sec, fin1[p], HAS2 ? fin2[p] : make_float4(0.f, 0.f, 1.f, 1.f), pst[p],
+                                       pst[M + p]);
+        }
+        load_items_pair<HAS2>(it, v, n0, sbase, r_lo, gw, gcode, stab, tmp, 1);  // ends with __syncthreads
+    } else {
+        load_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gw, gcode, stab, tmp);  // ends with __syncthreads
+    }
     if (CL > 1) cluster_sync();
 
     const float dt = v.dt;
@@ -164,18 +199,27 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         for (int i = tid; i < nown; i += nthr)
             iext[i] = input_current(v, inp[i], inp[nown + i], in_pulse, (long long)n0 + r_lo + i, step);
         // iext is read in the N-phase, after the S-phase barrier
-        stage<0, CL, HAS2>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
-                           acc1, fin1, cur2, acc2, fin2, stab);
-        stage<1, CL, HAS2>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
-                           acc1, fin1, cur2, acc2, fin2, stab);
-        stage<2, CL, HAS2>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
-                           acc1, fin1, cur2, acc2, fin2, stab);
-        stage<3, CL, HAS2>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
-                           acc1, fin1, cur2, acc2, fin2, stab);
+        stage<0, CL, HAS2, PAIR>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
+        stage<1, CL, HAS2, PAIR>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
+        stage<2, CL, HAS2, PAIR>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
+        stage<3, CL, HAS2, PAIR>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
     }
 
     // write back: owned synapses with the last step's gate map, owned neurons
-    store_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gcode, stab, SmemCoef{fin1, fin2});
+    if (PAIR) {
+        const long long k0 = v.row_ptr[n0 + r_lo] - sbase, k1 = v.row_ptr[n0 + r_lo + nown] - sbase;
+        for (long long k = k0 + tid; k < k1; k += nthr) {
+            const int ci = (int)(gcode[k] & 0xFFFFFFu);
+            gr[k] = pst[ci];
+            if (HAS2 && second_order(stab, gcode[k])) gs[k] = pst[M + ci];
+        }
+    } else {
+        store_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gcode, stab, SmemCoef{fin1, fin2});
+    }
     bool bad = false;
     for (int i = tid; i < nown; i += nthr) {
 #pragma unroll
@@ -201,8 +245,14 @@ __global__ void __launch_bounds__(1024) net_kernel(NetView v, const int *list, c
     }
     __syncthreads();
     const int b = list[blockIdx.x / CL];
-    if (v.net_flags[b] & NET_HAS2) run_net<CL, true>(v, b, plans[b], step0, nsteps, smem, stab);
-    else run_net<CL, false>(v, b, plans[b], step0, nsteps, smem, stab);
+    const uint8_t f = v.net_flags[b];
+    if (f & NET_PAIR) {
+        if (f & NET_HAS2) run_net<CL, true, true>(v, b, plans[b], step0, nsteps, smem, stab);
+        else run_net<CL, false, true>(v, b, plans[b], step0, nsteps, smem, stab);
+    } else {
+        if (f & NET_HAS2) run_net<CL, true, false>(v, b, plans[b], step0, nsteps, smem, stab);
+        else run_net<CL, false, false>(v, b, plans[b], step0, nsteps, smem, stab);
+    }
 }
 
 template <int CL>
@@ -226,7 +276,38 @@ cudaError_t launch_cl(const NetView &v, const ClassLaunch &c, long long step0, i
     return cudaLaunchKernelEx(&cfg, net_kernel<CL>, v, c.list, c.plans, step0, nsteps);
 }
 
+// out[b] = 1 when every (presynaptic neuron, type) pair of network b has
+// bitwise-equal gates (r, s) in the state; one CTA per network, shared
+// memory holds the first synapse of each pair.
+__global__ void pair_check_kernel(NetView v, uint8_t *out) {
+    extern __shared__ int first[];
+    __shared__ int bad;
+    const int b = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
+    const int n0 = v.net_off[b], N = v.net_off[b + 1] - n0, M = N * v.n_stypes;
+    const long long sbase = v.row_ptr[n0], S = v.row_ptr[n0 + N] - sbase;
+    const uint32_t *code = v.syn_code + sbase;
+    const float *r = v.state + 4 * v.N + sbase, *s = v.state + 4 * v.N + v.S + sbase;
+    for (int p = tid; p < M; p += nthr) first[p] = 0x7fffffff;
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (long long k = tid; k < S; k += nthr) atomicMin(&first[code[k] & 0xFFFFFFu], (int)k);
+    __syncthreads();
+    for (long long k = tid; k < S; k += nthr) {
+        const int f = first[code[k] & 0xFFFFFFu];
+        if (__float_as_uint(r[k]) != __float_as_uint(r[f]) || __float_as_uint(s[k]) != __float_as_uint(s[f])) bad = 1;
+    }
+    __syncthreads();
+    if (tid == 0) out[b] = bad ? 0 : 1;
+}
+
 }  // namespace
+
+cudaError_t pair_check(const NetView &v, uint8_t *out, int smem, cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(pair_check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    pair_check_kernel<<<v.n_nets, 256, smem, stream>>>(v, out);
+    return cudaGetLastError();
+}
 
 int cta_static_smem() { return (int)(PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM * sizeof(float)); }
 

@@ -45,7 +45,7 @@ struct NetView {
     int *err;                    // device error word (first error wins)
 };
 
-enum : uint8_t { NET_HAS2 = 1 };
+enum : uint8_t { NET_HAS2 = 1, NET_PAIR = 2 };  // NET_PAIR: all gates of each (pre, type) pair equal
 
 // Extra device state of the grid-wide mode (one network over all SMs).
 struct GridView {
@@ -109,6 +109,7 @@ struct NeuronLayout {
     int inp;               // float [2][n_own]: constant current, pulse amplitude
     int vst;               // float [2][n_all]: stage potential, by stage parity
     int tmp;               // int [2][n_own + 1]: scan scratch
+    int pair;              // per-pair variant: float [3][m]: step-start r, s and the stage gate
     int syn;               // start of the synapse items
 };
 
@@ -118,7 +119,7 @@ __host__ __device__ inline int lay_take(int &o, long long bytes) {
     return at;
 }
 
-__host__ __device__ inline NeuronLayout make_nlayout(int n_own, int n_all, int m, bool has2) {
+__host__ __device__ inline NeuronLayout make_nlayout(int n_own, int n_all, int m, bool has2, bool pair = false) {
     NeuronLayout L;
     int o = 0;
     L.cur2 = has2 ? lay_take(o, 16LL * m) : -1;
@@ -137,6 +138,7 @@ __host__ __device__ inline NeuronLayout make_nlayout(int n_own, int n_all, int m
     L.iext = lay_take(o, 4LL * n_own);
     L.inp = lay_take(o, 8LL * n_own);
     L.tmp = lay_take(o, 8LL * (n_own + 1));
+    L.pair = pair ? lay_take(o, 12LL * m) : -1;
     L.syn = o;
     return L;
 }

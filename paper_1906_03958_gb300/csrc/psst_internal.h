@@ -19,6 +19,7 @@ struct ClassLaunch {
 // CTA/cluster batched kernel (psst_cta.cu).
 int cta_static_smem();
 cudaError_t cta_prepare(int cl, int max_smem);
+cudaError_t pair_check(const NetView &v, uint8_t *out, int smem, cudaStream_t stream);
 cudaError_t cta_launch(const NetView &v, const ClassLaunch &c, long long step0, int nsteps, cudaStream_t stream);
 
 // Grid-wide single-network kernel (psst_grid.cu).

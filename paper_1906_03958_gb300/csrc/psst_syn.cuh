@@ -273,6 +273,149 @@ __device__ __forceinline__ float row_current(const Items &it, int i, float V) {
     return fmaf(V, A, -B);
 }
 
+// ------------------------------------------------- per-pair gate variant
+//
+// When all gates of a (presynaptic neuron, type) pair hold the same value
+// (true from rest, and preserved by the dynamics), each stage's gate value
+// is computed once per pair, G_p = P_s + Q_s r0_p with the same FMA as the
+// per-synapse path, so the two paths give bitwise-identical sums.  The items
+// then carry no gate state: float4 w, wE and ushort4 gate-table index.
+
+__host__ __device__ inline long long items_smem_bytes_pair(int n1, int n2, int K, int nrows) {
+    const long long c = (long long)K * (n1 + n2);
+    return c * (16 * 2 + 8) + 8LL * (n1 + n2) + 8LL * (nrows + 1) + 64;
+}
+
+__device__ inline Items carve_items_pair(unsigned char *base, int nrows, int K, int n1, int n2) {
+    Items it;
+    it.nrows = nrows;
+    it.K = K;
+    it.n1 = n1;
+    it.n2 = n2;
+    const long long c = (long long)K * (n1 + n2);
+    unsigned char *p = base;
+    it.r = nullptr;
+    it.s = nullptr;
+    it.w = (float4 *)p;
+    p += 16 * c;
+    it.we = (float4 *)p;
+    p += 16 * c;
+    it.id = (ushort4 *)p;
+    p += 8 * c;
+    it.pa = (float *)p;
+    p += 4LL * (n1 + n2);
+    it.pb = (float *)p;
+    p += 4LL * (n1 + n2);
+    it.ib1 = (int *)p;
+    p += 4LL * (nrows + 1);
+    it.ib2 = (int *)p;
+    return it;
+}
+
+// Items of rows [row0, row0 + nrows) without gate state; the gate-table
+// index of a synapse is its coefficient index divided by idx_div (1: one
+// entry per (neuron, type); n_types: one entry per presynaptic neuron).
+template <bool HAS2>
+__device__ void load_items_pair(Items &it, const NetView &v, long long row_g0, long long sbase, int row0,
+                                const float *gw, const uint32_t *gcode, const float *stab, int *tmp,
+                                int idx_div) {
+    const int tid = threadIdx.x, nthr = blockDim.x, nrows = it.nrows, K = it.K;
+    int *c1 = tmp, *c2 = tmp + nrows + 1;
+    for (int i = tid; i < nrows; i += nthr) {
+        const long long k0 = v.row_ptr[row_g0 + row0 + i] - sbase, k1 = v.row_ptr[row_g0 + row0 + i + 1] - sbase;
+        int n2 = 0;
+        if (HAS2)
+            for (long long k = k0; k < k1; ++k) n2 += second_order(stab, gcode[k]);
+        c1[i] = part_items((int)(k1 - k0) - n2, K);
+        c2[i] = part_items(n2, K);
+    }
+    __syncthreads();
+    block_scan(c1, it.ib1, nrows);
+    block_scan(c2, it.ib2, nrows);
+    const long long chunks = (long long)K * (it.n1 + it.n2);
+    for (long long c = tid; c < chunks; c += nthr) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        it.w[c] = z;
+        it.we[c] = z;
+        it.id[c] = make_ushort4(0, 0, 0, 0);
+    }
+    __syncthreads();
+    float *W = (float *)it.w, *WE = (float *)it.we;
+    unsigned short *ID = (unsigned short *)it.id;
+    for (int i = tid; i < nrows; i += nthr) {
+        const long long k0 = v.row_ptr[row_g0 + row0 + i] - sbase, k1 = v.row_ptr[row_g0 + row0 + i + 1] - sbase;
+        int m1 = 0, m2 = 0;
+        for (long long k = k0; k < k1; ++k) {
+            const uint32_t code = gcode[k];
+            const bool sec = HAS2 && second_order(stab, code);
+            const long long p = sec ? item_slot(it.ib2[i], m2++, K, it.n2, K * it.n1)
+                                    : item_slot(it.ib1[i], m1++, K, it.n1, 0);
+            const float w = gw[k];
+            W[p] = w;
+            WE[p] = w * stab[(code >> 24) * 9 + SP_E];
+            ID[p] = (unsigned short)((code & 0xFFFFFFu) / (uint32_t)idx_div);
+        }
+    }
+    __syncthreads();
+}
+
+// S-phase of the per-pair variant: the gate of every synapse is Gt[id].
+__device__ __forceinline__ void sphase_pair(const Items &it, const float *Gt, bool has2) {
+    const int tid = threadIdx.x, nthr = blockDim.x, K = it.K, n1 = it.n1;
+    for (int t = tid; t < n1; t += nthr) {
+        float A = 0.0f, B = 0.0f;
+        for (int j = 0; j < K; ++j) {
+            const int c = j * n1 + t;
+            const float4 w = it.w[c], we = it.we[c];
+            const ushort4 id = it.id[c];
+            const float g0 = Gt[id.x], g1 = Gt[id.y], g2 = Gt[id.z], g3 = Gt[id.w];
+            A = fmaf(w.x, g0, A);
+            B = fmaf(we.x, g0, B);
+            A = fmaf(w.y, g1, A);
+            B = fmaf(we.y, g1, B);
+            A = fmaf(w.z, g2, A);
+            B = fmaf(we.z, g2, B);
+            A = fmaf(w.w, g3, A);
+            B = fmaf(we.w, g3, B);
+        }
+        it.pa[t] = A;
+        it.pb[t] = B;
+    }
+    if (has2) {
+        const int n2 = it.n2, base = K * n1;
+        for (int t = tid; t < n2; t += nthr) {
+            float A = 0.0f, B = 0.0f;
+            for (int j = 0; j < K; ++j) {
+                const int c = base + j * n2 + t;
+                const float4 w = it.w[c], we = it.we[c];
+                const ushort4 id = it.id[c];
+                const float g0 = Gt[id.x], g1 = Gt[id.y], g2 = Gt[id.z], g3 = Gt[id.w];
+                A = fmaf(w.x, g0, A);
+                B = fmaf(we.x, g0, B);
+                A = fmaf(w.y, g1, A);
+                B = fmaf(we.y, g1, B);
+                A = fmaf(w.z, g2, A);
+                B = fmaf(we.z, g2, B);
+                A = fmaf(w.w, g3, A);
+                B = fmaf(we.w, g3, B);
+            }
+            it.pa[n1 + t] = A;
+            it.pb[n1 + t] = B;
+        }
+    }
+}
+
+// Gate value G of a pair from its stage maps and step-start gates, with
+// exactly the operations of syn1/syn2 (first order: r; second order:
+// s^4 / (s^4 + Kd), Kd in F2.w).
+__device__ __forceinline__ float pair_gate(bool second, float2 F, float4 F2, float r0, float s0) {
+    const float rr = fmaf(F.y, r0, F.x);
+    if (!second) return rr;
+    const float ss = fmaf(F2.z, s0, fmaf(F2.y, r0, F2.x));
+    const float s2 = ss * ss, s4 = s2 * s2;
+    return __fdividef(s4, s4 + F2.w);
+}
+
 // Gate-map update of one (presynaptic neuron j, synapse type tau) pair at
 // stage ST from the stage-ST potential V of j.  cur/acc hold this stage's
 // map and the running RK4 sum; writes the next stage's map into cur (ST < 3)

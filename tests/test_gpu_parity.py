@@ -311,3 +311,38 @@ def test_autotune_keeps_results_bitwise():
         b.integrate(200)
         a.status(), b.status()
         np.testing.assert_array_equal(a.get_state_numpy(), b.get_state_numpy())
+
+
+def test_pair_gates_bitwise_equal_to_per_synapse_gates():
+    # one gate per (presynaptic neuron, type) pair evaluates the same FMAs as
+    # one gate per synapse when the pair's gates are equal (from rest)
+    specs = [ng.antennal_lobe(seed=61), ng.antennal_lobe(seed=62, n_pn=40, n_ln=20)]
+    spec = ng.concat_specs(specs)
+    y0 = oracle.rest_state(spec).astype(np.float32)
+    out = []
+    for gm in (0, 1):
+        with _net(spec, init_state=y0, gate_mode=gm, rec_stride=20, rec_capacity=100) as net:
+            net.set_step(9900)
+            net.integrate(600)
+            net.status()
+            out.append((net.get_state_numpy(), net.read_record()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_set_state_switches_gate_layout():
+    # a state whose pair gates differ must leave the per-pair layout; results
+    # then equal a network that always runs per synapse
+    spec = ng.antennal_lobe(seed=63)
+    N = spec.n_neurons
+    y = oracle.rest_state(spec).astype(np.float32)
+    y[4 * N:4 * N + spec.n_synapses] = np.random.default_rng(0).uniform(0, 1, spec.n_synapses)
+    with _net(spec) as a, _net(spec, gate_mode=1) as b:
+        a.integrate(10)          # per-pair layout from rest
+        a.set_state(y)
+        b.set_state(y)
+        a.set_step(0), b.set_step(0)
+        a.integrate(200)
+        b.integrate(200)
+        a.status(), b.status()
+        np.testing.assert_array_equal(a.get_state_numpy(), b.get_state_numpy())
