@@ -125,6 +125,8 @@ typedef struct {
     int32_t n_cluster_nets;        /* CTA mode: networks spread over a cluster of 2 or 4 CTAs */
     int32_t n_launch_classes;      /* CTA mode: launches per integrate chunk (size classes) */
     int32_t kernel_launches;       /* kernels the last psst_integrate enqueued */
+    int32_t n_pair_gate_nets;      /* networks whose forward keeps one gate per (presynaptic neuron, type)
+                                      pair; the others keep one gate per synapse (gate_mode) */
 } psst_info;
 
 typedef struct psst_net psst_net;

@@ -379,12 +379,51 @@ std::vector<uint8_t> uniform_pairs(const float *y, const PlanInput &in, const in
     return ok;
 }
 
+// Grid mode, per-pair gates: the compact table index of every
+// (presynaptic neuron, type) pair that has a synapse, in pair order, and one
+// synapse of each such pair.  Built once from the connectivity.
+int grid_pair_tables(psst_net *h, const psst_network_desc *d, cudaError_t *err) {
+    const long long N = h->v.N, S = h->v.S;
+    const int nt = h->v.n_stypes;
+    const long long M = N * nt;
+    std::vector<long long> first((size_t)M, -1);
+    for (long long k = 0; k < S; ++k) {
+        const size_t p = (size_t)d->pre[k] * nt + d->syn_type[k];
+        if (first[p] < 0) first[p] = k;
+    }
+    std::vector<int> tix((size_t)M, -1);
+    std::vector<long long> rep;
+    for (long long p = 0; p < M; ++p)
+        if (first[p] >= 0) {
+            tix[p] = (int)rep.size();
+            rep.push_back(first[p]);
+        }
+    psst::GridView &g = h->gv;
+    const long long used = (long long)rep.size();
+    g.mt = (int)((used + 3) & ~3LL);
+    int *t = nullptr;
+    long long *r = nullptr;
+    cudaError_t e = upload(h, &t, tix.data(), tix.size());
+    if (e == cudaSuccess) e = upload(h, &r, rep.data(), rep.size());
+    if (e == cudaSuccess) e = h->alloc(&g.gt, (size_t)2 * g.mt);
+    if (e == cudaSuccess) e = cudaMemset(g.gt, 0, (size_t)2 * std::max(g.mt, 1) * sizeof(float));
+    if (e == cudaSuccess) e = h->alloc(&g.r0g, (size_t)used);
+    if (e == cudaSuccess) e = h->alloc(&g.s0g, (size_t)used);
+    g.tix = t;
+    g.rep = r;
+    if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid pair tables");
+    return PSST_OK;
+}
+
 // Grid mode: one contiguous block of rows per CTA with balanced cost, the
-// double-buffered gate-map tables and the barrier words.
-int setup_grid(psst_net *h, const psst_network_desc *d, const SmemCaps &caps, bool has2, const std::vector<int> &n1,
-               const std::vector<int> &n2, cudaError_t *err) {
+// double-buffered gate tables and the barrier words.  Per-pair gates when
+// the network's pairs are uniform (flag NET_PAIR) and the compact gate
+// table fits in shared memory next to the items; re-run when that changes.
+int setup_grid(psst_net *h, const SmemCaps &caps, cudaError_t *err) {
+    const PlanInput &in = h->pin;
     const long long N = h->v.N;
     const int nt = h->v.n_stypes;
+    const bool has2 = in.flags[0] & psst::NET_HAS2;
     if (N * nt >= 65536)
         return fail(PSST_ERR_UNSUPPORTED, "grid mode: %lld neurons x %d synapse types must stay below 65536", N, nt);
     int sms = 0;
@@ -393,43 +432,54 @@ int setup_grid(psst_net *h, const psst_network_desc *d, const SmemCaps &caps, bo
     const int parts = (int)std::max<long long>(1, std::min<long long>(sms, (N + 7) / 8));
     std::vector<Share> sh;
     int K = 1;
-    make_shares(n1.data(), n2.data(), (int)N, parts, d->item_chunks, sh, &K);
+    make_shares(in.n1.data(), in.n2.data(), (int)N, parts, in.user_K, sh, &K);
+    psst::GridView &g = h->gv;
+    bool pair = (in.flags[0] & psst::NET_PAIR) && g.tix != nullptr;
     std::vector<int> split((size_t)parts + 1), items((size_t)2 * parts);
-    int need = 0;
+    long long need = 0, need_pair = 0;
     for (int c = 0; c < parts; ++c) {
         const int n = sh[c].r1 - sh[c].r0;
         const long long bytes = psst::make_nlayout(n, n, n * nt, has2).syn +
                                 psst::items_smem_bytes(sh[c].items1, sh[c].items2, K, n, has2);
-        if (bytes > caps.max_dyn)
-            return fail(PSST_ERR_UNSUPPORTED, "grid mode: block %d needs %lld B of shared memory (max %d)", c, bytes,
-                        caps.max_dyn);
+        const long long bytes_pair = psst::make_nlayout(n, n, n * nt, has2, true).syn + 4LL * g.mt +
+                                     psst::items_smem_bytes_pair(sh[c].items1, sh[c].items2, K, n);
         split[c] = sh[c].r0;
         items[c] = sh[c].items1;
         items[parts + c] = sh[c].items2;
-        need = std::max<int>(need, (int)bytes);
+        need = std::max(need, bytes);
+        need_pair = std::max(need_pair, bytes_pair);
     }
     split[parts] = (int)N;
+    if (pair && need_pair > caps.max_dyn) pair = false;
+    if (!pair && need > caps.max_dyn)
+        return fail(PSST_ERR_UNSUPPORTED, "grid mode: a block needs %lld B of shared memory (max %d)", need,
+                    caps.max_dyn);
     if (!h->block) h->block = 1024;
     h->K = K;
-    h->smem = need;
+    h->smem = (int)(pair ? need_pair : need);
     int per_sm = 0;
     // the kernel attribute is an upper bound shared by every handle's launches
     e = psst::grid_occupancy(h->block, caps.max_dyn, &per_sm);
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid occupancy");
     if (per_sm < 1) return fail(PSST_ERR_UNSUPPORTED, "grid mode: a CTA of %d threads does not fit an SM", h->block);
     h->grid = parts;
-    psst::GridView &g = h->gv;
-    int *rs = nullptr, *itd = nullptr;
-    e = upload(h, &rs, split.data(), split.size());
-    if (e == cudaSuccess) e = upload(h, &itd, items.data(), items.size());
-    if (e == cudaSuccess) e = h->alloc(&g.c1, (size_t)(2 * N * nt));
-    if (e == cudaSuccess && has2) e = h->alloc(&g.c2, (size_t)(2 * N * nt));
-    if (e == cudaSuccess) e = h->alloc(&g.bar, 2);
-    g.row_split = rs;
-    g.items = itd;
+    if (!g.row_split) {
+        int *rs = nullptr, *itd = nullptr;
+        e = h->alloc(&rs, split.size());
+        if (e == cudaSuccess) e = h->alloc(&itd, items.size());
+        if (e == cudaSuccess) e = h->alloc(&g.c1, (size_t)(2 * N * nt));
+        if (e == cudaSuccess && has2) e = h->alloc(&g.c2, (size_t)(2 * N * nt));
+        if (e == cudaSuccess) e = h->alloc(&g.bar, 2);
+        g.row_split = rs;
+        g.items = itd;
+        if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid buffers");
+    }
+    e = cudaMemcpy((void *)g.row_split, split.data(), split.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy((void *)g.items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid plan upload");
     g.K = K;
-    g.timeout_ns = 2000000000ULL;
-    if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid buffers");
+    g.pair = pair ? 1 : 0;
     return PSST_OK;
 }
 
@@ -550,7 +600,6 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
         pin.net_syn[b] = d->row_ptr[d->net_neuron_off[b + 1]] - d->row_ptr[d->net_neuron_off[b]];
     std::vector<uint8_t> has2;
     row_counts(d, pin.n1, pin.n2, has2);
-    const std::vector<int> &n1 = pin.n1, &n2 = pin.n2;
     pin.flags.assign(n_nets, 0);
     {
         const std::vector<uint8_t> uni = uniform_pairs(d->init_state, pin, d->row_ptr, d->pre, d->syn_type, N, S);
@@ -661,7 +710,13 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
         return cuda_fail(e, "psst_create_network");
     }
     h->caps = caps;
-    rc = mode == PSST_MODE_GRID ? setup_grid(h, d, caps, has2[0] != 0, n1, n2, &e) : setup_cta(h, caps, &e);
+    if (mode == PSST_MODE_GRID) {
+        h->gv.timeout_ns = 2000000000ULL;
+        rc = grid_pair_tables(h, d, &e);
+        if (!rc) rc = setup_grid(h, caps, &e);
+    } else {
+        rc = setup_cta(h, caps, &e);
+    }
     if (rc) {
         h->release();
         delete h;
@@ -767,7 +822,7 @@ int replay_steps(psst_net *h, long long step0, long long n_steps, cudaStream_t s
 // every (presynaptic neuron, type) pair?  When that changes, the CTA-mode
 // plan (per-pair or per-synapse layout) is rebuilt.
 int recheck_pairs(psst_net *h, cudaStream_t st) {
-    if (h->mode != PSST_MODE_CTA || h->pin.force_synapse_gates) return PSST_OK;
+    if (h->pin.force_synapse_gates) return PSST_OK;
     const int n_nets = h->pin.n_nets;
     if (!h->d_check) {
         cudaError_t e = h->alloc(&h->d_check, (size_t)n_nets);
@@ -792,10 +847,7 @@ int recheck_pairs(psst_net *h, cudaStream_t st) {
     cudaError_t e = cudaMemcpy((void *)h->v.net_flags, h->pin.flags.data(), (size_t)n_nets, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "flags");
     h->drop_graph();
-    const int blk = h->block;
-    const int rc = setup_cta(h, h->caps, &e);
-    (void)blk;
-    return rc;
+    return h->mode == PSST_MODE_GRID ? setup_grid(h, h->caps, &e) : setup_cta(h, h->caps, &e);
 }
 
 }  // namespace
@@ -1168,6 +1220,11 @@ int psst_query(const psst_net *h, psst_info *out) {
     out->n_cluster_nets = h->n_global;
     out->n_launch_classes = (int32_t)h->classes.size();
     out->kernel_launches = h->launches;
+    if (h->mode == PSST_MODE_GRID) {
+        out->n_pair_gate_nets = h->gv.pair;
+    } else {
+        for (uint8_t f : h->pin.flags) out->n_pair_gate_nets += (f & psst::NET_PAIR) ? 1 : 0;
+    }
     return PSST_OK;
 }
 

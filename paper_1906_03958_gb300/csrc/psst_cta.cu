@@ -182,7 +182,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
             pst[2 * M + p] = pair_gate(sec, fin1[p], HAS2 ? fin2[p] : make_float4(0.f, 0.f, 1.f, 1.f), pst[p],
                                        pst[M + p]);
         }
-        load_items_pair<HAS2>(it, v, n0, sbase, r_lo, gw, gcode, stab, tmp, 1);  // ends with __syncthreads
+        load_items_pair<HAS2>(it, v, n0, sbase, r_lo, gw, gcode, stab, tmp, nullptr);  // ends with __syncthreads
     } else {
         load_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gw, gcode, stab, tmp);  // ends with __syncthreads
     }

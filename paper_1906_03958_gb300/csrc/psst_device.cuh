@@ -56,6 +56,13 @@ struct GridView {
     const int *items;            // [2][gridDim.x] first- and second-order work items of each CTA
     int K;                       // 4-synapse chunks per work item
     unsigned long long timeout_ns;  // limit of one barrier wait
+    // one gate per used (presynaptic neuron, type) pair (all gates of a pair equal)
+    int pair;                    // 1: per-pair gate tables below; 0: per-synapse gates
+    int mt;                      // entries of one gate table (used pairs, padded to a multiple of 4)
+    const int *tix;              // [N * n_stypes] table index of each pair, -1 when no synapse uses it
+    const long long *rep;        // [used pairs] one synapse of each pair (holds the pair's gates)
+    float *gt;                   // [2][mt] each pair's gate for the next stage, double-buffered by stage parity
+    float *r0g, *s0g;            // [used pairs] step-start gates handed to the synapses' owners at the end
 };
 
 // Column indices of the parameter tables.

@@ -12,6 +12,14 @@
 // from readers, and double buffering removes the write-after-read hazard.
 // The barrier spins with a time limit: on expiry it records
 // PSST_ERR_TIMEOUT and every CTA returns.
+//
+// Per-pair variant (all gates of each (presynaptic neuron, type) pair equal,
+// as from rest): the owner of a presynaptic neuron keeps its pairs' gate
+// state and writes each used pair's next-stage gate value (4 bytes) to a
+// compact global table; every CTA copies that table into shared memory with
+// coalesced loads once per stage and gathers its synapses' gates from there,
+// instead of gathering an 8-byte map per synapse from L2.  Results are
+// bitwise equal to the per-synapse variant.
 #include <cuda_runtime.h>
 
 #include "psst_device.cuh"
@@ -77,16 +85,27 @@ struct GlobalCoef {
     __device__ __forceinline__ float4 s(int i) const { return __ldcg(t2 + i); }
 };
 
-template <int ST, bool HAS2>
+template <int ST, bool HAS2, bool PAIR>
 __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, const Items &it, int lo, int N,
                                            int nt, int M, int tq, long long step, float dt, float *vst, float *y0,
                                            float *acc, float *ys, const float *prm, const float *iext,
-                                           float2 *cur1, float2 *acc1, float4 *cur2, float4 *acc2,
-                                           const float *stab) {
+                                           float2 *cur1, float2 *acc1, float4 *cur2, float4 *acc2, float *pst,
+                                           float *gtab, const float *stab) {
     const int tid = threadIdx.x, nthr = blockDim.x, Mloc = N * nt;
     const float *vcur = vst + (ST & 1) * N;
     float *vnxt = vst + ((ST + 1) & 1) * N;
-    sphase<ST, HAS2>(it, GlobalCoef{g.c1 + (size_t)(ST & 1) * M, HAS2 ? g.c2 + (size_t)(ST & 1) * M : nullptr});
+    if (PAIR) {
+        // this stage's gate of every used pair, written by the owners before the last barrier
+        const float4 *src = (const float4 *)(g.gt + (size_t)(ST & 1) * g.mt);
+        float4 *dst = (float4 *)gtab;
+        const int n4 = g.mt >> 2;
+#pragma unroll 4
+        for (int q = tid; q < n4; q += nthr) dst[q] = __ldcg(src + q);
+        __syncthreads();
+        sphase_pair(it, gtab, HAS2);
+    } else {
+        sphase<ST, HAS2>(it, GlobalCoef{g.c1 + (size_t)(ST & 1) * M, HAS2 ? g.c2 + (size_t)(ST & 1) * M : nullptr});
+    }
     __syncthreads();
     for (int i = tid; i < N; i += nthr) {
         const float V = vcur[i];
@@ -98,30 +117,58 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
             v.rec[(frame % v.rec_cap) * v.N + lo + i] = vn;
         }
     }
-    // gate maps of the own pairs: local copy for the next stage, and the
-    // table every CTA reads at the next stage
-    float2 *o1 = g.c1 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt;
-    float4 *o2 = HAS2 ? g.c2 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt : nullptr;
-    for (int p = tq; p < Mloc; p += nthr) {
-        float2 f1;
-        float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;
-        float4 &c2 = HAS2 ? cur2[p] : d4;
-        float4 &a2 = HAS2 ? acc2[p] : d4;
-        coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
-        o1[p] = ST == 3 ? f1 : cur1[p];
-        if (HAS2) o2[p] = ST == 3 ? f2 : cur2[p];
+    if (PAIR) {
+        // gates of the own used pairs for the next stage (same operations as
+        // the per-synapse path), published in the other table
+        float *r0p = pst, *s0p = pst + Mloc;
+        float *gout = g.gt + (size_t)((ST + 1) & 1) * g.mt;
+        for (int p = tq; p < Mloc; p += nthr) {
+            const int t = __ldg(g.tix + (size_t)lo * nt + p);
+            if (t < 0) continue;
+            float2 f1;
+            float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;
+            float4 &c2 = HAS2 ? cur2[p] : d4;
+            float4 &a2 = HAS2 ? acc2[p] : d4;
+            const float *sp = stab + (p % nt) * 9;
+            coef_update<ST, HAS2>(sp, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
+            const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
+            float G;
+            if (ST < 3) {
+                G = pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]);
+            } else {
+                const float r0 = r0p[p], s0 = s0p[p];
+                G = pair_gate(sec, f1, f2, r0, s0);
+                r0p[p] = fmaf(f1.y, r0, f1.x);
+                if (sec) s0p[p] = fmaf(f2.z, s0, fmaf(f2.y, r0, f2.x));
+            }
+            gout[t] = G;
+        }
+    } else {
+        // gate maps of the own pairs: local copy for the next stage, and the
+        // table every CTA reads at the next stage
+        float2 *o1 = g.c1 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt;
+        float4 *o2 = HAS2 ? g.c2 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt : nullptr;
+        for (int p = tq; p < Mloc; p += nthr) {
+            float2 f1;
+            float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;
+            float4 &c2 = HAS2 ? cur2[p] : d4;
+            float4 &a2 = HAS2 ? acc2[p] : d4;
+            coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
+            o1[p] = ST == 3 ? f1 : cur1[p];
+            if (HAS2) o2[p] = ST == 3 ? f2 : cur2[p];
+        }
     }
     return grid_barrier(g.bar, g.timeout_ns, v.err);
 }
 
-template <bool HAS2>
+template <bool HAS2, bool PAIR>
 __device__ void grid_run(const NetView &v, const GridView &g, long long step0, int nsteps, unsigned char *smem,
                          const float *stab) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lo = g.row_split[blockIdx.x], N = g.row_split[blockIdx.x + 1] - lo;
     const int nt = v.n_stypes, Mloc = N * nt;
     const int M = (int)(v.N * nt);
-    const NeuronLayout L = make_nlayout(N, N, Mloc, HAS2);
+    const NeuronLayout L = make_nlayout(N, N, Mloc, HAS2, PAIR);
     float *y0 = (float *)(smem + L.y0), *ys = (float *)(smem + L.ys), *acc = (float *)(smem + L.acc);
     float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext), *inp = (float *)(smem + L.inp);
     float *vst = (float *)(smem + L.vst);
@@ -129,7 +176,11 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
     float4 *cur2 = HAS2 ? (float4 *)(smem + L.cur2) : nullptr;
     float4 *acc2 = HAS2 ? (float4 *)(smem + L.acc2) : nullptr;
     int *tmp = (int *)(smem + L.tmp);
-    Items it = carve_items(smem + L.syn, N, g.K, g.items[blockIdx.x], g.items[gridDim.x + blockIdx.x], HAS2);
+    float *pst = PAIR ? (float *)(smem + L.pair) : nullptr;
+    float *gtab = PAIR ? (float *)(smem + L.syn) : nullptr;
+    const int items1 = g.items[blockIdx.x], items2 = g.items[gridDim.x + blockIdx.x];
+    Items it = PAIR ? carve_items_pair(smem + L.syn + 4LL * g.mt, N, g.K, items1, items2)
+                    : carve_items(smem + L.syn, N, g.K, items1, items2, HAS2);
 
     float *gV = v.state + lo;
     float *gr = v.state + 4 * v.N;
@@ -152,16 +203,38 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         inp[N + i] = v.pulse_amp ? v.pulse_amp[lo + i] : 0.0f;
     }
     const long long pon = v.pulse_on[0], poff = v.pulse_off[0];
-    // identity step-end maps of the own pairs in table 0 (read by stage 0)
-    for (int p = tid; p < Mloc; p += nthr) {
-        const int gi = lo * nt + p;
-        g.c1[gi] = make_float2(0.0f, 1.0f);
-        if (HAS2) {
-            const float *sp = stab + (p % nt) * 9;
-            g.c2[gi] = make_float4(0.0f, 0.0f, 1.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
+    if (PAIR) {
+        // own pairs' step-start gates from one synapse of each, and their
+        // stage-0 gates (identity step-end map) in table 0
+        float *r0p = pst, *s0p = pst + Mloc;
+        for (int p = tid; p < Mloc; p += nthr) {
+            const int t = g.tix[(size_t)lo * nt + p];
+            float r0 = 0.0f, s0 = 0.0f;
+            if (t >= 0) {
+                const float *sp = stab + (p % nt) * 9;
+                const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
+                const long long k = g.rep[t];
+                r0 = gr[k];
+                if (sec) s0 = gs[k];
+                g.gt[t] = pair_gate(sec, make_float2(0.0f, 1.0f),
+                                    make_float4(0.0f, 0.0f, 1.0f, sec ? sp[SP_KD] : 1.0f), r0, s0);
+            }
+            r0p[p] = r0;
+            s0p[p] = s0;
         }
+        load_items_pair<HAS2>(it, v, 0, 0, lo, v.weight, v.syn_code, stab, tmp, g.tix);
+    } else {
+        // identity step-end maps of the own pairs in table 0 (read by stage 0)
+        for (int p = tid; p < Mloc; p += nthr) {
+            const int gi = lo * nt + p;
+            g.c1[gi] = make_float2(0.0f, 1.0f);
+            if (HAS2) {
+                const float *sp = stab + (p % nt) * 9;
+                g.c2[gi] = make_float4(0.0f, 0.0f, 1.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
+            }
+        }
+        load_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.weight, v.syn_code, stab, tmp);
     }
-    load_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.weight, v.syn_code, stab, tmp);
     bool ok = grid_barrier(g.bar, g.timeout_ns, v.err);
 
     const float dt = v.dt;
@@ -172,21 +245,41 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         const bool in_pulse = step >= pon && step < poff;
         for (int i = tid; i < N; i += nthr)
             iext[i] = input_current(v, inp[i], inp[N + i], in_pulse, (long long)lo + i, step);
-        ok = grid_stage<0, HAS2>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1, acc1,
-                                 cur2, acc2, stab);
+        ok = grid_stage<0, HAS2, PAIR>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+                                       acc1, cur2, acc2, pst, gtab, stab);
         if (ok)
-            ok = grid_stage<1, HAS2>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1, acc1,
-                                     cur2, acc2, stab);
+            ok = grid_stage<1, HAS2, PAIR>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+                                           acc1, cur2, acc2, pst, gtab, stab);
         if (ok)
-            ok = grid_stage<2, HAS2>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1, acc1,
-                                     cur2, acc2, stab);
+            ok = grid_stage<2, HAS2, PAIR>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+                                           acc1, cur2, acc2, pst, gtab, stab);
         if (ok)
-            ok = grid_stage<3, HAS2>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1, acc1,
-                                     cur2, acc2, stab);
+            ok = grid_stage<3, HAS2, PAIR>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+                                           acc1, cur2, acc2, pst, gtab, stab);
     }
     if (!ok) return;  // error recorded; global state keeps its value from before the call
 
-    store_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.syn_code, stab, GlobalCoef{g.c1, HAS2 ? g.c2 : nullptr});
+    if (PAIR) {
+        // the owners hand their pairs' gates to the CTAs owning the synapses
+        const float *r0p = pst, *s0p = pst + Mloc;
+        for (int p = tid; p < Mloc; p += nthr) {
+            const int t = g.tix[(size_t)lo * nt + p];
+            if (t >= 0) {
+                g.r0g[t] = r0p[p];
+                g.s0g[t] = s0p[p];
+            }
+        }
+        if (!grid_barrier(g.bar, g.timeout_ns, v.err)) return;
+        const long long k0 = v.row_ptr[lo], k1 = v.row_ptr[lo + N];
+        for (long long k = k0 + tid; k < k1; k += nthr) {
+            const uint32_t code = v.syn_code[k];
+            const int t = g.tix[code & 0xFFFFFFu];
+            gr[k] = __ldcg(g.r0g + t);
+            if (HAS2 && second_order(stab, code)) gs[k] = __ldcg(g.s0g + t);
+        }
+    } else {
+        store_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.syn_code, stab, GlobalCoef{g.c1, HAS2 ? g.c2 : nullptr});
+    }
     bool bad = false;
     for (int i = tid; i < N; i += nthr) {
 #pragma unroll
@@ -208,8 +301,14 @@ __global__ void __launch_bounds__(1024, 1) grid_kernel(NetView v, GridView g, lo
         stab[i] = x;
     }
     __syncthreads();
-    if (v.net_flags[0] & NET_HAS2) grid_run<true>(v, g, step0, nsteps, smem, stab);
-    else grid_run<false>(v, g, step0, nsteps, smem, stab);
+    const bool has2 = v.net_flags[0] & NET_HAS2;
+    if (g.pair) {
+        if (has2) grid_run<true, true>(v, g, step0, nsteps, smem, stab);
+        else grid_run<false, true>(v, g, step0, nsteps, smem, stab);
+    } else {
+        if (has2) grid_run<true, false>(v, g, step0, nsteps, smem, stab);
+        else grid_run<false, false>(v, g, step0, nsteps, smem, stab);
+    }
 }
 
 }  // namespace

@@ -313,12 +313,12 @@ __device__ inline Items carve_items_pair(unsigned char *base, int nrows, int K, 
 }
 
 // Items of rows [row0, row0 + nrows) without gate state; the gate-table
-// index of a synapse is its coefficient index divided by idx_div (1: one
-// entry per (neuron, type); n_types: one entry per presynaptic neuron).
+// index of a synapse is its (neuron, type) pair index, or tix[pair] when a
+// compact table of the used pairs is given.
 template <bool HAS2>
 __device__ void load_items_pair(Items &it, const NetView &v, long long row_g0, long long sbase, int row0,
                                 const float *gw, const uint32_t *gcode, const float *stab, int *tmp,
-                                int idx_div) {
+                                const int *tix) {
     const int tid = threadIdx.x, nthr = blockDim.x, nrows = it.nrows, K = it.K;
     int *c1 = tmp, *c2 = tmp + nrows + 1;
     for (int i = tid; i < nrows; i += nthr) {
@@ -353,7 +353,8 @@ __device__ void load_items_pair(Items &it, const NetView &v, long long row_g0, l
             const float w = gw[k];
             W[p] = w;
             WE[p] = w * stab[(code >> 24) * 9 + SP_E];
-            ID[p] = (unsigned short)((code & 0xFFFFFFu) / (uint32_t)idx_div);
+            const uint32_t ci = code & 0xFFFFFFu;
+            ID[p] = (unsigned short)(tix ? tix[ci] : (int)ci);
         }
     }
     __syncthreads();

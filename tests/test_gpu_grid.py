@@ -95,6 +95,7 @@ def test_sparse_large_full_size_single_step():
     y64, _ = oracle.integrate(spec, y32.astype(np.float64), 1, step0=777)
     with _net(spec, init_state=y32) as net:
         assert net.info()["mode"] == psst.MODE_GRID
+        assert net.info()["n_pair_gate_nets"] == 1  # the compact gate table fits next to the items
         net.set_step(777)
         net.integrate(1)
         net.status()
@@ -124,3 +125,45 @@ def test_barrier_timeout_is_reported_and_recoverable():
         ref.integrate(20)
         ref.status()
         np.testing.assert_array_equal(got, ref.get_state_numpy())
+
+
+def test_grid_pair_gates_bitwise_equal_to_per_synapse_gates():
+    # the compact per-pair gate table gives the same sums as one gate per
+    # synapse, to the bit, with noise and a record
+    from paper_1906_03958_gb300 import psst
+    spec = _mid_sparse(seed=35)
+    y0 = oracle.rest_state(spec).astype(np.float32)
+    out = []
+    for gm in (0, 1):
+        with _net(spec, init_state=y0, mode=psst.MODE_GRID, gate_mode=gm, rec_stride=7, rec_capacity=100) as net:
+            assert net.info()["n_pair_gate_nets"] == (1 if gm == 0 else 0)
+            net.set_step(4321)
+            net.integrate(350)
+            net.status()
+            out.append((net.get_state_numpy(), net.read_record()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_grid_set_state_switches_gate_layout():
+    # unequal gates within a pair force one gate per synapse; a state with
+    # equal pair gates brings the per-pair table back
+    from paper_1906_03958_gb300 import psst
+    spec = _mid_sparse(seed=36, noise=False)
+    N, S = spec.n_neurons, spec.n_synapses
+    rest = oracle.rest_state(spec).astype(np.float32)
+    y = rest.copy()
+    y[4 * N:4 * N + S] = np.random.default_rng(1).uniform(0, 1, S)
+    with _net(spec, mode=psst.MODE_GRID) as a, _net(spec, mode=psst.MODE_GRID, gate_mode=1) as b:
+        assert a.info()["n_pair_gate_nets"] == 1
+        a.integrate(10)
+        a.set_state(y)
+        b.set_state(y)
+        assert a.info()["n_pair_gate_nets"] == 0
+        a.set_step(0), b.set_step(0)
+        a.integrate(150)
+        b.integrate(150)
+        a.status(), b.status()
+        np.testing.assert_array_equal(a.get_state_numpy(), b.get_state_numpy())
+        a.set_state(rest)
+        assert a.info()["n_pair_gate_nets"] == 1
