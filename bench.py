@@ -41,14 +41,19 @@ UNIT = "neuron-steps/s"
 FLOP_NEURON_STAGE = 80       # HH rates, currents, 4-variable stage update
 FLOP_COEF1_STAGE = 16        # per (presynaptic neuron, synapse type): T, r-map update
 FLOP_COEF2_STAGE = 20        # extra per (neuron, type) when second-order gates exist
-FLOP_SYN1_STAGE = 6          # first-order synapse: r = P + Q r0, w r (V - E) accumulate
-FLOP_SYN2_STAGE = 14         # second-order synapse: + s map, s^4 / (s^4 + Kd)
+FLOP_SYN1_STAGE = 6          # per-synapse gates, first order: r = P + Q r0, w r (V - E) accumulate
+FLOP_SYN2_STAGE = 14         # per-synapse gates, second order: + s map, s^4 / (s^4 + Kd)
+FLOP_SYN_PAIR_STAGE = 4      # per-pair gates: A += w G, B += wE G (the gate is gathered)
+FLOP_PAIR1_STAGE = 2         # per-pair gates: G = P + Q r0 of a first-order (neuron, type) pair
+FLOP_PAIR2_STAGE = 10        # per-pair gates, second order: + s map, s^4 / (s^4 + Kd)
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 
 
-def workload_flops_per_step(spec) -> float:
-    """Algorithmic FLOP per RK4 step of the whole batch."""
+def workload_flops_per_step(spec, pair_gates: bool = True) -> float:
+    """Algorithmic FLOP per RK4 step of the whole batch, counted for the
+    formulation the kernels execute (one gate per (presynaptic neuron, type)
+    pair when pair_gates, else one per synapse)."""
     kinds = spec.syn_params[:, 0]
     nt = spec.syn_params.shape[0]
     N = spec.n_neurons
@@ -60,8 +65,13 @@ def workload_flops_per_step(spec) -> float:
     has2 = np.zeros(spec.n_nets, bool)
     has2[np.unique(net_of_syn)] = True
     n_has2 = int(spec.net_sizes()[has2].sum())
-    per_stage = (FLOP_NEURON_STAGE * N + FLOP_COEF1_STAGE * N * nt + FLOP_COEF2_STAGE * n_has2 * nt
-                 + FLOP_SYN1_STAGE * n_syn1 + FLOP_SYN2_STAGE * n_syn2)
+    per_stage = FLOP_NEURON_STAGE * N + FLOP_COEF1_STAGE * N * nt + FLOP_COEF2_STAGE * n_has2 * nt
+    if pair_gates:
+        n_sec_types = int(np.count_nonzero(kinds))
+        per_stage += (FLOP_SYN_PAIR_STAGE * spec.n_synapses + FLOP_PAIR1_STAGE * N * nt
+                      + FLOP_PAIR2_STAGE * n_has2 * n_sec_types)
+    else:
+        per_stage += FLOP_SYN1_STAGE * n_syn1 + FLOP_SYN2_STAGE * n_syn2
     return 4.0 * per_stage
 
 
@@ -394,13 +404,18 @@ def main():
     peaks = measured_peaks()
     smax = peaks.get("sm_max_mhz", 2070.0)
     peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
-    flops_launch = workload_flops_per_step(spec) * args.chunk
-    dur = t_local / max(launches, 1)
-    roof = {"bound": "alu", "achieved": flops_launch / dur / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": flops_launch / dur / 1e12 / peak_tflops,
+    # one integrate call = the size-class launches back to back, together
+    # covering every network once: its FLOP over its duration
+    pair_gates = info["n_pair_gate_nets"] == spec.n_nets
+    flops_call = workload_flops_per_step(spec, pair_gates) * args.chunk
+    dur = t_local / args.steps
+    roof = {"bound": "alu", "achieved": flops_call / dur / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": flops_call / dur / 1e12 / peak_tflops,
             "traffic": traffic_for("net_kernel", args.workload),
-            "kernel": "net_kernel (all size classes)", "peak_source": f"FP32 FMA pipes: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                                                    f"{smax:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"}
+            "kernel": f"net_kernel: the {info['n_launch_classes']} size-class launches of one integrate call",
+            "gates": "per (presynaptic neuron, type) pair" if pair_gates else "per synapse",
+            "peak_source": f"FP32 FMA pipes: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                           f"{smax:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -260,8 +260,10 @@ const char *psst_last_error(void);
  *
  * psst_integrate_grid_noalloc advances the single network *net by n_steps
  * RK4 steps starting at global step index step0, exactly like
- * psst_integrate in PSST_MODE_GRID (same kernel; with the same item_chunks
- * the results are bitwise identical).  It runs on the current device and
+ * psst_integrate in PSST_MODE_GRID with one gate per synapse (same kernel;
+ * with gate_mode = 1 and the same item_chunks the results are bitwise
+ * identical; the per-pair gate table of psst_integrate groups the synaptic
+ * sums by type and agrees to rounding).  It runs on the current device and
  * `stream`.  Its first call on a device looks up that device's address of
  * the fixed array (cudaGetSymbolAddress); make that first call before any
  * stream capture.  Each call synchronises `stream` once, after planning and

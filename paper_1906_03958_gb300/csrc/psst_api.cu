@@ -62,6 +62,7 @@ struct PlanInput {
     int n_nets = 0, nt = 0, user_K = 0, user_block = 0;
     bool force_synapse_gates = false;
     std::vector<int> net_off, n1, n2;
+    std::vector<int> tcnt;       // [N][nt] synapses of each type per row
     std::vector<long long> net_syn;
     std::vector<uint8_t> flags;  // NET_HAS2 | NET_PAIR per network
 };
@@ -228,18 +229,22 @@ int validate(const psst_network_desc *d) {
     return PSST_OK;
 }
 
-// Per-row counts of first- and second-order synapses, and which networks
-// hold second-order synapses.
-void row_counts(const psst_network_desc *d, std::vector<int> &n1, std::vector<int> &n2, std::vector<uint8_t> &has2) {
+// Per-row counts of first- and second-order synapses and of each synapse
+// type, and which networks hold second-order synapses.
+void row_counts(const psst_network_desc *d, std::vector<int> &n1, std::vector<int> &n2, std::vector<int> &tcnt,
+                std::vector<uint8_t> &has2) {
     const long long N = d->net_neuron_off[d->n_nets];
+    const int nt = d->n_syn_types;
     n1.assign((size_t)N, 0);
     n2.assign((size_t)N, 0);
+    tcnt.assign((size_t)N * nt, 0);
     has2.assign((size_t)d->n_nets, 0);
     for (int b = 0; b < d->n_nets; ++b) {
         for (long long i = d->net_neuron_off[b]; i < d->net_neuron_off[b + 1]; ++i) {
             for (long long k = d->row_ptr[i]; k < d->row_ptr[i + 1]; ++k) {
                 if (d->syn_params[(size_t)d->syn_type[k] * PSST_SYN_NPARAM] != 0.0f) ++n2[i];
                 else ++n1[i];
+                ++tcnt[(size_t)i * nt + d->syn_type[k]];
             }
             if (n2[i]) has2[b] = 1;
         }
@@ -294,10 +299,19 @@ struct Share {  // one CTA's share of a network
 };
 
 // Shares of `parts` CTAs over rows [0, n) (row i of the network at n1[i],
-// n2[i]) and the work-item size.
-void make_shares(const int *n1, const int *n2, int n, int parts, int user_K, std::vector<Share> &sh, int *K) {
+// n2[i]) and the work-item size.  With tcnt (per row, synapses of each of
+// the nt types) the items are the per-pair variant's typed items, all in
+// list 1.
+void make_shares(const int *n1, const int *n2, const int *tcnt, int nt, int n, int parts, int user_K,
+                 std::vector<Share> &sh, int *K) {
+    auto row_chunks = [&](int i) -> long long {
+        if (!tcnt) return (n1[i] + 3) / 4 + (n2[i] + 3) / 4;
+        long long c = 0;
+        for (int t = 0; t < nt; ++t) c += (tcnt[(size_t)i * nt + t] + 3) / 4;
+        return c;
+    };
     std::vector<double> cost((size_t)n);
-    for (int i = 0; i < n; ++i) cost[i] = (n1[i] + 3) / 4 + (n2[i] + 3) / 4 + 2.0;
+    for (int i = 0; i < n; ++i) cost[i] = (double)row_chunks(i) + 2.0;
     std::vector<int> split;
     balanced_split(cost, parts, split);
     sh.assign((size_t)parts, Share{});
@@ -305,15 +319,19 @@ void make_shares(const int *n1, const int *n2, int n, int parts, int user_K, std
     for (int q = 0; q < parts; ++q) {
         sh[q].r0 = split[q];
         sh[q].r1 = split[q + 1];
-        for (int i = split[q]; i < split[q + 1]; ++i) sh[q].chunks += (n1[i] + 3) / 4 + (n2[i] + 3) / 4;
+        for (int i = split[q]; i < split[q + 1]; ++i) sh[q].chunks += row_chunks(i);
         worst = std::max(worst, sh[q].chunks);
     }
     *K = choose_K(worst, user_K);
     for (int q = 0; q < parts; ++q) {
         sh[q].items1 = sh[q].items2 = 0;
         for (int i = split[q]; i < split[q + 1]; ++i) {
-            sh[q].items1 += psst::part_items(n1[i], *K);
-            sh[q].items2 += psst::part_items(n2[i], *K);
+            if (tcnt) {
+                sh[q].items1 += psst::typed_row_items(tcnt + (size_t)i * nt, nt, *K);
+            } else {
+                sh[q].items1 += psst::part_items(n1[i], *K);
+                sh[q].items2 += psst::part_items(n2[i], *K);
+            }
         }
     }
 }
@@ -321,7 +339,7 @@ void make_shares(const int *n1, const int *n2, int n, int parts, int user_K, std
 // Dynamic shared memory of one CTA of a network of N neurons in CTA mode.
 long long cta_share_bytes(int N, int nt, bool has2, bool pair, const Share &s, int K) {
     const psst::NeuronLayout L = psst::make_nlayout(s.r1 - s.r0, N, N * nt, has2, pair);
-    return L.syn + (pair ? psst::items_smem_bytes_pair(s.items1, s.items2, K, s.r1 - s.r0)
+    return L.syn + (pair ? psst::items_smem_bytes_pair(s.items1, K, s.r1 - s.r0)
                          : psst::items_smem_bytes(s.items1, s.items2, K, s.r1 - s.r0, has2));
 }
 
@@ -334,7 +352,8 @@ int plan_network(const PlanInput &in, int b, const SmemCaps &caps, psst::NetPlan
         if (cl > 1 && N < 2 * cl) break;
         std::vector<Share> sh;
         int K = 1;
-        make_shares(n1.data() + n0, n2.data() + n0, N, cl, in.user_K, sh, &K);
+        make_shares(n1.data() + n0, n2.data() + n0, pair ? in.tcnt.data() + (size_t)n0 * nt : nullptr, nt, N, cl,
+                    in.user_K, sh, &K);
         long long worst = 0;
         for (int q = 0; q < cl; ++q) worst = std::max(worst, cta_share_bytes(N, nt, has2, pair, sh[q], K));
         if (worst <= caps.max_dyn) {
@@ -430,33 +449,42 @@ int setup_grid(psst_net *h, const SmemCaps &caps, cudaError_t *err) {
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "device attributes");
     const int parts = (int)std::max<long long>(1, std::min<long long>(sms, (N + 7) / 8));
+    psst::GridView &g = h->gv;
+    // per-pair plan (typed items next to the compact gate table), else per synapse
+    auto plan = [&](bool pair, std::vector<Share> &sh, int *K) -> long long {
+        make_shares(in.n1.data(), in.n2.data(), pair ? in.tcnt.data() : nullptr, nt, (int)N, parts, in.user_K, sh,
+                    K);
+        long long need = 0;
+        for (int c = 0; c < parts; ++c) {
+            const int n = sh[c].r1 - sh[c].r0;
+            const long long bytes =
+                pair ? psst::make_nlayout(n, n, n * nt, has2, true).syn + 4LL * g.mt +
+                           psst::items_smem_bytes_pair(sh[c].items1, *K, n)
+                     : psst::make_nlayout(n, n, n * nt, has2).syn +
+                           psst::items_smem_bytes(sh[c].items1, sh[c].items2, *K, n, has2);
+            need = std::max(need, bytes);
+        }
+        return need;
+    };
     std::vector<Share> sh;
     int K = 1;
-    make_shares(in.n1.data(), in.n2.data(), (int)N, parts, in.user_K, sh, &K);
-    psst::GridView &g = h->gv;
     bool pair = (in.flags[0] & psst::NET_PAIR) && g.tix != nullptr;
+    long long need = pair ? plan(true, sh, &K) : 0;
+    if (pair && need > caps.max_dyn) pair = false;
+    if (!pair) need = plan(false, sh, &K);
+    if (need > caps.max_dyn)
+        return fail(PSST_ERR_UNSUPPORTED, "grid mode: a block needs %lld B of shared memory (max %d)", need,
+                    caps.max_dyn);
     std::vector<int> split((size_t)parts + 1), items((size_t)2 * parts);
-    long long need = 0, need_pair = 0;
     for (int c = 0; c < parts; ++c) {
-        const int n = sh[c].r1 - sh[c].r0;
-        const long long bytes = psst::make_nlayout(n, n, n * nt, has2).syn +
-                                psst::items_smem_bytes(sh[c].items1, sh[c].items2, K, n, has2);
-        const long long bytes_pair = psst::make_nlayout(n, n, n * nt, has2, true).syn + 4LL * g.mt +
-                                     psst::items_smem_bytes_pair(sh[c].items1, sh[c].items2, K, n);
         split[c] = sh[c].r0;
         items[c] = sh[c].items1;
         items[parts + c] = sh[c].items2;
-        need = std::max(need, bytes);
-        need_pair = std::max(need_pair, bytes_pair);
     }
     split[parts] = (int)N;
-    if (pair && need_pair > caps.max_dyn) pair = false;
-    if (!pair && need > caps.max_dyn)
-        return fail(PSST_ERR_UNSUPPORTED, "grid mode: a block needs %lld B of shared memory (max %d)", need,
-                    caps.max_dyn);
     if (!h->block) h->block = 1024;
     h->K = K;
-    h->smem = (int)(pair ? need_pair : need);
+    h->smem = (int)need;
     int per_sm = 0;
     // the kernel attribute is an upper bound shared by every handle's launches
     e = psst::grid_occupancy(h->block, caps.max_dyn, &per_sm);
@@ -599,7 +627,7 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
     for (int b = 0; b < n_nets; ++b)
         pin.net_syn[b] = d->row_ptr[d->net_neuron_off[b + 1]] - d->row_ptr[d->net_neuron_off[b]];
     std::vector<uint8_t> has2;
-    row_counts(d, pin.n1, pin.n2, has2);
+    row_counts(d, pin.n1, pin.n2, pin.tcnt, has2);
     pin.flags.assign(n_nets, 0);
     {
         const std::vector<uint8_t> uni = uniform_pairs(d->init_state, pin, d->row_ptr, d->pre, d->syn_type, N, S);

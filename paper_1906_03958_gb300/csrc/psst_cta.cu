@@ -74,12 +74,12 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
     const float *vcur = vst + (ST & 1) * N;
     float *vnxt = vst + ((ST + 1) & 1) * N;
     float *r0p = pst, *s0p = pst + M, *Gt = pst + 2 * M;
-    if (PAIR) sphase_pair(it, Gt, HAS2);
+    if (PAIR) sphase_pair(it, Gt);
     else sphase<ST, HAS2>(it, SmemCoef{ST == 0 ? fin1 : cur1, ST == 0 ? fin2 : cur2});
     __syncthreads();
     for (int i = tid; i < nown; i += nthr) {
         const float V = vcur[r_lo + i];
-        const float isyn = row_current<HAS2>(it, i, V);
+        const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
         const float vn = neuron_update<ST>(i, nown, V, y0, acc, ys, prm, iext[i], isyn, dt);
         vnxt[r_lo + i] = vn;
         if (CL > 1) {
@@ -133,7 +133,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     float4 *fin2 = HAS2 ? (float4 *)(smem + L.fin2) : nullptr;
     int *tmp = (int *)(smem + L.tmp);
     float *pst = PAIR ? (float *)(smem + L.pair) : nullptr;
-    Items it = PAIR ? carve_items_pair(smem + L.syn, nown, pl.K, pl.n1[rank], pl.n2[rank])
+    Items it = PAIR ? carve_items_pair(smem + L.syn, nown, pl.K, pl.n1[rank])
                     : carve_items(smem + L.syn, nown, pl.K, pl.n1[rank], pl.n2[rank], HAS2);
 
     float *gV = v.state + n0;
@@ -182,7 +182,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
             pst[2 * M + p] = pair_gate(sec, fin1[p], HAS2 ? fin2[p] : make_float4(0.f, 0.f, 1.f, 1.f), pst[p],
                                        pst[M + p]);
         }
-        load_items_pair<HAS2>(it, v, n0, sbase, r_lo, gw, gcode, stab, tmp, nullptr);  // ends with __syncthreads
+        load_items_pair(it, v, n0, sbase, r_lo, gw, gcode, stab, tmp, nullptr);  // ends with __syncthreads
     } else {
         load_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gw, gcode, stab, tmp);  // ends with __syncthreads
     }

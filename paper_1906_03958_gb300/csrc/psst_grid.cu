@@ -102,14 +102,14 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
 #pragma unroll 4
         for (int q = tid; q < n4; q += nthr) dst[q] = __ldcg(src + q);
         __syncthreads();
-        sphase_pair(it, gtab, HAS2);
+        sphase_pair(it, gtab);
     } else {
         sphase<ST, HAS2>(it, GlobalCoef{g.c1 + (size_t)(ST & 1) * M, HAS2 ? g.c2 + (size_t)(ST & 1) * M : nullptr});
     }
     __syncthreads();
     for (int i = tid; i < N; i += nthr) {
         const float V = vcur[i];
-        const float isyn = row_current<HAS2>(it, i, V);
+        const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
         const float vn = neuron_update<ST>(i, N, V, y0, acc, ys, prm, iext[i], isyn, dt);
         vnxt[i] = vn;
         if (ST == 3 && v.rec_stride > 0 && ((step + 1) % v.rec_stride) == 0) {
@@ -179,7 +179,7 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
     float *pst = PAIR ? (float *)(smem + L.pair) : nullptr;
     float *gtab = PAIR ? (float *)(smem + L.syn) : nullptr;
     const int items1 = g.items[blockIdx.x], items2 = g.items[gridDim.x + blockIdx.x];
-    Items it = PAIR ? carve_items_pair(smem + L.syn + 4LL * g.mt, N, g.K, items1, items2)
+    Items it = PAIR ? carve_items_pair(smem + L.syn + 4LL * g.mt, N, g.K, items1)
                     : carve_items(smem + L.syn, N, g.K, items1, items2, HAS2);
 
     float *gV = v.state + lo;
@@ -222,7 +222,7 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
             r0p[p] = r0;
             s0p[p] = s0;
         }
-        load_items_pair<HAS2>(it, v, 0, 0, lo, v.weight, v.syn_code, stab, tmp, g.tix);
+        load_items_pair(it, v, 0, 0, lo, v.weight, v.syn_code, stab, tmp, g.tix);
     } else {
         // identity step-end maps of the own pairs in table 0 (read by stage 0)
         for (int p = tid; p < Mloc; p += nthr) {

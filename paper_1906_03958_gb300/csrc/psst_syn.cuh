@@ -277,133 +277,125 @@ __device__ __forceinline__ float row_current(const Items &it, int i, float V) {
 //
 // When all gates of a (presynaptic neuron, type) pair hold the same value
 // (true from rest, and preserved by the dynamics), each stage's gate value
-// is computed once per pair, G_p = P_s + Q_s r0_p with the same FMA as the
-// per-synapse path, so the two paths give bitwise-identical sums.  The items
-// then carry no gate state: float4 w, wE and ushort4 gate-table index.
+// is computed once per pair, G_p = P_s + Q_s r0_p with the same operations
+// as the per-synapse path, and the items carry no gate state.  A row's
+// synapses are then cut into items per synapse type, so that an item needs
+// only A = sum w G (the reversal potential E is the item's, not the
+// synapse's): chunk = float4 w + ushort4 gate-table index, one partial per
+// item, and I_syn,i = V_i sum_t A_t - sum_t E_t A_t over the row's items in
+// item order (bitwise reproducible for a given K).
 
-__host__ __device__ inline long long items_smem_bytes_pair(int n1, int n2, int K, int nrows) {
-    const long long c = (long long)K * (n1 + n2);
-    return c * (16 * 2 + 8) + 8LL * (n1 + n2) + 8LL * (nrows + 1) + 64;
+__host__ __device__ inline long long items_smem_bytes_pair(int n_items, int K, int nrows) {
+    const long long c = (long long)K * n_items;
+    return c * (16 + 8) + 8LL * n_items + 4LL * (nrows + 1) + 64;
 }
 
-__device__ inline Items carve_items_pair(unsigned char *base, int nrows, int K, int n1, int n2) {
+__device__ inline Items carve_items_pair(unsigned char *base, int nrows, int K, int n_items) {
     Items it;
     it.nrows = nrows;
     it.K = K;
-    it.n1 = n1;
-    it.n2 = n2;
-    const long long c = (long long)K * (n1 + n2);
+    it.n1 = n_items;
+    it.n2 = 0;
+    const long long c = (long long)K * n_items;
     unsigned char *p = base;
     it.r = nullptr;
     it.s = nullptr;
+    it.we = nullptr;
     it.w = (float4 *)p;
-    p += 16 * c;
-    it.we = (float4 *)p;
     p += 16 * c;
     it.id = (ushort4 *)p;
     p += 8 * c;
-    it.pa = (float *)p;
-    p += 4LL * (n1 + n2);
-    it.pb = (float *)p;
-    p += 4LL * (n1 + n2);
+    it.pa = (float *)p;   // item partial A
+    p += 4LL * n_items;
+    it.pb = (float *)p;   // item's reversal potential E
+    p += 4LL * n_items;
     it.ib1 = (int *)p;
-    p += 4LL * (nrows + 1);
-    it.ib2 = (int *)p;
+    it.ib2 = nullptr;
     return it;
 }
 
-// Items of rows [row0, row0 + nrows) without gate state; the gate-table
-// index of a synapse is its (neuron, type) pair index, or tix[pair] when a
-// compact table of the used pairs is given.
-template <bool HAS2>
-__device__ void load_items_pair(Items &it, const NetView &v, long long row_g0, long long sbase, int row0,
+// Synapses of a row part of one type in items of K chunks.
+__host__ __device__ inline int typed_row_items(const int *cnt, int nt, int K) {
+    int n = 0;
+    for (int t = 0; t < nt; ++t) n += part_items(cnt[t], K);
+    return n;
+}
+
+// Items of rows [row0, row0 + nrows), per row one run of items per synapse
+// type (types in increasing order); the gate-table index of a synapse is its
+// (neuron, type) pair index, or tix[pair] when a compact table of the used
+// pairs is given.  tmp: shared scratch of nrows + 1 ints.
+__device__ inline void load_items_pair(Items &it, const NetView &v, long long row_g0, long long sbase, int row0,
                                 const float *gw, const uint32_t *gcode, const float *stab, int *tmp,
                                 const int *tix) {
-    const int tid = threadIdx.x, nthr = blockDim.x, nrows = it.nrows, K = it.K;
-    int *c1 = tmp, *c2 = tmp + nrows + 1;
+    const int tid = threadIdx.x, nthr = blockDim.x, nrows = it.nrows, K = it.K, nt = v.n_stypes;
     for (int i = tid; i < nrows; i += nthr) {
         const long long k0 = v.row_ptr[row_g0 + row0 + i] - sbase, k1 = v.row_ptr[row_g0 + row0 + i + 1] - sbase;
-        int n2 = 0;
-        if (HAS2)
-            for (long long k = k0; k < k1; ++k) n2 += second_order(stab, gcode[k]);
-        c1[i] = part_items((int)(k1 - k0) - n2, K);
-        c2[i] = part_items(n2, K);
+        int cnt[PSST_MAX_SYN_TYPES] = {};
+        for (long long k = k0; k < k1; ++k) ++cnt[gcode[k] >> 24];
+        tmp[i] = typed_row_items(cnt, nt, K);
     }
     __syncthreads();
-    block_scan(c1, it.ib1, nrows);
-    block_scan(c2, it.ib2, nrows);
-    const long long chunks = (long long)K * (it.n1 + it.n2);
+    block_scan(tmp, it.ib1, nrows);
+    const long long chunks = (long long)K * it.n1;
     for (long long c = tid; c < chunks; c += nthr) {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        it.w[c] = z;
-        it.we[c] = z;
+        it.w[c] = make_float4(0.f, 0.f, 0.f, 0.f);
         it.id[c] = make_ushort4(0, 0, 0, 0);
     }
     __syncthreads();
-    float *W = (float *)it.w, *WE = (float *)it.we;
+    float *W = (float *)it.w;
     unsigned short *ID = (unsigned short *)it.id;
     for (int i = tid; i < nrows; i += nthr) {
         const long long k0 = v.row_ptr[row_g0 + row0 + i] - sbase, k1 = v.row_ptr[row_g0 + row0 + i + 1] - sbase;
-        int m1 = 0, m2 = 0;
+        int cnt[PSST_MAX_SYN_TYPES] = {}, base[PSST_MAX_SYN_TYPES], m[PSST_MAX_SYN_TYPES] = {};
+        for (long long k = k0; k < k1; ++k) ++cnt[gcode[k] >> 24];
+        int b = it.ib1[i];
+        for (int t = 0; t < nt; ++t) {
+            base[t] = b;
+            const int q = part_items(cnt[t], K);
+            for (int u = 0; u < q; ++u) it.pb[b + u] = stab[t * 9 + SP_E];
+            b += q;
+        }
         for (long long k = k0; k < k1; ++k) {
             const uint32_t code = gcode[k];
-            const bool sec = HAS2 && second_order(stab, code);
-            const long long p = sec ? item_slot(it.ib2[i], m2++, K, it.n2, K * it.n1)
-                                    : item_slot(it.ib1[i], m1++, K, it.n1, 0);
-            const float w = gw[k];
-            W[p] = w;
-            WE[p] = w * stab[(code >> 24) * 9 + SP_E];
+            const int t = (int)(code >> 24);
+            const long long p = item_slot(base[t], m[t]++, K, it.n1, 0);
             const uint32_t ci = code & 0xFFFFFFu;
+            W[p] = gw[k];
             ID[p] = (unsigned short)(tix ? tix[ci] : (int)ci);
         }
     }
     __syncthreads();
 }
 
-// S-phase of the per-pair variant: the gate of every synapse is Gt[id].
-__device__ __forceinline__ void sphase_pair(const Items &it, const float *Gt, bool has2) {
-    const int tid = threadIdx.x, nthr = blockDim.x, K = it.K, n1 = it.n1;
-    for (int t = tid; t < n1; t += nthr) {
-        float A = 0.0f, B = 0.0f;
+// S-phase of the per-pair variant: every item's A = sum w G with G = Gt[id].
+__device__ __forceinline__ void sphase_pair(const Items &it, const float *Gt) {
+    const int tid = threadIdx.x, nthr = blockDim.x, K = it.K, n = it.n1;
+    for (int t = tid; t < n; t += nthr) {
+        float A = 0.0f;
         for (int j = 0; j < K; ++j) {
-            const int c = j * n1 + t;
-            const float4 w = it.w[c], we = it.we[c];
+            const int c = j * n + t;
+            const float4 w = it.w[c];
             const ushort4 id = it.id[c];
             const float g0 = Gt[id.x], g1 = Gt[id.y], g2 = Gt[id.z], g3 = Gt[id.w];
             A = fmaf(w.x, g0, A);
-            B = fmaf(we.x, g0, B);
             A = fmaf(w.y, g1, A);
-            B = fmaf(we.y, g1, B);
             A = fmaf(w.z, g2, A);
-            B = fmaf(we.z, g2, B);
             A = fmaf(w.w, g3, A);
-            B = fmaf(we.w, g3, B);
         }
         it.pa[t] = A;
-        it.pb[t] = B;
     }
-    if (has2) {
-        const int n2 = it.n2, base = K * n1;
-        for (int t = tid; t < n2; t += nthr) {
-            float A = 0.0f, B = 0.0f;
-            for (int j = 0; j < K; ++j) {
-                const int c = base + j * n2 + t;
-                const float4 w = it.w[c], we = it.we[c];
-                const ushort4 id = it.id[c];
-                const float g0 = Gt[id.x], g1 = Gt[id.y], g2 = Gt[id.z], g3 = Gt[id.w];
-                A = fmaf(w.x, g0, A);
-                B = fmaf(we.x, g0, B);
-                A = fmaf(w.y, g1, A);
-                B = fmaf(we.y, g1, B);
-                A = fmaf(w.z, g2, A);
-                B = fmaf(we.z, g2, B);
-                A = fmaf(w.w, g3, A);
-                B = fmaf(we.w, g3, B);
-            }
-            it.pa[n1 + t] = A;
-            it.pb[n1 + t] = B;
-        }
+}
+
+// Synaptic current of owned row i from its typed items (fixed order).
+__device__ __forceinline__ float row_current_pair(const Items &it, int i, float V) {
+    float A = 0.0f, B = 0.0f;
+    for (int t = it.ib1[i]; t < it.ib1[i + 1]; ++t) {
+        const float a = it.pa[t];
+        A += a;
+        B = fmaf(it.pb[t], a, B);
     }
+    return fmaf(V, A, -B);
 }
 
 // Gate value G of a pair from its stage maps and step-start gates, with

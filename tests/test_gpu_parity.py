@@ -313,21 +313,29 @@ def test_autotune_keeps_results_bitwise():
         np.testing.assert_array_equal(a.get_state_numpy(), b.get_state_numpy())
 
 
-def test_pair_gates_bitwise_equal_to_per_synapse_gates():
-    # one gate per (presynaptic neuron, type) pair evaluates the same FMAs as
-    # one gate per synapse when the pair's gates are equal (from rest)
+def test_pair_gates_agree_with_per_synapse_gates():
+    # one gate per (presynaptic neuron, type) pair and one per synapse reach
+    # the same RK4 map; only the summation grouping of the synaptic current
+    # differs (typed items), so both meet the single-step bound against the
+    # oracle and stay together over a short horizon
+    from paper_1906_03958_gb300 import psst
     specs = [ng.antennal_lobe(seed=61), ng.antennal_lobe(seed=62, n_pn=40, n_ln=20)]
     spec = ng.concat_specs(specs)
-    y0 = oracle.rest_state(spec).astype(np.float32)
-    out = []
+    N, S = spec.n_neurons, spec.n_synapses
+    y32 = oracle.integrate(spec, oracle.rest_state(spec), 40, step0=9900)[0].astype(np.float32)
+    y64, _ = oracle.integrate(spec, y32.astype(np.float64), 1, step0=9940)
+    traj = []
     for gm in (0, 1):
-        with _net(spec, init_state=y0, gate_mode=gm, rec_stride=20, rec_capacity=100) as net:
-            net.set_step(9900)
-            net.integrate(600)
+        with _net(spec, init_state=y32, gate_mode=gm, rec_stride=20, rec_capacity=100) as net:
+            assert net.info()["n_pair_gate_nets"] == (2 if gm == 0 else 0)
+            net.set_step(9940)
+            net.integrate(1)
             net.status()
-            out.append((net.get_state_numpy(), net.read_record()))
-    np.testing.assert_array_equal(out[0][0], out[1][0])
-    np.testing.assert_array_equal(out[0][1], out[1][1])
+            assert step_error(net.get_state_numpy(), y64, N, S) <= STEP_TOL
+            net.integrate(299)
+            net.status()
+            traj.append(net.read_record())
+    np.testing.assert_allclose(traj[0], traj[1], rtol=0, atol=1e-3)
 
 
 def test_set_state_switches_gate_layout():

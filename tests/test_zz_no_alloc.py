@@ -54,7 +54,9 @@ def test_noalloc_matches_grid_mode_on_two_calls():
     spec.pulse_on[:] = 40
     spec.pulse_off[:] = 220
     K = 3
-    with psst.Network(spec, mode=psst.MODE_GRID, item_chunks=K, rec_stride=10, rec_capacity=100) as ref:
+    # the no-alloc call keeps one gate per synapse: compare with gate_mode 1
+    with psst.Network(spec, mode=psst.MODE_GRID, item_chunks=K, gate_mode=1, rec_stride=10,
+                      rec_capacity=100) as ref:
         state = ref.get_state().clone()          # caller-owned buffers
         rec = torch.zeros((100, spec.n_neurons), dtype=torch.float32, device=state.device)
         err = torch.zeros(1, dtype=torch.int32, device=state.device)
