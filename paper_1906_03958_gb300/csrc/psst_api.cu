@@ -124,8 +124,38 @@ struct psst_net {
         *p = (T *)q;
         return e;
     }
+    // CTA mode: one stream per size class; an integrate call forks them off
+    // the caller's stream and joins them back, so the classes' launches run
+    // concurrently and one class's tail overlaps the others' work
+    std::vector<cudaStream_t> class_streams;
+    std::vector<cudaEvent_t> class_events;  // [0] fork, [1 + c] join of class c
+
+    void drop_streams() {
+        for (cudaStream_t s : class_streams) cudaStreamDestroy(s);
+        for (cudaEvent_t e : class_events) cudaEventDestroy(e);
+        class_streams.clear();
+        class_events.clear();
+    }
+    cudaError_t make_streams(size_t n) {
+        if (class_streams.size() == n) return cudaSuccess;
+        drop_streams();
+        for (size_t i = 0; i < n; ++i) {
+            cudaStream_t s;
+            cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return e;
+            class_streams.push_back(s);
+        }
+        for (size_t i = 0; i <= n; ++i) {
+            cudaEvent_t ev;
+            cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+            class_events.push_back(ev);
+        }
+        return cudaSuccess;
+    }
     void release() {
         drop_graph();
+        drop_streams();
         for (void *p : allocs) cudaFree(p);
         allocs.clear();
     }
@@ -567,6 +597,7 @@ int setup_cta(psst_net *h, const SmemCaps &caps, cudaError_t *err) {
         h->classes[i].plans = dp;
         e = psst::cta_prepare(h->classes[i].cl, caps.max_dyn);
     }
+    if (e == cudaSuccess) e = h->make_streams(h->classes.size() > 1 ? h->classes.size() : 0);
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "CTA mode setup");
     h->block = h->classes.empty() ? 0 : h->classes.back().block;
     h->K = plans.empty() ? 0 : plans[h->classes.empty() ? 0 : all_lists.back()].K;
@@ -756,9 +787,34 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
 
 namespace {
 
+int launch_chunks(psst_net *h, long long step0, long long n_steps, long long chunk, cudaStream_t st);
+
 // Launch the kernels for n_steps steps starting at global step `step0`.
 int launch_steps(psst_net *h, long long step0, long long n_steps, cudaStream_t st) {
     const long long chunk = 1LL << 30;
+    const bool fork = h->mode != PSST_MODE_GRID && !h->class_streams.empty();
+    if (fork) {
+        // the class streams start after everything queued on st so far
+        cudaError_t e = cudaEventRecord(h->class_events[0], st);
+        for (size_t c = 0; e == cudaSuccess && c < h->class_streams.size(); ++c)
+            e = cudaStreamWaitEvent(h->class_streams[c], h->class_events[0], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "psst_integrate fork");
+    }
+    const int rc = launch_chunks(h, step0, n_steps, chunk, st);
+    if (fork) {
+        // st continues once every class is done (also on a launch error)
+        cudaError_t e = cudaSuccess;
+        for (size_t c = 0; c < h->class_streams.size(); ++c) {
+            const cudaError_t e1 = cudaEventRecord(h->class_events[1 + c], h->class_streams[c]);
+            const cudaError_t e2 = cudaStreamWaitEvent(st, h->class_events[1 + c], 0);
+            if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+        }
+        if (e != cudaSuccess && !rc) return cuda_fail(e, "psst_integrate join");
+    }
+    return rc;
+}
+
+int launch_chunks(psst_net *h, long long step0, long long n_steps, long long chunk, cudaStream_t st) {
     for (long long done = 0; done < n_steps;) {
         const int n = (int)std::min<long long>(chunk, n_steps - done);
         if (h->mode == PSST_MODE_GRID) {
@@ -766,8 +822,10 @@ int launch_steps(psst_net *h, long long step0, long long n_steps, cudaStream_t s
             if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
             ++h->launches;
         } else {
-            for (const psst::ClassLaunch &c : h->classes) {
-                cudaError_t e = psst::cta_launch(h->v, c, step0 + done, n, st);
+            const bool fork = !h->class_streams.empty();
+            for (size_t c = 0; c < h->classes.size(); ++c) {
+                cudaError_t e = psst::cta_launch(h->v, h->classes[c], step0 + done, n,
+                                                 fork ? h->class_streams[c] : st);
                 if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
                 ++h->launches;
             }
