@@ -46,6 +46,7 @@ FLOP_SYN2_STAGE = 14         # per-synapse gates, second order: + s map, s^4 / (
 FLOP_SYN_PAIR_STAGE = 4      # per-pair gates: A += w G, B += wE G (the gate is gathered)
 FLOP_PAIR1_STAGE = 2         # per-pair gates: G = P + Q r0 of a first-order (neuron, type) pair
 FLOP_PAIR2_STAGE = 10        # per-pair gates, second order: + s map, s^4 / (s^4 + Kd)
+# (per-pair gates: gate maps are updated for the pairs that have synapses only)
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 
@@ -65,13 +66,19 @@ def workload_flops_per_step(spec, pair_gates: bool = True) -> float:
     has2 = np.zeros(spec.n_nets, bool)
     has2[np.unique(net_of_syn)] = True
     n_has2 = int(spec.net_sizes()[has2].sum())
-    per_stage = FLOP_NEURON_STAGE * N + FLOP_COEF1_STAGE * N * nt + FLOP_COEF2_STAGE * n_has2 * nt
     if pair_gates:
-        n_sec_types = int(np.count_nonzero(kinds))
-        per_stage += (FLOP_SYN_PAIR_STAGE * spec.n_synapses + FLOP_PAIR1_STAGE * N * nt
-                      + FLOP_PAIR2_STAGE * n_has2 * n_sec_types)
+        # gate maps and gates of the (presynaptic neuron, type) pairs that have synapses
+        net_of_syn = np.searchsorted(spec.row_ptr[spec.net_neuron_off], np.arange(spec.n_synapses),
+                                     side="right") - 1
+        pre_global = spec.net_neuron_off[net_of_syn].astype(np.int64) + spec.pre
+        pairs = np.unique(pre_global * nt + spec.syn_type)
+        sec_pairs = int(np.count_nonzero(kinds[pairs % nt]))
+        per_stage = (FLOP_NEURON_STAGE * N + FLOP_SYN_PAIR_STAGE * spec.n_synapses
+                     + (FLOP_COEF1_STAGE + FLOP_PAIR1_STAGE) * len(pairs)
+                     + (FLOP_COEF2_STAGE + FLOP_PAIR2_STAGE) * sec_pairs)
     else:
-        per_stage += FLOP_SYN1_STAGE * n_syn1 + FLOP_SYN2_STAGE * n_syn2
+        per_stage = (FLOP_NEURON_STAGE * N + FLOP_COEF1_STAGE * N * nt + FLOP_COEF2_STAGE * n_has2 * nt
+                     + FLOP_SYN1_STAGE * n_syn1 + FLOP_SYN2_STAGE * n_syn2)
     return 4.0 * per_stage
 
 

@@ -63,6 +63,7 @@ struct PlanInput {
     bool force_synapse_gates = false;
     std::vector<int> net_off, n1, n2;
     std::vector<int> tcnt;       // [N][nt] synapses of each type per row
+    std::vector<int> pair_off;   // [n_nets + 1] used (presynaptic neuron, type) pairs of the networks
     std::vector<long long> net_syn;
     std::vector<uint8_t> flags;  // NET_HAS2 | NET_PAIR per network
 };
@@ -367,8 +368,8 @@ void make_shares(const int *n1, const int *n2, const int *tcnt, int nt, int n, i
 }
 
 // Dynamic shared memory of one CTA of a network of N neurons in CTA mode.
-long long cta_share_bytes(int N, int nt, bool has2, bool pair, const Share &s, int K) {
-    const psst::NeuronLayout L = psst::make_nlayout(s.r1 - s.r0, N, N * nt, has2, pair);
+long long cta_share_bytes(int N, int nt, int used_pairs, bool has2, bool pair, const Share &s, int K) {
+    const psst::NeuronLayout L = psst::make_nlayout(s.r1 - s.r0, N, pair ? used_pairs : N * nt, has2, pair);
     return L.syn + (pair ? psst::items_smem_bytes_pair(s.items1, K, s.r1 - s.r0)
                          : psst::items_smem_bytes(s.items1, s.items2, K, s.r1 - s.r0, has2));
 }
@@ -385,7 +386,8 @@ int plan_network(const PlanInput &in, int b, const SmemCaps &caps, psst::NetPlan
         make_shares(n1.data() + n0, n2.data() + n0, pair ? in.tcnt.data() + (size_t)n0 * nt : nullptr, nt, N, cl,
                     in.user_K, sh, &K);
         long long worst = 0;
-        for (int q = 0; q < cl; ++q) worst = std::max(worst, cta_share_bytes(N, nt, has2, pair, sh[q], K));
+        const int used = in.pair_off[b + 1] - in.pair_off[b];
+        for (int q = 0; q < cl; ++q) worst = std::max(worst, cta_share_bytes(N, nt, used, has2, pair, sh[q], K));
         if (worst <= caps.max_dyn) {
             std::memset(pl, 0, sizeof *pl);
             pl->K = K;
@@ -440,25 +442,19 @@ int grid_pair_tables(psst_net *h, const psst_network_desc *d, cudaError_t *err) 
         const size_t p = (size_t)d->pre[k] * nt + d->syn_type[k];
         if (first[p] < 0) first[p] = k;
     }
-    std::vector<int> tix((size_t)M, -1);
-    std::vector<long long> rep;
+    std::vector<long long> rep;  // in pair order, as the compact index of the network's used pairs
     for (long long p = 0; p < M; ++p)
-        if (first[p] >= 0) {
-            tix[p] = (int)rep.size();
-            rep.push_back(first[p]);
-        }
+        if (first[p] >= 0) rep.push_back(first[p]);
     psst::GridView &g = h->gv;
     const long long used = (long long)rep.size();
     g.mt = (int)((used + 3) & ~3LL);
-    int *t = nullptr;
     long long *r = nullptr;
-    cudaError_t e = upload(h, &t, tix.data(), tix.size());
-    if (e == cudaSuccess) e = upload(h, &r, rep.data(), rep.size());
+    cudaError_t e = upload(h, &r, rep.data(), rep.size());
     if (e == cudaSuccess) e = h->alloc(&g.gt, (size_t)2 * g.mt);
     if (e == cudaSuccess) e = cudaMemset(g.gt, 0, (size_t)2 * std::max(g.mt, 1) * sizeof(float));
     if (e == cudaSuccess) e = h->alloc(&g.r0g, (size_t)used);
     if (e == cudaSuccess) e = h->alloc(&g.s0g, (size_t)used);
-    g.tix = t;
+    g.tix = h->v.pair_tix;
     g.rep = r;
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid pair tables");
     return PSST_OK;
@@ -666,6 +662,22 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
             pin.flags[b] = (has2[b] ? psst::NET_HAS2 : 0) |
                            (uni[b] && !pin.force_synapse_gates ? psst::NET_PAIR : 0);
     }
+    // compact index of each network's used (presynaptic neuron, type) pairs
+    std::vector<int> ptix((size_t)N * nt, -1), pof;
+    std::vector<int> &pair_off = pin.pair_off;
+    pair_off.assign((size_t)n_nets + 1, 0);
+    for (int b = 0; b < n_nets; ++b) {
+        const long long n0 = d->net_neuron_off[b], nb = d->net_neuron_off[b + 1] - n0;
+        int *tb = ptix.data() + n0 * nt;
+        for (long long k = d->row_ptr[n0]; k < d->row_ptr[n0 + nb]; ++k) tb[(size_t)d->pre[k] * nt + d->syn_type[k]] = 0;
+        pair_off[b] = (int)pof.size();
+        for (long long p = 0; p < nb * nt; ++p)
+            if (tb[p] == 0) {
+                tb[p] = (int)pof.size() - pair_off[b];
+                pof.push_back((int)p);
+            }
+    }
+    pair_off[n_nets] = (int)pof.size();
     bool all_fit = true;
     for (int b = 0; b < n_nets && all_fit; ++b) {
         psst::NetPlan pl;
@@ -700,6 +712,7 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
     for (long long k = 0; k < S; ++k)
         code[k] = ((uint32_t)d->syn_type[k] << 24) | (uint32_t)(d->pre[k] * nt + d->syn_type[k]);
 
+
     cudaError_t e = cudaSuccess;
     std::vector<long long> rp(d->row_ptr, d->row_ptr + N + 1);
     std::vector<long long> pon((size_t)n_nets, 0), poff((size_t)n_nets, 0);
@@ -727,6 +740,13 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
         UP(p_on, pon.data(), n_nets);
         UP(p_offp, poff.data(), n_nets);
         UP(p_fl, pin.flags.data(), n_nets);
+        int *p_tix, *p_pof, *p_poff;
+        UP(p_tix, ptix.data(), ptix.size());
+        UP(p_pof, pof.data(), pof.size());
+        UP(p_poff, pin.pair_off.data(), pin.pair_off.size());
+        v.pair_tix = p_tix;
+        v.pair_of = p_pof;
+        v.pair_off = p_poff;
         v.net_off = p_off;
         v.row_ptr = p_rp;
         v.syn_code = p_code;

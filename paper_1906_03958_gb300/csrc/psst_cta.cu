@@ -65,15 +65,18 @@ struct SmemCoef {
 };
 
 template <int ST, int CL, bool HAS2, bool PAIR>
-__device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0, int N, int nt, int r_lo, int nown,
+__device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0, int N, int nt, int M, int r_lo,
+                                      int nown,
                                       unsigned rank, int tq, long long step, float dt, float *vst, float *y0,
                                       float *acc, float *ys, const float *prm, const float *iext, float2 *cur1,
                                       float2 *acc1, float2 *fin1, float4 *cur2, float4 *acc2, float4 *fin2,
                                       float *pst, const float *stab) {
-    const int tid = threadIdx.x, nthr = blockDim.x, M = N * nt;
+    const int tid = threadIdx.x, nthr = blockDim.x;
     const float *vcur = vst + (ST & 1) * N;
     float *vnxt = vst + ((ST + 1) & 1) * N;
+    // gate-map entries: every (neuron, type) pair, or the used pairs (PAIR)
     float *r0p = pst, *s0p = pst + M, *Gt = pst + 2 * M;
+    const unsigned short *pof = (const unsigned short *)(pst + 3 * M);
     if (PAIR) sphase_pair(it, Gt);
     else sphase<ST, HAS2>(it, SmemCoef{ST == 0 ? fin1 : cur1, ST == 0 ? fin2 : cur2});
     __syncthreads();
@@ -96,10 +99,12 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
         float4 &c2 = HAS2 ? cur2[p] : d4;
         float4 &a2 = HAS2 ? acc2[p] : d4;
         float4 &f2 = HAS2 ? fin2[p] : d4;
-        coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], fin1[p], c2, a2, f2);
+        const int ci = PAIR ? (int)pof[p] : p;  // (neuron, type) pair of the entry
+        const float *sp = stab + (ci % nt) * 9;
+        coef_update<ST, HAS2>(sp, vcur[ci / nt], dt, cur1[p], acc1[p], fin1[p], c2, a2, f2);
         if (PAIR) {
             // the pair's gate for the next stage (same operations as the per-synapse path)
-            const bool sec = HAS2 && stab[(p % nt) * 9 + SP_KIND] != 0.0f;
+            const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
             if (ST < 3) {
                 Gt[p] = pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]);
             } else {
@@ -120,7 +125,10 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     const int tid = threadIdx.x, nthr = blockDim.x;
     const unsigned rank = CL > 1 ? cluster_rank() : 0u;
     const int n0 = v.net_off[b], N = v.net_off[b + 1] - n0;
-    const int nt = v.n_stypes, M = N * nt;
+    const int nt = v.n_stypes;
+    // gate-map entries: all (neuron, type) pairs, or the network's used pairs
+    const int M = PAIR ? v.pair_off[b + 1] - v.pair_off[b] : N * nt;
+    const int *ptix = PAIR ? v.pair_tix + (long long)n0 * nt : nullptr;  // local pair -> entry
     const long long sbase = v.row_ptr[n0];
     const int r_lo = pl.split[rank], nown = pl.split[rank + 1] - r_lo;
     const NeuronLayout L = make_nlayout(nown, N, M, HAS2, PAIR);
@@ -159,10 +167,14 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         inp[nown + i] = v.pulse_amp ? v.pulse_amp[n0 + gi] : 0.0f;
     }
     const long long pon = v.pulse_on[b], poff = v.pulse_off[b];
+    unsigned short *pof = PAIR ? (unsigned short *)(pst + 3 * M) : nullptr;
+    if (PAIR)
+        for (int k = tid; k < M; k += nthr) pof[k] = (unsigned short)v.pair_of[v.pair_off[b] + k];
     for (int k = tid; k < M; k += nthr) {
         fin1[k] = make_float2(0.0f, 1.0f);
         if (HAS2) {
-            const float *sp = stab + (k % nt) * 9;
+            const int ci = PAIR ? v.pair_of[v.pair_off[b] + k] : k;
+            const float *sp = stab + (ci % nt) * 9;
             fin2[k] = make_float4(0.0f, 0.0f, 1.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
         }
     }
@@ -172,17 +184,17 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         __syncthreads();
         const int S = (int)(v.row_ptr[n0 + N] - sbase);
         for (int k = tid; k < S; k += nthr) {
-            const int ci = (int)(gcode[k] & 0xFFFFFFu);
-            pst[ci] = gr[k];
-            if (HAS2 && second_order(stab, gcode[k])) pst[M + ci] = gs[k];
+            const int t = ptix[gcode[k] & 0xFFFFFFu];
+            pst[t] = gr[k];
+            if (HAS2 && second_order(stab, gcode[k])) pst[M + t] = gs[k];
         }
         __syncthreads();
         for (int p = tid; p < M; p += nthr) {
-            const bool sec = HAS2 && stab[(p % nt) * 9 + SP_KIND] != 0.0f;
+            const bool sec = HAS2 && stab[(pof[p] % nt) * 9 + SP_KIND] != 0.0f;
             pst[2 * M + p] = pair_gate(sec, fin1[p], HAS2 ? fin2[p] : make_float4(0.f, 0.f, 1.f, 1.f), pst[p],
                                        pst[M + p]);
         }
-        load_items_pair(it, v, n0, sbase, r_lo, gw, gcode, stab, tmp, nullptr);  // ends with __syncthreads
+        load_items_pair(it, v, n0, sbase, r_lo, gw, gcode, stab, tmp, ptix);  // ends with __syncthreads
     } else {
         load_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gw, gcode, stab, tmp);  // ends with __syncthreads
     }
@@ -199,13 +211,13 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         for (int i = tid; i < nown; i += nthr)
             iext[i] = input_current(v, inp[i], inp[nown + i], in_pulse, (long long)n0 + r_lo + i, step);
         // iext is read in the N-phase, after the S-phase barrier
-        stage<0, CL, HAS2, PAIR>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
+        stage<0, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
                                  cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
-        stage<1, CL, HAS2, PAIR>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
+        stage<1, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
                                  cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
-        stage<2, CL, HAS2, PAIR>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
+        stage<2, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
                                  cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
-        stage<3, CL, HAS2, PAIR>(v, it, n0, N, nt, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
+        stage<3, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
                                  cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
     }
 
@@ -213,9 +225,9 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     if (PAIR) {
         const long long k0 = v.row_ptr[n0 + r_lo] - sbase, k1 = v.row_ptr[n0 + r_lo + nown] - sbase;
         for (long long k = k0 + tid; k < k1; k += nthr) {
-            const int ci = (int)(gcode[k] & 0xFFFFFFu);
-            gr[k] = pst[ci];
-            if (HAS2 && second_order(stab, gcode[k])) gs[k] = pst[M + ci];
+            const int t = ptix[gcode[k] & 0xFFFFFFu];
+            gr[k] = pst[t];
+            if (HAS2 && second_order(stab, gcode[k])) gs[k] = pst[M + t];
         }
     } else {
         store_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gcode, stab, SmemCoef{fin1, fin2});

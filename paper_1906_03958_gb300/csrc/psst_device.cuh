@@ -43,6 +43,12 @@ struct NetView {
     long long rec_cap;
     const uint8_t *net_flags;    // [n_nets]: bit 0 = has second-order synapses
     int *err;                    // device error word (first error wins)
+    // the (presynaptic neuron, type) pairs that have synapses, per network in
+    // pair order: compact index t of local pair p at pair_tix[net_off[b] *
+    // n_stypes + p] (-1: no synapse), local pair of t at pair_of[pair_off[b] + t]
+    const int *pair_tix;         // [N * n_stypes] or null
+    const int *pair_of;          // [used pairs of all networks]
+    const int *pair_off;         // [n_nets + 1]
 };
 
 enum : uint8_t { NET_HAS2 = 1, NET_PAIR = 2 };  // NET_PAIR: all gates of each (pre, type) pair equal
@@ -116,7 +122,7 @@ struct NeuronLayout {
     int inp;               // float [2][n_own]: constant current, pulse amplitude
     int vst;               // float [2][n_all]: stage potential, by stage parity
     int tmp;               // int [2][n_own + 1]: scan scratch
-    int pair;              // per-pair variant: float [3][m]: step-start r, s and the stage gate
+    int pair;              // per-pair variant: float [3][m] step-start r, s and stage gate, ushort [m] local pair
     int syn;               // start of the synapse items
 };
 
@@ -145,7 +151,7 @@ __host__ __device__ inline NeuronLayout make_nlayout(int n_own, int n_all, int m
     L.iext = lay_take(o, 4LL * n_own);
     L.inp = lay_take(o, 8LL * n_own);
     L.tmp = lay_take(o, 8LL * (n_own + 1));
-    L.pair = pair ? lay_take(o, 12LL * m) : -1;
+    L.pair = pair ? lay_take(o, 14LL * m) : -1;  // r0, s0, G (float) and the local pair (ushort) per entry
     L.syn = o;
     return L;
 }
