@@ -338,6 +338,8 @@ def main():
         from paper_1906_03958_gb300 import netgen as ng
         al = ng.antennal_lobe()
         with psst.Network(al) as sn:
+            if args.autotune > 0:
+                sn.autotune(args.autotune)    # CTA size and gate-table copies (setup, not timed)
             sn.integrate(2000)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -347,9 +349,11 @@ def main():
             torch.cuda.synchronize()
             sn.status()
             sms = e0.elapsed_time(e1)
+            sn_info = sn.info()
         single = {"workload": "antennal lobe, 120 neurons, one network per launch",
                   "value": al.n_neurons * args.single_steps / (sms / 1e3), "unit": UNIT,
-                  "us_per_rk4_step": sms * 1e3 / args.single_steps}
+                  "us_per_rk4_step": sms * 1e3 / args.single_steps,
+                  "block_threads": sn_info["block_threads"]}
 
     # ---- the large sparse network (one network over the whole GPU)
     sparse = None

@@ -163,10 +163,12 @@ int psst_set_barrier_timeout(psst_net *h, int64_t timeout_ns);
 int psst_set_graph_mode(psst_net *h, int enable);
 
 /* Autotuner: for each size class of a CTA-mode handle, time trial_steps
-   steps with the class's largest CTA size and its halves (from a copy of
-   the state, recording off; the state is restored) and keep the fastest.
-   The summation order does not depend on the CTA size, so results stay
-   bitwise identical.  Synchronises `stream`.  Grid mode: no-op. */
+   steps with twice, once, half and a quarter of the class's default CTA
+   size, each with the planned number of shared-memory copies of the
+   per-pair gate table and with a single copy (from a copy of the state,
+   recording off; the state is restored), and keep the fastest.  Neither
+   choice changes the summation order, so results stay bitwise identical.
+   Synchronises `stream`.  Grid mode: no-op. */
 int psst_autotune(psst_net *h, int64_t trial_steps, void *stream);
 
 /* Synchronise `stream` and return the device error word (0 if none), then

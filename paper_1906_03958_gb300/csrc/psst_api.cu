@@ -368,13 +368,21 @@ void make_shares(const int *n1, const int *n2, const int *tcnt, int nt, int n, i
 }
 
 // Dynamic shared memory of one CTA of a network of N neurons in CTA mode.
-long long cta_share_bytes(int N, int nt, int used_pairs, bool has2, bool pair, const Share &s, int K) {
-    const psst::NeuronLayout L = psst::make_nlayout(s.r1 - s.r0, N, pair ? used_pairs : N * nt, has2, pair);
+long long cta_share_bytes(int N, int nt, int used_pairs, bool has2, bool pair, const Share &s, int K,
+                          int rep = 1) {
+    const psst::NeuronLayout L = psst::make_nlayout(s.r1 - s.r0, N, pair ? used_pairs : N * nt, has2, pair, rep);
     return L.syn + (pair ? psst::items_smem_bytes_pair(s.items1, K, s.r1 - s.r0)
                          : psst::items_smem_bytes(s.items1, s.items2, K, s.r1 - s.r0, has2));
 }
 
-// Smallest cluster size (1, 2, 4) whose CTAs all fit; 0 if none.
+// CTAs of `need` bytes of dynamic shared memory that one SM holds (1..4).
+int ctas_per_sm(const SmemCaps &caps, long long need) {
+    return (int)std::max(1LL, std::min(4LL, (long long)caps.per_sm / (need + caps.per_cta)));
+}
+
+// Smallest cluster size (1, 2, 4) whose CTAs all fit; 0 if none.  Per-pair
+// gates: the gate table gets the most copies (up to 32) that leave the CTAs
+// per SM as they are with one copy.
 int plan_network(const PlanInput &in, int b, const SmemCaps &caps, psst::NetPlan *pl, long long *need) {
     const int n0 = in.net_off[b], N = in.net_off[b + 1] - n0, nt = in.nt;
     const bool has2 = in.flags[b] & psst::NET_HAS2, pair = in.flags[b] & psst::NET_PAIR;
@@ -390,6 +398,19 @@ int plan_network(const PlanInput &in, int b, const SmemCaps &caps, psst::NetPlan
         for (int q = 0; q < cl; ++q) worst = std::max(worst, cta_share_bytes(N, nt, used, has2, pair, sh[q], K));
         if (worst <= caps.max_dyn) {
             std::memset(pl, 0, sizeof *pl);
+            if (pair) {
+                const int base = ctas_per_sm(caps, worst);
+                for (int lrep = 5; lrep > 0; --lrep) {
+                    long long w = 0;
+                    for (int q = 0; q < cl; ++q)
+                        w = std::max(w, cta_share_bytes(N, nt, used, has2, pair, sh[q], K, 1 << lrep));
+                    if (w <= caps.max_dyn && ctas_per_sm(caps, w) >= base) {
+                        pl->lrep = lrep;
+                        worst = w;
+                        break;
+                    }
+                }
+            }
             pl->K = K;
             for (int q = 0; q < cl; ++q) {
                 pl->split[q] = sh[q].r0;
@@ -484,7 +505,7 @@ int setup_grid(psst_net *h, const SmemCaps &caps, cudaError_t *err) {
         for (int c = 0; c < parts; ++c) {
             const int n = sh[c].r1 - sh[c].r0;
             const long long bytes =
-                pair ? psst::make_nlayout(n, n, n * nt, has2, true).syn + 4LL * g.mt +
+                pair ? psst::make_nlayout(n, n, n * nt, has2, true, 0).syn + 4LL * g.mt +
                            psst::items_smem_bytes_pair(sh[c].items1, *K, n)
                      : psst::make_nlayout(n, n, n * nt, has2).syn +
                            psst::items_smem_bytes(sh[c].items1, sh[c].items2, *K, n, has2);
@@ -558,7 +579,7 @@ int setup_cta(psst_net *h, const SmemCaps &caps, cudaError_t *err) {
             return fail(PSST_ERR_UNSUPPORTED, "net %d (%d neurons, %lld synapses) does not fit %d CTAs", b, N,
                         in.net_syn[b], PSST_MAX_CL);
         cl_of[b] = cl;
-        per_sm[b] = (int)std::max(1LL, std::min(4LL, (long long)caps.per_sm / (need[b] + caps.per_cta)));
+        per_sm[b] = ctas_per_sm(caps, need[b]);
         double c = 0;
         for (int i = n0; i < n0 + N; ++i) c += n1[i] + n2[i] + 30.0;
         cost[b] = c;
@@ -576,7 +597,10 @@ int setup_cta(psst_net *h, const SmemCaps &caps, cudaError_t *err) {
             c.cl = cl;
             c.n_nets = (int)list.size();
             long long mx = 0;
-            for (int b : list) mx = std::max(mx, need[b]);
+            for (int b : list) {
+                mx = std::max(mx, need[b]);
+                c.lrep_cap = std::max(c.lrep_cap, plans[b].lrep);
+            }
             c.smem = (int)mx;
             c.block = in.user_block ? in.user_block : ((1024 / k) / 32) * 32;
             ranges.push_back({(int)all_lists.size(), (int)list.size()});
@@ -856,7 +880,7 @@ int launch_chunks(psst_net *h, long long step0, long long n_steps, long long chu
 }
 
 // Kernel nodes take the global step index as an argument: net_kernel's 4th
-// (v, list, plans, step0, nsteps), grid_kernel's 3rd (v, g, step0, nsteps).
+// (v, list, plans, step0, nsteps, lrep_cap), grid_kernel's 3rd (v, g, step0, nsteps).
 int patch_step0(psst_net *h, long long step0) {
     size_t n = 0;
     cudaError_t e = cudaGraphGetNodes(h->graph, nullptr, &n);
@@ -873,12 +897,12 @@ int patch_step0(psst_net *h, long long step0) {
         e = cudaGraphKernelNodeGetParams(nodes[i], &p);
         if (e != cudaSuccess) break;
         const int idx = h->mode == PSST_MODE_GRID ? 2 : 3;
-        const int nargs = h->mode == PSST_MODE_GRID ? 4 : 5;
+        const int nargs = h->mode == PSST_MODE_GRID ? 4 : 6;
         // launches of one chunk share step0; chunks follow in capture order
         const int per_chunk = h->mode == PSST_MODE_GRID ? 1 : (int)h->classes.size();
         chunk_base = (long long)(k / per_chunk) * chunk;
         long long s = step0 + chunk_base;
-        void *args[5];
+        void *args[6];
         for (int q = 0; q < nargs; ++q) args[q] = p.kernelParams[q];
         args[idx] = &s;
         p.kernelParams = args;
@@ -985,15 +1009,19 @@ int psst_autotune(psst_net *h, int64_t trial_steps, void *stream) {
     for (size_t ci = 0; e == cudaSuccess && ci < h->classes.size(); ++ci) {
         psst::ClassLaunch &c = h->classes[ci];
         // the class's CTAs per SM are fixed by its shared memory and its
-        // largest CTA keeps 1024 threads per SM (64 registers each); the
-        // trials try that size and its halves
+        // default CTA keeps 1024 threads per SM (64 registers each); the
+        // trials try twice, once, half and a quarter of that size, each with
+        // the planned copies of the per-pair gate table and with one copy
         const int base = c.block;
         float best = 1e30f;
-        int best_block = base;
-        for (int b = base; b >= 64 && b >= base / 4; b /= 2) {
-            if (b % 32) continue;
+        int best_block = base, best_cap = c.lrep_cap;
+        for (int trial = 0; trial < 8; ++trial) {
+            const int b = trial / 2 == 0 ? 2 * base : base >> (trial / 2 - 1);
+            const int cap = trial % 2 ? 0 : c.lrep_cap;
+            if (b > 1024 || b < 64 || b % 32 || (trial % 2 && c.lrep_cap == 0)) continue;
             psst::ClassLaunch t = c;
             t.block = b;
+            t.lrep_cap = cap;
             const int n = (int)std::min<long long>(trial_steps, 1 << 20);
             e = psst::cta_launch(h->v, t, 0, n, st);  // warm-up
             if (e != cudaSuccess) {
@@ -1010,9 +1038,11 @@ int psst_autotune(psst_net *h, int64_t trial_steps, void *stream) {
             if (e == cudaSuccess && ms < best) {
                 best = ms;
                 best_block = b;
+                best_cap = cap;
             }
         }
         c.block = best_block;
+        c.lrep_cap = best_cap;
     }
     h->v.rec_stride = stride;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->v.state, h->tune_buf, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);

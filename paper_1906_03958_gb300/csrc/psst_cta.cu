@@ -66,52 +66,59 @@ struct SmemCoef {
 
 template <int ST, int CL, bool HAS2, bool PAIR>
 __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0, int N, int nt, int M, int r_lo,
-                                      int nown,
-                                      unsigned rank, int tq, long long step, float dt, float *vst, float *y0,
+                                      int nown, unsigned rank, long long rec_slot, float dt, float *vst, float *y0,
                                       float *acc, float *ys, const float *prm, const float *iext, float2 *cur1,
                                       float2 *acc1, float2 *fin1, float4 *cur2, float4 *acc2, float4 *fin2,
-                                      float *pst, const float *stab) {
+                                      float *pst, float *Gt, int lrep, const float *stab) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const float *vcur = vst + (ST & 1) * N;
     float *vnxt = vst + ((ST + 1) & 1) * N;
+    const float *ysc = ys + (ST & 1) * 3 * nown;
+    float *ysn = ys + ((ST + 1) & 1) * 3 * nown;
     // gate-map entries: every (neuron, type) pair, or the used pairs (PAIR)
-    float *r0p = pst, *s0p = pst + M, *Gt = pst + 2 * M;
-    const unsigned short *pof = (const unsigned short *)(pst + 3 * M);
-    if (PAIR) sphase_pair(it, Gt);
+    float *r0p = pst, *s0p = pst + M;
+    const unsigned short *pof = (const unsigned short *)(pst + 2 * M);
+    if (PAIR) sphase_pair(it, Gt, lrep);
     else sphase<ST, HAS2>(it, SmemCoef{ST == 0 ? fin1 : cur1, ST == 0 ? fin2 : cur2});
     __syncthreads();
-    for (int i = tid; i < nown; i += nthr) {
-        const float V = vcur[r_lo + i];
-        const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
-        const float vn = neuron_update<ST>(i, nown, V, y0, acc, ys, prm, iext[i], isyn, dt);
-        vnxt[r_lo + i] = vn;
-        if (CL > 1) {
+    // independent work units: potential of each owned neuron, its gates, and
+    // the gate map (and per-pair gate) of each entry
+    const int U = 2 * nown + M;
+    for (int u = tid; u < U; u += nthr) {
+        if (u < nown) {
+            const int i = u;
+            const float V = vcur[r_lo + i];
+            const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
+            const float vn = neuron_v<ST>(i, nown, V, ysc, y0, acc, prm, iext[i], isyn, dt);
+            vnxt[r_lo + i] = vn;
+            if (CL > 1) {
 #pragma unroll
-            for (unsigned q = 1; q < CL; ++q) st_peer(vnxt + r_lo + i, (rank + q) % CL, vn);
-        }
-        if (ST == 3 && v.rec_stride > 0 && ((step + 1) % v.rec_stride) == 0) {
-            const long long frame = (step + 1) / v.rec_stride - 1;
-            v.rec[(frame % v.rec_cap) * v.N + n0 + r_lo + i] = vn;
-        }
-    }
-    for (int p = tq; p < M; p += nthr) {
-        float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 &c2 = HAS2 ? cur2[p] : d4;
-        float4 &a2 = HAS2 ? acc2[p] : d4;
-        float4 &f2 = HAS2 ? fin2[p] : d4;
-        const int ci = PAIR ? (int)pof[p] : p;  // (neuron, type) pair of the entry
-        const float *sp = stab + (ci % nt) * 9;
-        coef_update<ST, HAS2>(sp, vcur[ci / nt], dt, cur1[p], acc1[p], fin1[p], c2, a2, f2);
-        if (PAIR) {
-            // the pair's gate for the next stage (same operations as the per-synapse path)
-            const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
-            if (ST < 3) {
-                Gt[p] = pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]);
-            } else {
-                const float r0 = r0p[p], s0 = s0p[p];
-                Gt[p] = pair_gate(sec, fin1[p], f2, r0, s0);
-                r0p[p] = fmaf(fin1[p].y, r0, fin1[p].x);
-                if (sec) s0p[p] = fmaf(f2.z, s0, fmaf(f2.y, r0, f2.x));
+                for (unsigned q = 1; q < CL; ++q) st_peer(vnxt + r_lo + i, (rank + q) % CL, vn);
+            }
+            if (ST == 3 && rec_slot >= 0) v.rec[rec_slot * v.N + n0 + r_lo + i] = vn;
+        } else if (u < 2 * nown) {
+            const int i = u - nown;
+            neuron_gates<ST>(i, nown, vcur[r_lo + i], ysc, ysn, y0, acc, dt);
+        } else {
+            const int p = u - 2 * nown;
+            float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 &c2 = HAS2 ? cur2[p] : d4;
+            float4 &a2 = HAS2 ? acc2[p] : d4;
+            float4 &f2 = HAS2 ? fin2[p] : d4;
+            const int ci = PAIR ? (int)pof[p] : p;  // (neuron, type) pair of the entry
+            const float *sp = stab + (ci % nt) * 9;
+            coef_update<ST, HAS2>(sp, vcur[ci / nt], dt, cur1[p], acc1[p], fin1[p], c2, a2, f2);
+            if (PAIR) {
+                // the pair's gate for the next stage (same operations as the per-synapse path)
+                const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
+                if (ST < 3) {
+                    put_gate(Gt, p, lrep, pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]));
+                } else {
+                    const float r0 = r0p[p], s0 = s0p[p];
+                    put_gate(Gt, p, lrep, pair_gate(sec, fin1[p], f2, r0, s0));
+                    r0p[p] = fmaf(fin1[p].y, r0, fin1[p].x);
+                    if (sec) s0p[p] = fmaf(f2.z, s0, fmaf(f2.y, r0, f2.x));
+                }
             }
         }
     }
@@ -120,7 +127,7 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
 }
 
 template <int CL, bool HAS2, bool PAIR>
-__device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long step0, int nsteps,
+__device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long step0, int nsteps, int lrep_cap,
                         unsigned char *smem, const float *stab) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const unsigned rank = CL > 1 ? cluster_rank() : 0u;
@@ -131,7 +138,8 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     const int *ptix = PAIR ? v.pair_tix + (long long)n0 * nt : nullptr;  // local pair -> entry
     const long long sbase = v.row_ptr[n0];
     const int r_lo = pl.split[rank], nown = pl.split[rank + 1] - r_lo;
-    const NeuronLayout L = make_nlayout(nown, N, M, HAS2, PAIR);
+    const int lrep = PAIR ? min(pl.lrep, lrep_cap) : 0;  // copies of the gate table (at most the plan's)
+    const NeuronLayout L = make_nlayout(nown, N, M, HAS2, PAIR, 1 << lrep);
     float *y0 = (float *)(smem + L.y0), *ys = (float *)(smem + L.ys), *acc = (float *)(smem + L.acc);
     float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext), *inp = (float *)(smem + L.inp);
     float *vst = (float *)(smem + L.vst);
@@ -141,6 +149,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     float4 *fin2 = HAS2 ? (float4 *)(smem + L.fin2) : nullptr;
     int *tmp = (int *)(smem + L.tmp);
     float *pst = PAIR ? (float *)(smem + L.pair) : nullptr;
+    float *Gt = PAIR ? (float *)(smem + L.gt) : nullptr;
     Items it = PAIR ? carve_items_pair(smem + L.syn, nown, pl.K, pl.n1[rank])
                     : carve_items(smem + L.syn, nown, pl.K, pl.n1[rank], pl.n2[rank], HAS2);
 
@@ -157,7 +166,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         for (int x = 0; x < 4; ++x) {
             const float y = gV[(long long)x * v.N + gi];
             y0[x * nown + i] = y;
-            ys[x * nown + i] = y;
+            if (x > 0) ys[(x - 1) * nown + i] = y;  // stage-0 gates, parity 0
         }
         const float *p = v.nparams + (long long)v.neuron_type[n0 + gi] * PSST_NEURON_NPARAM;
         prm[NP_C * nown + i] = 1.0f / p[NP_C];
@@ -167,7 +176,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         inp[nown + i] = v.pulse_amp ? v.pulse_amp[n0 + gi] : 0.0f;
     }
     const long long pon = v.pulse_on[b], poff = v.pulse_off[b];
-    unsigned short *pof = PAIR ? (unsigned short *)(pst + 3 * M) : nullptr;
+    unsigned short *pof = PAIR ? (unsigned short *)(pst + 2 * M) : nullptr;
     if (PAIR)
         for (int k = tid; k < M; k += nthr) pof[k] = (unsigned short)v.pair_of[v.pair_off[b] + k];
     for (int k = tid; k < M; k += nthr) {
@@ -191,8 +200,8 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         __syncthreads();
         for (int p = tid; p < M; p += nthr) {
             const bool sec = HAS2 && stab[(pof[p] % nt) * 9 + SP_KIND] != 0.0f;
-            pst[2 * M + p] = pair_gate(sec, fin1[p], HAS2 ? fin2[p] : make_float4(0.f, 0.f, 1.f, 1.f), pst[p],
-                                       pst[M + p]);
+            put_gate(Gt, p, lrep,
+                     pair_gate(sec, fin1[p], HAS2 ? fin2[p] : make_float4(0.f, 0.f, 1.f, 1.f), pst[p], pst[M + p]));
         }
         load_items_pair(it, v, n0, sbase, r_lo, gw, gcode, stab, tmp, ptix);  // ends with __syncthreads
     } else {
@@ -201,24 +210,27 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     if (CL > 1) cluster_sync();
 
     const float dt = v.dt;
-    // gate-map pairs are taken by the threads after the owned-neuron threads
-    int tq = tid - nown % nthr;
-    if (tq < 0) tq += nthr;
-
+    // record: phase of (step + 1) modulo the stride, advanced once per step
+    int rec_phase = v.rec_stride > 0 ? (int)((step0 + 1) % v.rec_stride) : -1;
     for (int itn = 0; itn < nsteps; ++itn) {
         const long long step = step0 + itn;
         const bool in_pulse = step >= pon && step < poff;
+        long long rec_slot = -1;
+        if (rec_phase >= 0) {
+            if (rec_phase == 0) rec_slot = ((step + 1) / v.rec_stride - 1) % v.rec_cap;
+            rec_phase = rec_phase + 1 == v.rec_stride ? 0 : rec_phase + 1;
+        }
         for (int i = tid; i < nown; i += nthr)
             iext[i] = input_current(v, inp[i], inp[nown + i], in_pulse, (long long)n0 + r_lo + i, step);
         // iext is read in the N-phase, after the S-phase barrier
-        stage<0, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
-        stage<1, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
-        stage<2, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
-        stage<3, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, tq, step, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, stab);
+        stage<0, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab);
+        stage<1, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab);
+        stage<2, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab);
+        stage<3, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab);
     }
 
     // write back: owned synapses with the last step's gate map, owned neurons
@@ -247,7 +259,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
 
 template <int CL>
 __global__ void __launch_bounds__(1024) net_kernel(NetView v, const int *list, const NetPlan *plans,
-                                                   long long step0, int nsteps) {
+                                                   long long step0, int nsteps, int lrep_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float stab[PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM];
     for (int i = threadIdx.x; i < v.n_stypes * PSST_SYN_NPARAM; i += blockDim.x) {
@@ -259,18 +271,18 @@ __global__ void __launch_bounds__(1024) net_kernel(NetView v, const int *list, c
     const int b = list[blockIdx.x / CL];
     const uint8_t f = v.net_flags[b];
     if (f & NET_PAIR) {
-        if (f & NET_HAS2) run_net<CL, true, true>(v, b, plans[b], step0, nsteps, smem, stab);
-        else run_net<CL, false, true>(v, b, plans[b], step0, nsteps, smem, stab);
+        if (f & NET_HAS2) run_net<CL, true, true>(v, b, plans[b], step0, nsteps, lrep_cap, smem, stab);
+        else run_net<CL, false, true>(v, b, plans[b], step0, nsteps, lrep_cap, smem, stab);
     } else {
-        if (f & NET_HAS2) run_net<CL, true, false>(v, b, plans[b], step0, nsteps, smem, stab);
-        else run_net<CL, false, false>(v, b, plans[b], step0, nsteps, smem, stab);
+        if (f & NET_HAS2) run_net<CL, true, false>(v, b, plans[b], step0, nsteps, lrep_cap, smem, stab);
+        else run_net<CL, false, false>(v, b, plans[b], step0, nsteps, lrep_cap, smem, stab);
     }
 }
 
 template <int CL>
 cudaError_t launch_cl(const NetView &v, const ClassLaunch &c, long long step0, int nsteps, cudaStream_t stream) {
     if (CL == 1) {
-        net_kernel<1><<<c.n_nets, c.block, c.smem, stream>>>(v, c.list, c.plans, step0, nsteps);
+        net_kernel<1><<<c.n_nets, c.block, c.smem, stream>>>(v, c.list, c.plans, step0, nsteps, c.lrep_cap);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -285,7 +297,7 @@ cudaError_t launch_cl(const NetView &v, const ClassLaunch &c, long long step0, i
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, net_kernel<CL>, v, c.list, c.plans, step0, nsteps);
+    return cudaLaunchKernelEx(&cfg, net_kernel<CL>, v, c.list, c.plans, step0, nsteps, c.lrep_cap);
 }
 
 // out[b] = 1 when every (presynaptic neuron, type) pair of network b has

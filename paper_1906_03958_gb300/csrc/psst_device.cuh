@@ -107,6 +107,7 @@ struct NetPlan {
     int K;
     int n1[PSST_MAX_CL];
     int n2[PSST_MAX_CL];
+    int lrep;  // per-pair gates: the gate table is held in 2^lrep copies (lane l reads copy l mod 2^lrep)
 };
 
 // Shared-memory layout of one CTA: its own neurons (n_own), the stage
@@ -116,13 +117,14 @@ struct NetPlan {
 struct NeuronLayout {
     int cur2, acc2, fin2;  // float4 [m]: s-maps (second order only)
     int cur1, acc1, fin1;  // float2 [m]: r-maps
-    int y0, ys, acc;       // float [4][n_own]: step-start state, stage m/h/n, RK4 k-sum
+    int y0, ys, acc;       // float [4][n_own] step-start state, [2][3][n_own] stage m/h/n, [4][n_own] RK4 k-sum
     int prm;               // float [9][n_own]: 1/C, gNa, gK, gL, ENa, EK, EL, gKL, EKL
     int iext;              // float [n_own]
     int inp;               // float [2][n_own]: constant current, pulse amplitude
     int vst;               // float [2][n_all]: stage potential, by stage parity
     int tmp;               // int [2][n_own + 1]: scan scratch
-    int pair;              // per-pair variant: float [3][m] step-start r, s and stage gate, ushort [m] local pair
+    int pair;              // per-pair variant: float [2][m] step-start r, s, ushort [m] local pair
+    int gt;                // per-pair variant: float [m][rep] stage gate of each entry, rep copies
     int syn;               // start of the synapse items
 };
 
@@ -132,7 +134,8 @@ __host__ __device__ inline int lay_take(int &o, long long bytes) {
     return at;
 }
 
-__host__ __device__ inline NeuronLayout make_nlayout(int n_own, int n_all, int m, bool has2, bool pair = false) {
+__host__ __device__ inline NeuronLayout make_nlayout(int n_own, int n_all, int m, bool has2, bool pair = false,
+                                                     int rep = 1) {
     NeuronLayout L;
     int o = 0;
     L.cur2 = has2 ? lay_take(o, 16LL * m) : -1;
@@ -145,13 +148,14 @@ __host__ __device__ inline NeuronLayout make_nlayout(int n_own, int n_all, int m
     // (peers write into them through distributed shared memory)
     L.vst = lay_take(o, 8LL * n_all);
     L.y0 = lay_take(o, 16LL * n_own);
-    L.ys = lay_take(o, 16LL * n_own);
+    L.ys = lay_take(o, 24LL * n_own);  // stage m, h, n: [2][3][n] by stage parity
     L.acc = lay_take(o, 16LL * n_own);
     L.prm = lay_take(o, 36LL * n_own);
     L.iext = lay_take(o, 4LL * n_own);
     L.inp = lay_take(o, 8LL * n_own);
     L.tmp = lay_take(o, 8LL * (n_own + 1));
-    L.pair = pair ? lay_take(o, 14LL * m) : -1;  // r0, s0, G (float) and the local pair (ushort) per entry
+    L.pair = pair ? lay_take(o, 10LL * m) : -1;  // r0, s0 (float) and the local pair (ushort) per entry
+    L.gt = pair ? lay_take(o, 4LL * rep * m) : -1;
     L.syn = o;
     return L;
 }

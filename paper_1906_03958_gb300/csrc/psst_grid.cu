@@ -87,13 +87,15 @@ struct GlobalCoef {
 
 template <int ST, bool HAS2, bool PAIR>
 __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, const Items &it, int lo, int N,
-                                           int nt, int M, int tq, long long step, float dt, float *vst, float *y0,
+                                           int nt, int M, long long rec_slot, float dt, float *vst, float *y0,
                                            float *acc, float *ys, const float *prm, const float *iext,
                                            float2 *cur1, float2 *acc1, float4 *cur2, float4 *acc2, float *pst,
                                            float *gtab, const float *stab) {
     const int tid = threadIdx.x, nthr = blockDim.x, Mloc = N * nt;
     const float *vcur = vst + (ST & 1) * N;
     float *vnxt = vst + ((ST + 1) & 1) * N;
+    const float *ysc = ys + (ST & 1) * 3 * N;
+    float *ysn = ys + ((ST + 1) & 1) * 3 * N;
     if (PAIR) {
         // this stage's gate of every used pair, written by the owners before the last barrier
         const float4 *src = (const float4 *)(g.gt + (size_t)(ST & 1) * g.mt);
@@ -102,60 +104,64 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
 #pragma unroll 4
         for (int q = tid; q < n4; q += nthr) dst[q] = __ldcg(src + q);
         __syncthreads();
-        sphase_pair(it, gtab);
+        sphase_pair(it, gtab, 0);
     } else {
         sphase<ST, HAS2>(it, GlobalCoef{g.c1 + (size_t)(ST & 1) * M, HAS2 ? g.c2 + (size_t)(ST & 1) * M : nullptr});
     }
     __syncthreads();
-    for (int i = tid; i < N; i += nthr) {
-        const float V = vcur[i];
-        const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
-        const float vn = neuron_update<ST>(i, N, V, y0, acc, ys, prm, iext[i], isyn, dt);
-        vnxt[i] = vn;
-        if (ST == 3 && v.rec_stride > 0 && ((step + 1) % v.rec_stride) == 0) {
-            const long long frame = (step + 1) / v.rec_stride - 1;
-            v.rec[(frame % v.rec_cap) * v.N + lo + i] = vn;
-        }
-    }
-    if (PAIR) {
-        // gates of the own used pairs for the next stage (same operations as
-        // the per-synapse path), published in the other table
-        float *r0p = pst, *s0p = pst + Mloc;
-        float *gout = g.gt + (size_t)((ST + 1) & 1) * g.mt;
-        for (int p = tq; p < Mloc; p += nthr) {
-            const int t = __ldg(g.tix + (size_t)lo * nt + p);
-            if (t < 0) continue;
-            float2 f1;
-            float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;
-            float4 &c2 = HAS2 ? cur2[p] : d4;
-            float4 &a2 = HAS2 ? acc2[p] : d4;
-            const float *sp = stab + (p % nt) * 9;
-            coef_update<ST, HAS2>(sp, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
-            const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
-            float G;
-            if (ST < 3) {
-                G = pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]);
+    // independent work units: potential and gates of each owned neuron, and
+    // the gate map of each own (neuron, type) pair
+    float *r0p = pst, *s0p = pst + Mloc;
+    float *gout = PAIR ? g.gt + (size_t)((ST + 1) & 1) * g.mt : nullptr;
+    float2 *o1 = g.c1 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt;
+    float4 *o2 = HAS2 ? g.c2 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt : nullptr;
+    const int U = 2 * N + Mloc;
+    for (int u = tid; u < U; u += nthr) {
+        if (u < N) {
+            const int i = u;
+            const float V = vcur[i];
+            const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
+            const float vn = neuron_v<ST>(i, N, V, ysc, y0, acc, prm, iext[i], isyn, dt);
+            vnxt[i] = vn;
+            if (ST == 3 && rec_slot >= 0) v.rec[rec_slot * v.N + lo + i] = vn;
+        } else if (u < 2 * N) {
+            const int i = u - N;
+            neuron_gates<ST>(i, N, vcur[i], ysc, ysn, y0, acc, dt);
+        } else {
+            const int p = u - 2 * N;
+            if (PAIR) {
+                // gate of an own used pair for the next stage (same operations as
+                // the per-synapse path), published in the other table
+                const int t = __ldg(g.tix + (size_t)lo * nt + p);
+                if (t < 0) continue;
+                float2 f1;
+                float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;
+                float4 &c2 = HAS2 ? cur2[p] : d4;
+                float4 &a2 = HAS2 ? acc2[p] : d4;
+                const float *sp = stab + (p % nt) * 9;
+                coef_update<ST, HAS2>(sp, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
+                const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
+                float G;
+                if (ST < 3) {
+                    G = pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]);
+                } else {
+                    const float r0 = r0p[p], s0 = s0p[p];
+                    G = pair_gate(sec, f1, f2, r0, s0);
+                    r0p[p] = fmaf(f1.y, r0, f1.x);
+                    if (sec) s0p[p] = fmaf(f2.z, s0, fmaf(f2.y, r0, f2.x));
+                }
+                gout[t] = G;
             } else {
-                const float r0 = r0p[p], s0 = s0p[p];
-                G = pair_gate(sec, f1, f2, r0, s0);
-                r0p[p] = fmaf(f1.y, r0, f1.x);
-                if (sec) s0p[p] = fmaf(f2.z, s0, fmaf(f2.y, r0, f2.x));
+                // gate map of an own pair: local copy for the next stage, and the
+                // table every CTA reads at the next stage
+                float2 f1;
+                float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;
+                float4 &c2 = HAS2 ? cur2[p] : d4;
+                float4 &a2 = HAS2 ? acc2[p] : d4;
+                coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
+                o1[p] = ST == 3 ? f1 : cur1[p];
+                if (HAS2) o2[p] = ST == 3 ? f2 : cur2[p];
             }
-            gout[t] = G;
-        }
-    } else {
-        // gate maps of the own pairs: local copy for the next stage, and the
-        // table every CTA reads at the next stage
-        float2 *o1 = g.c1 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt;
-        float4 *o2 = HAS2 ? g.c2 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt : nullptr;
-        for (int p = tq; p < Mloc; p += nthr) {
-            float2 f1;
-            float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;
-            float4 &c2 = HAS2 ? cur2[p] : d4;
-            float4 &a2 = HAS2 ? acc2[p] : d4;
-            coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
-            o1[p] = ST == 3 ? f1 : cur1[p];
-            if (HAS2) o2[p] = ST == 3 ? f2 : cur2[p];
         }
     }
     return grid_barrier(g.bar, g.timeout_ns, v.err);
@@ -168,7 +174,7 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
     const int lo = g.row_split[blockIdx.x], N = g.row_split[blockIdx.x + 1] - lo;
     const int nt = v.n_stypes, Mloc = N * nt;
     const int M = (int)(v.N * nt);
-    const NeuronLayout L = make_nlayout(N, N, Mloc, HAS2, PAIR);
+    const NeuronLayout L = make_nlayout(N, N, Mloc, HAS2, PAIR, 0);  // the gate table sits after the layout
     float *y0 = (float *)(smem + L.y0), *ys = (float *)(smem + L.ys), *acc = (float *)(smem + L.acc);
     float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext), *inp = (float *)(smem + L.inp);
     float *vst = (float *)(smem + L.vst);
@@ -193,7 +199,7 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         for (int x = 0; x < 4; ++x) {
             const float y = gV[(long long)x * v.N + i];
             y0[x * N + i] = y;
-            ys[x * N + i] = y;
+            if (x > 0) ys[(x - 1) * N + i] = y;  // stage-0 gates, parity 0
         }
         const float *p = v.nparams + (long long)v.neuron_type[lo + i] * PSST_NEURON_NPARAM;
         prm[NP_C * N + i] = 1.0f / p[NP_C];
@@ -238,23 +244,28 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
     bool ok = grid_barrier(g.bar, g.timeout_ns, v.err);
 
     const float dt = v.dt;
-    int tq = tid - N % nthr;
-    if (tq < 0) tq += nthr;
+    // record: phase of (step + 1) modulo the stride, advanced once per step
+    int rec_phase = v.rec_stride > 0 ? (int)((step0 + 1) % v.rec_stride) : -1;
     for (int itn = 0; ok && itn < nsteps; ++itn) {
         const long long step = step0 + itn;
         const bool in_pulse = step >= pon && step < poff;
+        long long rec_slot = -1;
+        if (rec_phase >= 0) {
+            if (rec_phase == 0) rec_slot = ((step + 1) / v.rec_stride - 1) % v.rec_cap;
+            rec_phase = rec_phase + 1 == v.rec_stride ? 0 : rec_phase + 1;
+        }
         for (int i = tid; i < N; i += nthr)
             iext[i] = input_current(v, inp[i], inp[N + i], in_pulse, (long long)lo + i, step);
-        ok = grid_stage<0, HAS2, PAIR>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+        ok = grid_stage<0, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
                                        acc1, cur2, acc2, pst, gtab, stab);
         if (ok)
-            ok = grid_stage<1, HAS2, PAIR>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+            ok = grid_stage<1, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
                                            acc1, cur2, acc2, pst, gtab, stab);
         if (ok)
-            ok = grid_stage<2, HAS2, PAIR>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+            ok = grid_stage<2, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
                                            acc1, cur2, acc2, pst, gtab, stab);
         if (ok)
-            ok = grid_stage<3, HAS2, PAIR>(v, g, it, lo, N, nt, M, tq, step, dt, vst, y0, acc, ys, prm, iext, cur1,
+            ok = grid_stage<3, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
                                            acc1, cur2, acc2, pst, gtab, stab);
     }
     if (!ok) return;  // error recorded; global state keeps its value from before the call

@@ -14,6 +14,7 @@ struct ClassLaunch {
     int block, smem;      // CTA size, dynamic shared memory
     const int *list;      // [n_nets] device: network indices, largest first
     const NetPlan *plans; // [all nets] device
+    int lrep_cap;         // per-pair gates: at most 2^lrep_cap copies of the gate table (autotuned)
 };
 
 // CTA/cluster batched kernel (psst_cta.cu).

@@ -368,16 +368,22 @@ __device__ inline void load_items_pair(Items &it, const NetView &v, long long ro
     __syncthreads();
 }
 
-// S-phase of the per-pair variant: every item's A = sum w G with G = Gt[id].
-__device__ __forceinline__ void sphase_pair(const Items &it, const float *Gt) {
+// S-phase of the per-pair variant: every item's A = sum w G with G the gate
+// of entry id.  The gate table holds 2^lrep copies of each entry side by
+// side (entry e, copy c at e * 2^lrep + c) and lane l reads copy
+// l mod 2^lrep: with 32 copies the 32 lanes of a gather hit 32 different
+// banks whatever the entries.
+__device__ __forceinline__ void sphase_pair(const Items &it, const float *Gt, int lrep) {
     const int tid = threadIdx.x, nthr = blockDim.x, K = it.K, n = it.n1;
+    const float *Gl = Gt + (threadIdx.x & ((1 << lrep) - 1));
     for (int t = tid; t < n; t += nthr) {
         float A = 0.0f;
-        for (int j = 0; j < K; ++j) {
+#pragma unroll 4
+        for (int j = 0; j < K; ++j) {  // unrolled: several chunks' loads in flight, sums in order
             const int c = j * n + t;
             const float4 w = it.w[c];
             const ushort4 id = it.id[c];
-            const float g0 = Gt[id.x], g1 = Gt[id.y], g2 = Gt[id.z], g3 = Gt[id.w];
+            const float g0 = Gl[id.x << lrep], g1 = Gl[id.y << lrep], g2 = Gl[id.z << lrep], g3 = Gl[id.w << lrep];
             A = fmaf(w.x, g0, A);
             A = fmaf(w.y, g1, A);
             A = fmaf(w.z, g2, A);
@@ -390,12 +396,41 @@ __device__ __forceinline__ void sphase_pair(const Items &it, const float *Gt) {
 // Synaptic current of owned row i from its typed items (fixed order).
 __device__ __forceinline__ float row_current_pair(const Items &it, int i, float V) {
     float A = 0.0f, B = 0.0f;
-    for (int t = it.ib1[i]; t < it.ib1[i + 1]; ++t) {
+    int t = it.ib1[i];
+    const int t1 = it.ib1[i + 1];
+    for (; t + 4 <= t1; t += 4) {  // loads issued together, sums in item order
+        const float a0 = it.pa[t], a1 = it.pa[t + 1], a2 = it.pa[t + 2], a3 = it.pa[t + 3];
+        const float e0 = it.pb[t], e1 = it.pb[t + 1], e2 = it.pb[t + 2], e3 = it.pb[t + 3];
+        A += a0;
+        B = fmaf(e0, a0, B);
+        A += a1;
+        B = fmaf(e1, a1, B);
+        A += a2;
+        B = fmaf(e2, a2, B);
+        A += a3;
+        B = fmaf(e3, a3, B);
+    }
+    for (; t < t1; ++t) {
         const float a = it.pa[t];
         A += a;
         B = fmaf(it.pb[t], a, B);
     }
     return fmaf(V, A, -B);
+}
+
+// Store the gate of entry e in all 2^lrep copies (16-byte stores from 4
+// copies on, the lane's first store rotated so that a warp's stores spread
+// over the banks).
+__device__ __forceinline__ void put_gate(float *Gt, int e, int lrep, float G) {
+    const int R = 1 << lrep, l = (int)threadIdx.x;
+    float *row = Gt + ((long long)e << lrep);
+    if (R >= 4) {
+        const float4 g4 = make_float4(G, G, G, G);
+        const int n4 = R >> 2;
+        for (int c = 0; c < n4; ++c) ((float4 *)row)[(c + l) & (n4 - 1)] = g4;
+    } else {
+        for (int c = 0; c < R; ++c) row[c] = G;
+    }
 }
 
 // Gate value G of a pair from its stage maps and step-start gates, with
@@ -456,32 +491,52 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, float dt, 
     }
 }
 
-// Right-hand side and stage update of owned neuron i at stage ST.
-// y0/acc/ys hold [4][n] (ys rows 1..3 = stage m, h, n); V is the stage
-// potential; returns the potential of the next stage (ST < 3) or of the new
-// step start.
+// Right-hand side and stage update of owned neuron i at stage ST, in two
+// independent halves run by different threads: the potential (synaptic and
+// ionic currents) and the gates m, h, n (rate functions).  y0/acc hold
+// [4][n] (V, m, h, n); the stage gates are double-buffered by stage parity,
+// ysc = [3][n] of this stage (read by both halves), ysn = [3][n] of the next.
+
+// Potential: returns the next stage's V (ST < 3) or the new step-start V.
 template <int ST>
-__device__ __forceinline__ float neuron_update(int i, int n, float V, float *y0, float *acc, float *ys,
-                                               const float *prm, float iext, float isyn, float dt) {
+__device__ __forceinline__ float neuron_v(int i, int n, float V, const float *ysc, float *y0, float *acc,
+                                          const float *prm, float iext, float isyn, float dt) {
     constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
     const float cnext = (ST == 2) ? dt : 0.5f * dt;
     const float dt6 = dt * (1.0f / 6.0f);
-    const float m = ys[n + i], h = ys[2 * n + i], nn = ys[3 * n + i];
-    const Rates q = hh_rates(V);
+    const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
     const float m3h = m * m * m * h, n2 = nn * nn, n4 = n2 * n2;
     const float iion = prm[NP_GNA * n + i] * m3h * (V - prm[NP_ENA * n + i]) +
                        prm[NP_GK * n + i] * n4 * (V - prm[NP_EK * n + i]) +
                        prm[NP_GL * n + i] * (V - prm[NP_EL * n + i]) +
                        prm[NP_GKL * n + i] * (V - prm[NP_EKL * n + i]);
-    float d[4];
-    d[0] = (iext - iion - isyn) * prm[NP_C * n + i];  // prm row 0 holds 1/C
-    d[1] = q.am * (1.0f - m) - q.bm * m;
-    d[2] = q.ah * (1.0f - h) - q.bh * h;
-    d[3] = q.an * (1.0f - nn) - q.bn * nn;
-    float vnext = 0.0f;
+    const float d = (iext - iion - isyn) * prm[NP_C * n + i];  // prm row 0 holds 1/C
+    const float ac = (ST == 0) ? d : fmaf(WGT, d, acc[i]);
+    if (ST < 3) {
+        acc[i] = ac;
+        return fmaf(cnext, d, y0[i]);
+    }
+    const float yn = fmaf(dt6, ac, y0[i]);
+    y0[i] = yn;
+    return yn;
+}
+
+// Gates: writes the next stage's (ST < 3) or the new step-start m, h, n.
+template <int ST>
+__device__ __forceinline__ void neuron_gates(int i, int n, float V, const float *ysc, float *ysn, float *y0,
+                                             float *acc, float dt) {
+    constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
+    const float cnext = (ST == 2) ? dt : 0.5f * dt;
+    const float dt6 = dt * (1.0f / 6.0f);
+    const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
+    const Rates q = hh_rates(V);
+    float d[3];
+    d[0] = q.am * (1.0f - m) - q.bm * m;
+    d[1] = q.ah * (1.0f - h) - q.bh * h;
+    d[2] = q.an * (1.0f - nn) - q.bn * nn;
 #pragma unroll
-    for (int x = 0; x < 4; ++x) {
-        const int ix = x * n + i;
+    for (int x = 0; x < 3; ++x) {
+        const int ix = (x + 1) * n + i;
         const float ac = (ST == 0) ? d[x] : fmaf(WGT, d[x], acc[ix]);
         float yn;
         if (ST < 3) {
@@ -491,10 +546,8 @@ __device__ __forceinline__ float neuron_update(int i, int n, float V, float *y0,
             yn = fmaf(dt6, ac, y0[ix]);
             y0[ix] = yn;
         }
-        if (x == 0) vnext = yn;
-        else ys[ix] = yn;
+        ysn[x * n + i] = yn;
     }
-    return vnext;
 }
 
 }  // namespace psst
