@@ -32,9 +32,11 @@
 //   us_p = -C_p G'(s_p) - K4 kbs_p               [second order]
 //   with the column sum C_p = sum_{k in p} w_k (q_i V_i - q_i E_k);
 //   dL/dw_k += -q_i G_p (V_i - E_k);  dL/dgNa += -q_i m^3 h (V - ENa), ...
-// The column sums use shared-memory atomics (their order is not fixed).  The
-// weight gradients are summed over each step's four stages in one pass, into
-// an FP32 partial per segment, then into an FP64 total.
+// The column sums go through per-warp partial rows summed in warp order when
+// no row holds two synapses of one pair (fixed order, reproducible), else
+// through shared-memory atomics (order not fixed).  The weight gradients are
+// summed over each step's four stages in one pass, into an FP32 partial per
+// segment, then into an FP64 total.
 #include <cuda_runtime.h>
 
 #include "psst_device.cuh"
@@ -79,6 +81,7 @@ struct AdjSmem {
     float *Ep;                 // [M] reversal potential of each pair's type
     float *prm;                // [9][N] (row 0: 1/C)
     float *iext, *inp;         // [N], [2][N]
+    float *cpart;              // [ADJ_THREADS / 32][M] per-warp column-sum rows, or null (atomics)
 };
 
 __host__ __device__ inline long long adj_smem_bytes(int N, int M, int n_items, int K) {
@@ -230,6 +233,45 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
 
 // ---------------------------------------------------------------- reverse
 
+// Column sums C_p = sum_k w_k (q_i V_i - q_i E_k) of stage st into S.csum.
+// A warp walks one row's synapses at a time (their pairs are distinct, so
+// the lanes never meet on an address): into its own partial row when S.cpart
+// is set, then the rows are added in warp order; else with atomics.
+__device__ __forceinline__ void column_sums(const AdjNet &a, const AdjSmem &S, int st) {
+    const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, M = a.M, K = a.K, ni = a.n_items;
+    const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
+    const float *Wf = (const float *)S.w;
+    const unsigned short *Id = (const unsigned short *)S.id;
+    float *mine = S.cpart ? S.cpart + (long long)wid * M : nullptr;
+    for (int i = wid; i < N; i += nwarps) {
+        const float2 abv = S.ab[st * N + i];
+        const int t0 = S.ib[i], nslot = (S.ib[i + 1] - t0) * K * 4;
+        for (int m = lane; m < nslot; m += 32) {
+            const int cq = m >> 2, q = cq / K, j = cq - q * K;
+            const int slot = ((j * ni + t0 + q) << 2) + (m & 3);
+            const float w = Wf[slot];
+            if (w != 0.0f) {
+                const int pp = Id[slot];
+                const float x = w * fmaf(-S.Ep[pp], abv.y, abv.x);
+                if (mine) mine[pp] += x;
+                else atomicAdd(&S.csum[pp], x);
+            }
+        }
+        __syncwarp();  // the next row may touch the same pairs from other lanes
+    }
+    if (S.cpart) {
+        __syncthreads();
+        for (int q = tid; q < M; q += nthr) {
+            float c = 0.0f;
+            for (int w = 0; w < nwarps; ++w) {
+                c += S.cpart[(long long)w * M + q];
+                S.cpart[(long long)w * M + q] = 0.0f;
+            }
+            S.csum[q] = c;
+        }
+    }
+}
+
 // Reverse of the step whose stages fwd_step<true> just stored: lam holds the
 // adjoint of y_{n+1} on entry and of y_n on exit (before the frame term).
 __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, float dt, float4 *gpart) {
@@ -280,20 +322,8 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, f
             g[NP_EKL] += (double)(q * gKL);
         }
         __syncthreads();
-        // B) items: column sums C_p = sum_k w_k (q_i V_i - q_i E_k)
-        for (int it = tid; it < ni; it += nthr) {
-            const float2 abv = S.ab[st * N + S.irow[it]];
-            for (int j = 0; j < K; ++j) {
-                const int c = j * ni + it;
-                const float4 w = S.w[c];
-                const ushort4 id = S.id[c];
-                const float wv[4] = {w.x, w.y, w.z, w.w};
-                const int iv[4] = {id.x, id.y, id.z, id.w};
-#pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4)
-                    if (wv[q4] != 0.0f) atomicAdd(&S.csum[iv[q4]], wv[q4] * fmaf(-S.Ep[iv[q4]], abv.y, abv.x));
-            }
-        }
+        // B) column sums of the synaptic current's Jacobian
+        column_sums(a, S, st);
         __syncthreads();
         // C) owners: gate-pair products and the presynaptic voltage term
         for (int i = tid; i < N; i += nthr) {
@@ -462,6 +492,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     S.prm = (float *)take(p, 36LL * N);
     S.iext = (float *)take(p, 4LL * N);
     S.inp = (float *)take(p, 8LL * N);
+    S.cpart = av.col_warp[a.b] ? (float *)take(p, 4LL * (ADJ_THREADS / 32) * M) : nullptr;
 
     const long long *rp = v.row_ptr + a.n0;
     const uint32_t *gcode = v.syn_code + a.sbase;
@@ -481,6 +512,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         S.Ep[q] = stab[(q % nt) * 9 + SP_E];
         S.csum[q] = 0.0f;
     }
+    if (S.cpart)
+        for (int q = tid; q < (ADJ_THREADS / 32) * M; q += nthr) S.cpart[q] = 0.0f;
     for (int q = tid; q < a.R; q += nthr) {
         S.lam[q] = 0.0f;
         S.ysum[q] = 0.0f;
@@ -622,7 +655,9 @@ __global__ void adj_reduce_types(const int *neuron_type, long long N, const doub
 
 }  // namespace
 
-long long adj_smem_need(int N, int nt, int n_items, int K) { return adj_smem_bytes(N, N * nt, n_items, K); }
+long long adj_smem_need(int N, int nt, int n_items, int K, bool col_warp) {
+    return adj_smem_bytes(N, N * nt, n_items, K) + (col_warp ? 4LL * (ADJ_THREADS / 32) * N * nt + 16 : 0);
+}
 
 cudaError_t adj_launch(const NetView &v, const AdjView &av, long long step0, int nsteps, int smem, int n_types,
                        float *grad_np, cudaStream_t stream) {

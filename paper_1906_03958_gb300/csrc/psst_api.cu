@@ -64,6 +64,7 @@ struct PlanInput {
     std::vector<int> net_off, n1, n2;
     std::vector<int> tcnt;       // [N][nt] synapses of each type per row
     std::vector<int> pair_off;   // [n_nets + 1] used (presynaptic neuron, type) pairs of the networks
+    std::vector<uint8_t> rows_unique;  // [n_nets] no row holds two synapses of one pair
     std::vector<long long> net_syn;
     std::vector<uint8_t> flags;  // NET_HAS2 | NET_PAIR per network
 };
@@ -89,6 +90,7 @@ struct psst_net {
     int adj_smem = 0;
     int *d_adjK = nullptr, *d_adjI = nullptr;
     long long *d_ckoff = nullptr, *d_segoff = nullptr, *d_slotoff = nullptr;
+    uint8_t *d_colwarp = nullptr;  // [n_nets] adjoint column sums through per-warp rows
     float *adj_ckpt = nullptr, *adj_seg = nullptr, *adj_gy0 = nullptr;
     float4 *adj_gpart = nullptr;
     double *adj_gtot = nullptr;
@@ -702,6 +704,19 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
             }
     }
     pair_off[n_nets] = (int)pof.size();
+    pin.rows_unique.assign((size_t)n_nets, 1);
+    {
+        std::vector<long long> last_row((size_t)N * nt, -1);  // last row that used each pair
+        for (int b = 0; b < n_nets; ++b) {
+            const long long base = (long long)d->net_neuron_off[b] * nt;
+            for (long long i = d->net_neuron_off[b]; i < d->net_neuron_off[b + 1]; ++i)
+                for (long long k = d->row_ptr[i]; k < d->row_ptr[i + 1]; ++k) {
+                    const size_t p = (size_t)(base + (long long)d->pre[k] * nt + d->syn_type[k]);
+                    if (last_row[p] == i) pin.rows_unique[b] = 0;
+                    last_row[p] = i;
+                }
+        }
+    }
     bool all_fit = true;
     for (int b = 0; b < n_nets && all_fit; ++b) {
         psst::NetPlan pl;
@@ -1254,6 +1269,7 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         h->adj_K.resize(n_nets);
         h->adj_items.resize(n_nets);
         std::vector<long long> slot_off((size_t)n_nets), seg_rows((size_t)n_nets);
+        std::vector<uint8_t> col_warp((size_t)n_nets, 0);
         long long slots = 0;
         int need = 0;
         for (int b = 0; b < n_nets; ++b) {
@@ -1264,10 +1280,14 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
             for (int i = n0; i < n0 + N; ++i) items += (int)((rp[i + 1] - rp[i] + 4 * K - 1) / (4 * K));
             if (N >= 65536 || (long long)N * nt >= 65536)
                 return fail(PSST_ERR_UNSUPPORTED, "adjoint: net %d too large (%d neurons)", b, N);
-            const long long bytes = psst::adj_smem_need(N, nt, items, K);
+            long long bytes = psst::adj_smem_need(N, nt, items, K, false);
             if (bytes > h->max_dyn)
                 return fail(PSST_ERR_UNSUPPORTED, "adjoint: net %d needs %lld B of shared memory (max %d)", b, bytes,
                             h->max_dyn);
+            // per-warp column-sum rows when no row repeats a pair and they fit
+            const long long bytes_cw = psst::adj_smem_need(N, nt, items, K, true);
+            col_warp[b] = h->pin.rows_unique[b] && bytes_cw <= h->max_dyn;
+            if (col_warp[b]) bytes = bytes_cw;
             need = std::max<int>(need, (int)bytes);
             h->adj_K[b] = K;
             h->adj_items[b] = items;
@@ -1278,6 +1298,7 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         e = upload(h, &h->d_adjK, h->adj_K.data(), h->adj_K.size());
         if (e == cudaSuccess) e = upload(h, &h->d_adjI, h->adj_items.data(), h->adj_items.size());
         if (e == cudaSuccess) e = upload(h, &h->d_slotoff, slot_off.data(), slot_off.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_colwarp, col_warp.data(), col_warp.size());
         if (e == cudaSuccess) e = h->alloc(&h->adj_gpart, (size_t)slots / 4);
         if (e == cudaSuccess) e = h->alloc(&h->adj_gtot, (size_t)slots);
         if (e == cudaSuccess) e = h->alloc(&h->adj_gpn, (size_t)h->v.N * 9);
@@ -1332,6 +1353,7 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
     av.grad_w = grad_w;
     av.gp_neuron = h->adj_gpn;
     av.grad_y0 = grad_state0 ? grad_state0 : h->adj_gy0;
+    av.col_warp = h->d_colwarp;
     e = psst::adj_launch(h->v, av, s0, (int)n_steps, h->adj_smem, h->n_ntypes, grad_neuron_params,
                          (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint launch");

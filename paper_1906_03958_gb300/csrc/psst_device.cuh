@@ -95,6 +95,7 @@ struct AdjView {
     float *grad_w;              // [S] output, CSR order
     double *gp_neuron;          // [N][9] per-neuron parameter gradients
     float *grad_y0;             // [4][N] output: adjoint of V, m, h, n at the start
+    const uint8_t *col_warp;    // [n_nets] 1: column sums through per-warp partial rows (no atomics)
 };
 
 #define PSST_MAX_CL 4

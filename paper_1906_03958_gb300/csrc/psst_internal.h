@@ -29,7 +29,7 @@ cudaError_t grid_launch(const NetView &v, const GridView &g, long long step0, in
                         int smem, cudaStream_t stream);
 
 // Discrete adjoint (psst_adjoint.cu).
-long long adj_smem_need(int N, int nt, int n_items, int K);
+long long adj_smem_need(int N, int nt, int n_items, int K, bool col_warp);
 cudaError_t adj_launch(const NetView &v, const AdjView &av, long long step0, int nsteps, int smem, int n_types,
                        float *grad_np, cudaStream_t stream);
 
