@@ -48,6 +48,19 @@ namespace {
 
 constexpr int ADJ_THREADS = 1024;
 
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Barrier of the cluster's CTAs; release/acquire orders their global memory
+// accesses across it.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ float ratio_u_deriv(float u) {
     // d/du of u / (1 - e^{-u}); Bernoulli series near 0
     if (fabsf(u) < 0.1f) {
@@ -240,14 +253,16 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
 __device__ __forceinline__ void column_sums(const AdjNet &a, const AdjSmem &S, int st) {
     const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, M = a.M, K = a.K, ni = a.n_items;
     const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
+    const int lk = __ffs(K) - 1;  // K is a power of two
     const float *Wf = (const float *)S.w;
     const unsigned short *Id = (const unsigned short *)S.id;
     float *mine = S.cpart ? S.cpart + (long long)wid * M : nullptr;
     for (int i = wid; i < N; i += nwarps) {
         const float2 abv = S.ab[st * N + i];
         const int t0 = S.ib[i], nslot = (S.ib[i + 1] - t0) * K * 4;
+#pragma unroll 2
         for (int m = lane; m < nslot; m += 32) {
-            const int cq = m >> 2, q = cq / K, j = cq - q * K;
+            const int cq = m >> 2, q = cq >> lk, j = cq & (K - 1);
             const int slot = ((j * ni + t0 + q) << 2) + (m & 3);
             const float w = Wf[slot];
             if (w != 0.0f) {
@@ -449,7 +464,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     __syncthreads();
     const int tid = threadIdx.x, nthr = blockDim.x;
     AdjNet a;
-    a.b = blockIdx.x;
+    a.b = blockIdx.x / 2;  // one 2-CTA cluster per network
     a.n0 = v.net_off[a.b];
     a.N = v.net_off[a.b + 1] - a.n0;
     a.nt = v.n_stypes;
@@ -538,6 +553,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     }
     for (int i = tid; i < N; i += nthr)
         for (int it = S.ib[i]; it < S.ib[i + 1]; ++it) S.irow[it] = (unsigned short)i;
+    for (int it = S.ib[N] + tid; it < ni; it += nthr) S.irow[it] = 0;  // inert padding items (w = 0)
     __syncthreads();
     float *W = (float *)S.w;
     unsigned short *ID = (unsigned short *)S.id;
@@ -563,16 +579,22 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     // the four stages' arrays form one contiguous block (sV .. sfv)
     const int stage_floats = 4 * (6 * N + 3 * M);
     float4 *stage_blk = (float4 *)S.sV;
-    // pass 1: checkpoints every ckpt steps
-    float *ck = av.ckpt + av.ck_off[a.b];
-    float *seg = av.seg + av.seg_off[a.b];
-    float4 *gpart = av.gpart + av.slot_off[a.b] / 4;
-    double *gtot = av.gtot + av.slot_off[a.b];
-    for (long long c = tid; c < slots; c += nthr) gpart[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (long long c = tid; c < slots * 4; c += nthr) gtot[c] = 0.0;
     const int ckpt = av.ckpt_every;
     const float dt = v.dt;
-    if (!av.ck_full) {
+    // the two CTAs of the network's cluster: rank 0 recomputes segments
+    // forward, rank 1 sweeps them backward and owns the gradients
+    const bool fwd_cta = cluster_rank() == 0;
+    float *ck = av.ckpt + av.ck_off[a.b];
+    float *seg0 = av.seg + av.seg_off[a.b];
+    const long long seg_buf = (long long)min(ckpt, nsteps) * stage_floats;  // floats of one segment buffer
+    float4 *gpart = av.gpart + av.slot_off[a.b] / 4;
+    double *gtot = av.gtot + av.slot_off[a.b];
+    if (!fwd_cta) {
+        for (long long c = tid; c < slots; c += nthr) gpart[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (long long c = tid; c < slots * 4; c += nthr) gtot[c] = 0.0;
+    }
+    // pass 1 (rank 0): checkpoints every ckpt steps, unless recorded by the forward
+    if (fwd_cta && !av.ck_full) {
         for (int n = 0; n < nsteps; ++n) {
             if (n % ckpt == 0)
                 for (int q = tid; q < a.R; q += nthr) ck[(long long)(n / ckpt) * a.R + q] = S.y[q];
@@ -583,14 +605,14 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     const int stride = v.rec_stride;
     int frame = av.n_frames - 1;
     const float *dl = av.dLdV;
-    if (stride > 0 && (step0 + nsteps) % stride == 0 && frame >= 0) {
+    if (!fwd_cta && stride > 0 && (step0 + nsteps) % stride == 0 && frame >= 0) {
         for (int i = tid; i < N; i += nthr) S.lam[i] += dl[(long long)frame * v.N + a.n0 + i];
         --frame;
     }
     __syncthreads();
-    // pass 2: segments backward
-    const int nseg = (nsteps + ckpt - 1) / ckpt;
-    for (int c = nseg - 1; c >= 0; --c) {
+    // segment c recomputed forward from its checkpoint into buffer c mod 2,
+    // every step's four stages kept
+    auto recompute = [&](int c) {
         const int k0 = c * ckpt, k1 = min(k0 + ckpt, nsteps);
         if (av.ck_full) {
             load_reduced(v, a, S, av.ck_full + (long long)c * av.dim, rp, gcode, nullptr);
@@ -598,13 +620,18 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
             for (int q = tid; q < a.R; q += nthr) S.y[q] = ck[(long long)c * a.R + q];
             __syncthreads();
         }
-        // recompute the segment, keeping every step's four stages in global memory
+        float *seg = seg0 + (long long)(c & 1) * seg_buf;
         for (int n = k0; n < k1; ++n) {
             fwd_step<true>(v, a, S, stab, step0 + n, dt);
             float4 *dst = (float4 *)(seg + (long long)(n - k0) * stage_floats);
             for (int q = tid; q < stage_floats / 4; q += nthr) dst[q] = stage_blk[q];
             __syncthreads();
         }
+    };
+    // segment c swept backward from buffer c mod 2
+    auto sweep = [&](int c) {
+        const int k0 = c * ckpt, k1 = min(k0 + ckpt, nsteps);
+        const float *seg = seg0 + (long long)(c & 1) * seg_buf;
         for (int n = k1 - 1; n >= k0; --n) {
             const float4 *src = (const float4 *)(seg + (long long)(n - k0) * stage_floats);
             for (int q = tid; q < stage_floats / 4; q += nthr) stage_blk[q] = src[q];
@@ -626,8 +653,22 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
             gpart[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
         __syncthreads();
+    };
+    // pass 2: segments backward, rank 0 one segment ahead of rank 1; the
+    // cluster barrier (release/acquire) hands each buffer over
+    const int nseg = (nsteps + ckpt - 1) / ckpt;
+    if (fwd_cta) recompute(nseg - 1);
+    cluster_sync();
+    for (int c = nseg - 1; c >= 0; --c) {
+        if (fwd_cta) {
+            if (c > 0) recompute(c - 1);
+        } else {
+            sweep(c);
+        }
+        cluster_sync();
     }
-    // outputs: weight gradients in CSR order, neuron parameter partials
+    if (fwd_cta) return;
+    // outputs (rank 1): weight gradients in CSR order, neuron parameter partials
     for (int i = tid; i < N; i += nthr) {
         const long long k0 = rp[i] - a.sbase;
         for (long long k = k0; k < rp[i + 1] - a.sbase; ++k) {
@@ -663,8 +704,20 @@ cudaError_t adj_launch(const NetView &v, const AdjView &av, long long step0, int
                        float *grad_np, cudaStream_t stream) {
     cudaError_t e = cudaFuncSetAttribute(adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    adj_kernel<<<v.n_nets, ADJ_THREADS, smem, stream>>>(v, av, step0, nsteps);
-    e = cudaGetLastError();
+    // one cluster of two CTAs per network: forward recompute and reverse sweep
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * v.n_nets);
+    cfg.blockDim = dim3(ADJ_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, adj_kernel, v, av, step0, nsteps);
     if (e != cudaSuccess) return e;
     adj_reduce_types<<<n_types, 32, 0, stream>>>(v.neuron_type, v.N, av.gp_neuron, n_types, grad_np);
     return cudaGetLastError();

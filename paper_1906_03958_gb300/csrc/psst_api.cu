@@ -1275,9 +1275,16 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         for (int b = 0; b < n_nets; ++b) {
             const int n0 = off[b], N = off[b + 1] - n0;
             const long long S = rp[n0 + N] - rp[n0];
-            const int K = (int)std::max(1LL, std::min(8LL, (S / 4 + 1023) / 1024));
+            // chunks per item: a power of two (1..8), about 1024 items per network
+            const int K0 = (int)std::max(1LL, std::min(8LL, (S / 4 + 1023) / 1024));
+            const int K = K0 >= 8 ? 8 : K0 >= 4 ? 4 : K0 >= 2 ? 2 : 1;
             int items = 0;
             for (int i = n0; i < n0 + N; ++i) items += (int)((rp[i + 1] - rp[i] + 4 * K - 1) / (4 * K));
+            // inert items after the rows' make the chunk-plane stride congruent to
+            // 8/K modulo 8 (K = 8: odd), so that the 8 groups of 4 lanes reading
+            // consecutive synapses of a row (over planes j < K and items q < 8/K)
+            // start on 8 different 4-bank groups
+            while (items % 8 != (8 / K) % 8 && !(K == 8 && items % 2 == 1)) ++items;
             if (N >= 65536 || (long long)N * nt >= 65536)
                 return fail(PSST_ERR_UNSUPPORTED, "adjoint: net %d too large (%d neurons)", b, N);
             long long bytes = psst::adj_smem_need(N, nt, items, K, false);
@@ -1321,7 +1328,7 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
             ck[b] = ck_total;
             sg[b] = seg_total;
             ck_total += nck * R;
-            seg_total += (long long)std::min<long long>(ckpt_every, n_steps) * stage_floats;
+            seg_total += 2LL * std::min<long long>(ckpt_every, n_steps) * stage_floats;  // two buffers
         }
         if (ck_total > h->adj_ck_cap) {
             e = h->alloc(&h->adj_ckpt, (size_t)ck_total);
