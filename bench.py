@@ -10,8 +10,9 @@ steps cover the full 200 ms.  Metric: neuron-RK4-steps per second
 
 Also reported: the single-network forward (the 120-neuron antennal-lobe
 network) on the same GPU, the roofline of the dominant kernel, the FP64
-oracle on the host cores (bounded sample) and an end-to-end number through
-the C interface with host buffers.
+oracle on the host cores (bounded sample), an end-to-end number through
+the C interface with host buffers, and uncoupled neurons (the independent
+ODE systems of the paper's Fig. 2b) with a sweep over their number.
 
 Under torchrun each rank integrates its own batch (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
@@ -241,6 +242,8 @@ def main():
     ap.add_argument("--autotune", type=int, default=200, help="trial steps per shape (0 = off)")
     ap.add_argument("--graph", type=int, default=1, help="CUDA-graph replay of the launch sequence")
     ap.add_argument("--ckpt-every", type=int, default=1000)
+    ap.add_argument("--indep-steps", type=int, default=2000,
+                    help="steps of the independent-neuron leg (0 = off)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -357,6 +360,47 @@ def main():
                   "us_per_rk4_step": sms * 1e3 / args.single_steps,
                   "block_threads": sn_info["block_threads"]}
 
+    # ---- independent neurons (the paper's Fig. 2b systems): one thread per
+    # neuron, no coupling; throughput, ALU fraction and a sweep over N
+    indep = None
+    if rank == 0 and args.indep_steps > 0:
+        from paper_1906_03958_gb300 import netgen as ng
+        peaks = measured_peaks()
+        smax = peaks.get("sm_max_mhz", 2070.0)
+        peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
+
+        def timed(spec, nsteps, reps):
+            with psst.Network(spec) as inet:
+                inet.integrate(min(nsteps, 200))
+                torch.cuda.synchronize()
+                ms = []
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    inet.integrate(nsteps)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(a.elapsed_time(b))
+                inet.status()
+            return float(np.median(ms))
+
+        n_big = 1 << 22
+        big = ng.independent(n_big, rate_hz=20.0)
+        ms_big = timed(big, args.indep_steps, 3)
+        flop = 4.0 * FLOP_NEURON_STAGE * n_big * args.indep_steps
+        sweep = []
+        for n_sys in (1_000, 10_000, 100_000, 1_000_000, 4_000_000):
+            ms_n = timed(ng.independent(n_sys), 200, 20)
+            sweep.append({"n": n_sys, "ms_per_200_steps": ms_n, "neuron_steps_per_s": n_sys * 200 / (ms_n / 1e3)})
+        indep = {"workload": f"{n_big} uncoupled HH neurons (I ~ U[0,10], pulse, Philox shot noise), "
+                             "one thread per neuron, no barriers",
+                 "value": n_big * args.indep_steps / (ms_big / 1e3), "unit": UNIT,
+                 "us_per_rk4_step": ms_big * 1e3 / args.indep_steps,
+                 "roofline": {"bound": "alu", "achieved": flop / (ms_big / 1e3) / 1e12, "peak": peak_tflops,
+                              "unit": "TFLOP/s", "frac": flop / (ms_big / 1e3) / 1e12 / peak_tflops},
+                 "fig2b_sweep": {"method": "median of 20 replicates of 200 RK4 steps (the paper's Fig. 2 timing)",
+                                 "points": sweep}}
+
     # ---- the large sparse network (one network over the whole GPU)
     sparse = None
     if rank == 0 and args.sparse_steps > 0:
@@ -446,7 +490,8 @@ def main():
                           "parallelism": f"replicas x{world}"},
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
-               "single": single, "sparse_large": sparse, "adjoint_over_forward": adjoint}
+               "single": single, "sparse_large": sparse, "adjoint_over_forward": adjoint,
+               "independent": indep}
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -127,6 +127,8 @@ typedef struct {
     int32_t kernel_launches;       /* kernels the last psst_integrate enqueued */
     int32_t n_pair_gate_nets;      /* networks whose forward keeps one gate per (presynaptic neuron, type)
                                       pair; the others keep one gate per synapse (gate_mode) */
+    int32_t n_independent_nets;    /* CTA mode: networks without synapses, integrated one thread per neuron
+                                      without barriers (bitwise the same results) */
 } psst_info;
 
 typedef struct psst_net psst_net;

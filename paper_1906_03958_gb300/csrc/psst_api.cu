@@ -110,6 +110,9 @@ struct psst_net {
     int graph_launches = 0;
     float *tune_buf = nullptr;  // state copy for autotuning trials
     uint8_t *d_check = nullptr; // per-network result of the pair-uniformity check
+    // CTA mode: networks without synapses, integrated one thread per neuron
+    int *d_ind_neuron = nullptr, *d_ind_net = nullptr;
+    int n_ind_neurons = 0, n_ind_nets = 0;
 
     void drop_graph() {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -572,8 +575,17 @@ int setup_cta(psst_net *h, const SmemCaps &caps, cudaError_t *err) {
     std::vector<int> cl_of((size_t)n_nets), per_sm((size_t)n_nets);
     std::vector<long long> need((size_t)n_nets);
     std::vector<double> cost((size_t)n_nets);
+    std::vector<int> ind_neuron, ind_net;  // neurons of the networks without synapses
     for (int b = 0; b < n_nets; ++b) {
         const int n0 = in.net_off[b], N = in.net_off[b + 1] - n0;
+        if (in.net_syn[b] == 0) {  // independent neurons: no size class, no barrier
+            cl_of[b] = 0;
+            for (int i = n0; i < n0 + N; ++i) {
+                ind_neuron.push_back(i);
+                ind_net.push_back(b);
+            }
+            continue;
+        }
         if ((long long)N * nt >= 65536)
             return fail(PSST_ERR_UNSUPPORTED, "net %d: %d neurons x %d synapse types must stay below 65536", b, N, nt);
         const int cl = plan_network(in, b, caps, &plans[b], &need[b]);
@@ -619,7 +631,16 @@ int setup_cta(psst_net *h, const SmemCaps &caps, cudaError_t *err) {
         h->classes[i].plans = dp;
         e = psst::cta_prepare(h->classes[i].cl, caps.max_dyn);
     }
-    if (e == cudaSuccess) e = h->make_streams(h->classes.size() > 1 ? h->classes.size() : 0);
+    if (e == cudaSuccess && !ind_neuron.empty() && !h->d_ind_neuron) {
+        e = upload(h, &h->d_ind_neuron, ind_neuron.data(), ind_neuron.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_ind_net, ind_net.data(), ind_net.size());
+    }
+    h->n_ind_neurons = (int)ind_neuron.size();
+    h->n_ind_nets = 0;
+    for (int b = 0; b < n_nets; ++b) h->n_ind_nets += in.net_syn[b] == 0;
+    // one stream per launch of an integrate chunk when there are several
+    const size_t n_launch = h->classes.size() + (h->n_ind_neurons > 0 ? 1 : 0);
+    if (e == cudaSuccess) e = h->make_streams(n_launch > 1 ? n_launch : 0);
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "CTA mode setup");
     h->block = h->classes.empty() ? 0 : h->classes.back().block;
     h->K = plans.empty() ? 0 : plans[h->classes.empty() ? 0 : all_lists.back()].K;
@@ -719,6 +740,7 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
     }
     bool all_fit = true;
     for (int b = 0; b < n_nets && all_fit; ++b) {
+        if (pin.net_syn[b] == 0) continue;  // independent neurons need no shared-memory plan
         psst::NetPlan pl;
         long long need = 0;
         all_fit = plan_network(pin, b, caps, &pl, &need) != 0;
@@ -888,6 +910,12 @@ int launch_chunks(psst_net *h, long long step0, long long n_steps, long long chu
                 if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
                 ++h->launches;
             }
+            if (h->n_ind_neurons > 0) {
+                cudaError_t e = psst::indep_launch(h->v, h->d_ind_neuron, h->d_ind_net, h->n_ind_neurons,
+                                                   step0 + done, n, fork ? h->class_streams.back() : st);
+                if (e != cudaSuccess) return cuda_fail(e, "psst_integrate launch");
+                ++h->launches;
+            }
         }
         done += n;
     }
@@ -914,7 +942,8 @@ int patch_step0(psst_net *h, long long step0) {
         const int idx = h->mode == PSST_MODE_GRID ? 2 : 3;
         const int nargs = h->mode == PSST_MODE_GRID ? 4 : 6;
         // launches of one chunk share step0; chunks follow in capture order
-        const int per_chunk = h->mode == PSST_MODE_GRID ? 1 : (int)h->classes.size();
+        const int per_chunk =
+            h->mode == PSST_MODE_GRID ? 1 : (int)h->classes.size() + (h->n_ind_neurons > 0 ? 1 : 0);
         chunk_base = (long long)(k / per_chunk) * chunk;
         long long s = step0 + chunk_base;
         void *args[6];
@@ -1385,6 +1414,7 @@ int psst_query(const psst_net *h, psst_info *out) {
     out->n_cluster_nets = h->n_global;
     out->n_launch_classes = (int32_t)h->classes.size();
     out->kernel_launches = h->launches;
+    out->n_independent_nets = h->mode == PSST_MODE_GRID ? 0 : h->n_ind_nets;
     if (h->mode == PSST_MODE_GRID) {
         out->n_pair_gate_nets = h->gv.pair;
     } else {

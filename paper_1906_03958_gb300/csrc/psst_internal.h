@@ -23,6 +23,10 @@ cudaError_t cta_prepare(int cl, int max_smem);
 cudaError_t pair_check(const NetView &v, uint8_t *out, int smem, cudaStream_t stream);
 cudaError_t cta_launch(const NetView &v, const ClassLaunch &c, long long step0, int nsteps, cudaStream_t stream);
 
+// Networks without synapses, one thread per neuron (psst_indep.cu).
+cudaError_t indep_launch(const NetView &v, const int *ind_neuron, const int *ind_net, int count, long long step0,
+                         int nsteps, cudaStream_t stream);
+
 // Grid-wide single-network kernel (psst_grid.cu).
 cudaError_t grid_occupancy(int block, int smem, int *blocks_per_sm);
 cudaError_t grid_launch(const NetView &v, const GridView &g, long long step0, int nsteps, int grid, int block,

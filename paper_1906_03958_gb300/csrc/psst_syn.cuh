@@ -505,12 +505,15 @@ __device__ __forceinline__ float neuron_v(int i, int n, float V, const float *ys
     const float cnext = (ST == 2) ? dt : 0.5f * dt;
     const float dt6 = dt * (1.0f / 6.0f);
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
-    const float m3h = m * m * m * h, n2 = nn * nn, n4 = n2 * n2;
-    const float iion = prm[NP_GNA * n + i] * m3h * (V - prm[NP_ENA * n + i]) +
-                       prm[NP_GK * n + i] * n4 * (V - prm[NP_EK * n + i]) +
-                       prm[NP_GL * n + i] * (V - prm[NP_EL * n + i]) +
-                       prm[NP_GKL * n + i] * (V - prm[NP_EKL * n + i]);
-    const float d = (iext - iion - isyn) * prm[NP_C * n + i];  // prm row 0 holds 1/C
+    // explicit roundings (no contraction left to the compiler), so that every
+    // kernel evaluates the same operations in whatever context it is inlined
+    const float m3h = __fmul_rn(__fmul_rn(__fmul_rn(m, m), m), h);
+    const float n2 = __fmul_rn(nn, nn), n4 = __fmul_rn(n2, n2);
+    float iion = __fmul_rn(__fmul_rn(prm[NP_GNA * n + i], m3h), __fsub_rn(V, prm[NP_ENA * n + i]));
+    iion = fmaf(__fmul_rn(prm[NP_GK * n + i], n4), __fsub_rn(V, prm[NP_EK * n + i]), iion);
+    iion = fmaf(prm[NP_GL * n + i], __fsub_rn(V, prm[NP_EL * n + i]), iion);
+    iion = fmaf(prm[NP_GKL * n + i], __fsub_rn(V, prm[NP_EKL * n + i]), iion);
+    const float d = __fmul_rn(__fsub_rn(__fsub_rn(iext, iion), isyn), prm[NP_C * n + i]);  // row 0: 1/C
     const float ac = (ST == 0) ? d : fmaf(WGT, d, acc[i]);
     if (ST < 3) {
         acc[i] = ac;
@@ -531,9 +534,9 @@ __device__ __forceinline__ void neuron_gates(int i, int n, float V, const float 
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
     const Rates q = hh_rates(V);
     float d[3];
-    d[0] = q.am * (1.0f - m) - q.bm * m;
-    d[1] = q.ah * (1.0f - h) - q.bh * h;
-    d[2] = q.an * (1.0f - nn) - q.bn * nn;
+    d[0] = fmaf(q.am, __fsub_rn(1.0f, m), -__fmul_rn(q.bm, m));
+    d[1] = fmaf(q.ah, __fsub_rn(1.0f, h), -__fmul_rn(q.bh, h));
+    d[2] = fmaf(q.an, __fsub_rn(1.0f, nn), -__fmul_rn(q.bn, nn));
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
         const int ix = (x + 1) * n + i;

@@ -204,6 +204,32 @@ def plain20(seed: int = 1001, weight_scale: float = 1.0) -> NetworkSpec:
                           name=f"plain20(seed={seed},wscale={weight_scale})")
 
 
+def independent(n_neurons: int, seed: int = 1006, n_nets: int = 1, rate_hz: float = 0.0,
+                noise_amp: float = 10.0, pulse: bool = True) -> NetworkSpec:
+    """n_neurons uncoupled HH neurons (no synapses), the independent ODE systems
+    of the paper's Fig. 2b benchmark: I ~ U[0, 10] uA/cm^2, optionally a
+    10 uA/cm^2 pulse to every neuron from 20 to 150 ms and Philox shot noise
+    at ``rate_hz``, split into ``n_nets`` networks of about equal size."""
+    rng = np.random.default_rng(seed)
+    n = int(n_neurons)
+    cuts = np.linspace(0, n, n_nets + 1).round().astype(np.int64)
+    dt = DT
+    thresh = int(round(rate_hz * 1e-3 * dt * (1 << 24))) if rate_hz > 0 else 0
+    return NetworkSpec(
+        net_neuron_off=cuts.astype(np.int32),
+        neuron_type=np.zeros(n, np.int32),
+        neuron_params=np.asarray(neuron_table(HH), np.float32),
+        row_ptr=np.zeros(n + 1, np.int64),
+        pre=np.zeros(0, np.int32), weight=np.zeros(0, np.float32), syn_type=np.zeros(0, np.int32),
+        syn_params=np.asarray(synapse_table(ACH), np.float32),
+        i_const=rng.uniform(0.0, 10.0, n).astype(np.float32),
+        pulse_amp=np.full(n, 10.0 if pulse else 0.0, np.float32),
+        pulse_on=np.full(n_nets, int(round(20.0 / dt)), np.int64),
+        pulse_off=np.full(n_nets, int(round(150.0 / dt)), np.int64),
+        noise_seed=seed, noise_thresh=thresh, noise_amp=float(noise_amp) if thresh else 0.0,
+        dt=dt, name=f"independent(n={n},nets={n_nets},seed={seed})")
+
+
 def antennal_lobe(seed: int = 1002, n_pn: int = 90, n_ln: int = 30, p: float = 0.5,
                   odor_on_ms: float = 100.0, odor_off_ms: float = 600.0,
                   odor_frac: float = 1.0 / 3.0, odor_amp: float = 100.0,

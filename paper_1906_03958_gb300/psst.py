@@ -69,7 +69,8 @@ class Info(C.Structure):
                 ("block_threads", C.c_int32), ("item_chunks", C.c_int32), ("grid_ctas", C.c_int32),
                 ("smem_bytes", C.c_int32), ("n_single_cta_nets", C.c_int32),
                 ("n_cluster_nets", C.c_int32), ("n_launch_classes", C.c_int32),
-                ("kernel_launches", C.c_int32), ("n_pair_gate_nets", C.c_int32)]
+                ("kernel_launches", C.c_int32), ("n_pair_gate_nets", C.c_int32),
+                ("n_independent_nets", C.c_int32)]
 
 
 _lib = None
