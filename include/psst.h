@@ -60,6 +60,11 @@ extern "C" {
 #define PSST_SYN_NPARAM 9
 #define PSST_MAX_SYN_TYPES 8
 
+/* Integration methods (Sec. "Brain simulations as computational graphs":
+   Euler's method, Eq. euler, and the fourth-order Runge-Kutta method). */
+#define PSST_METHOD_RK4 0    /* classic RK4 (c = 0, 1/2, 1/2, 1; b = 1/6, 1/3, 1/3, 1/6) */
+#define PSST_METHOD_EULER 1  /* forward Euler: y_{n+1} = y_n + dt f(y_n, t_n) */
+
 /* Execution modes. */
 #define PSST_MODE_AUTO 0  /* CTA mode when every network fits one CTA, else grid */
 #define PSST_MODE_CTA 1   /* each network held on chip by one CTA or a cluster of
@@ -111,6 +116,7 @@ typedef struct {
     int32_t gate_mode;             /* 0: one gate per (presynaptic neuron, type) pair whenever all
                                       its synapses' gates are equal (bitwise-identical results,
                                       less work), else one per synapse; 1: always one per synapse */
+    int32_t method;                /* PSST_METHOD_RK4 (0) or PSST_METHOD_EULER; psst_adjoint needs RK4 */
 } psst_network_desc;
 
 typedef struct {
@@ -229,10 +235,12 @@ int psst_record_checkpoints(psst_net *h, int32_t every, int64_t max_steps);
    ckpt_every = 0 differentiates instead the span of the last psst_integrate
    call, whose checkpoints were recorded (psst_record_checkpoints); n_steps
    must equal that call's; PSST_ERR_STATE if no such checkpoints exist.
-   Preconditions: CTA mode; every network fits one CTA for the adjoint; all
+   Preconditions: CTA mode and method PSST_METHOD_RK4 (else
+   PSST_ERR_UNSUPPORTED); every network fits one CTA for the adjoint; all
    gates of a (presynaptic neuron, synapse type) pair hold the same value at
    the start (true from rest), else the device reports PSST_ERR_UNSUPPORTED
-   through psst_status.  Asynchronous on `stream`. */
+   through psst_status.  Each network runs on a cluster of two CTAs (forward
+   recompute beside the reverse sweep).  Asynchronous on `stream`. */
 int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_frames, int32_t ckpt_every,
                  float *grad_w, float *grad_neuron_params, float *grad_state0, void *stream);
 

@@ -262,6 +262,8 @@ int validate(const psst_network_desc *d) {
     }
     if (d->mode < PSST_MODE_AUTO || d->mode > PSST_MODE_GRID) return fail(PSST_ERR_INVALID_ARG, "unknown mode");
     if (d->gate_mode < 0 || d->gate_mode > 1) return fail(PSST_ERR_INVALID_ARG, "gate_mode must be 0 or 1");
+    if (d->method != PSST_METHOD_RK4 && d->method != PSST_METHOD_EULER)
+        return fail(PSST_ERR_INVALID_ARG, "method must be PSST_METHOD_RK4 (0) or PSST_METHOD_EULER (1)");
     return PSST_OK;
 }
 
@@ -766,6 +768,7 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
     v.noise_thresh = d->noise_thresh;
     v.noise_amp = d->noise_amp;
     v.dt = d->dt;
+    v.method = d->method;
     v.rec_stride = d->rec_stride;
     v.rec_cap = d->rec_stride > 0 ? d->rec_capacity : 0;
 
@@ -1271,6 +1274,8 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
                  float *grad_w, float *grad_neuron_params, float *grad_state0, void *stream) {
     if (!h || !grad_w || !grad_neuron_params) return fail(PSST_ERR_INVALID_ARG, "NULL argument");
     if (h->mode != PSST_MODE_CTA) return fail(PSST_ERR_UNSUPPORTED, "the adjoint runs in CTA mode only");
+    if (h->v.method != PSST_METHOD_RK4)
+        return fail(PSST_ERR_UNSUPPORTED, "the adjoint is the discrete adjoint of the RK4 map (method RK4 only)");
     if (n_steps < 1 || n_steps > (1LL << 30)) return fail(PSST_ERR_INVALID_ARG, "n_steps must be in 1..2^30");
     const bool recorded = ckpt_every == 0;
     if (recorded) {

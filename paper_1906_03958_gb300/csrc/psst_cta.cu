@@ -64,22 +64,26 @@ struct SmemCoef {
     __device__ __forceinline__ float4 s(int i) const { return t2[i]; }
 };
 
+// One stage: ST = 0..3 of classic RK4, or ST = 4, the single stage of forward
+// Euler.  par selects the double-buffered stage potentials and gates read by
+// this stage (RK4: ST & 1; Euler: the step's parity).
 template <int ST, int CL, bool HAS2, bool PAIR>
 __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0, int N, int nt, int M, int r_lo,
                                       int nown, unsigned rank, long long rec_slot, float dt, float *vst, float *y0,
                                       float *acc, float *ys, const float *prm, const float *iext, float2 *cur1,
                                       float2 *acc1, float2 *fin1, float4 *cur2, float4 *acc2, float4 *fin2,
-                                      float *pst, float *Gt, int lrep, const float *stab) {
+                                      float *pst, float *Gt, int lrep, const float *stab, int par) {
+    constexpr bool FIRST = ST == 0 || ST == 4, LAST = ST >= 3;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const float *vcur = vst + (ST & 1) * N;
-    float *vnxt = vst + ((ST + 1) & 1) * N;
-    const float *ysc = ys + (ST & 1) * 3 * nown;
-    float *ysn = ys + ((ST + 1) & 1) * 3 * nown;
+    const float *vcur = vst + par * N;
+    float *vnxt = vst + (par ^ 1) * N;
+    const float *ysc = ys + par * 3 * nown;
+    float *ysn = ys + (par ^ 1) * 3 * nown;
     // gate-map entries: every (neuron, type) pair, or the used pairs (PAIR)
     float *r0p = pst, *s0p = pst + M;
     const unsigned short *pof = (const unsigned short *)(pst + 2 * M);
     if (PAIR) sphase_pair(it, Gt, lrep);
-    else sphase<ST, HAS2>(it, SmemCoef{ST == 0 ? fin1 : cur1, ST == 0 ? fin2 : cur2});
+    else sphase<ST, HAS2>(it, SmemCoef{FIRST ? fin1 : cur1, FIRST ? fin2 : cur2});
     __syncthreads();
     // independent work units: potential of each owned neuron, its gates, and
     // the gate map (and per-pair gate) of each entry
@@ -95,7 +99,7 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
 #pragma unroll
                 for (unsigned q = 1; q < CL; ++q) st_peer(vnxt + r_lo + i, (rank + q) % CL, vn);
             }
-            if (ST == 3 && rec_slot >= 0) v.rec[rec_slot * v.N + n0 + r_lo + i] = vn;
+            if (LAST && rec_slot >= 0) v.rec[rec_slot * v.N + n0 + r_lo + i] = vn;
         } else if (u < 2 * nown) {
             const int i = u - nown;
             neuron_gates<ST>(i, nown, vcur[r_lo + i], ysc, ysn, y0, acc, dt);
@@ -111,7 +115,7 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
             if (PAIR) {
                 // the pair's gate for the next stage (same operations as the per-synapse path)
                 const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
-                if (ST < 3) {
+                if (!LAST) {
                     put_gate(Gt, p, lrep, pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]));
                 } else {
                     const float r0 = r0p[p], s0 = s0p[p];
@@ -223,14 +227,19 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         for (int i = tid; i < nown; i += nthr)
             iext[i] = input_current(v, inp[i], inp[nown + i], in_pulse, (long long)n0 + r_lo + i, step);
         // iext is read in the N-phase, after the S-phase barrier
+        if (v.method == PSST_METHOD_EULER) {
+            stage<4, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm,
+                                     iext, cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, itn & 1);
+            continue;
+        }
         stage<0, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab);
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, 0);
         stage<1, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab);
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, 1);
         stage<2, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab);
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, 0);
         stage<3, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab);
+                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, 1);
     }
 
     // write back: owned synapses with the last step's gate map, owned neurons

@@ -49,6 +49,7 @@ struct NetView {
     const int *pair_tix;         // [N * n_stypes] or null
     const int *pair_of;          // [used pairs of all networks]
     const int *pair_off;         // [n_nets + 1]
+    int method;                  // PSST_METHOD_RK4 or PSST_METHOD_EULER
 };
 
 enum : uint8_t { NET_HAS2 = 1, NET_PAIR = 2 };  // NET_PAIR: all gates of each (pre, type) pair equal

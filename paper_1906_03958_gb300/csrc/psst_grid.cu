@@ -85,20 +85,24 @@ struct GlobalCoef {
     __device__ __forceinline__ float4 s(int i) const { return __ldcg(t2 + i); }
 };
 
+// One stage: ST = 0..3 of classic RK4, or ST = 4, forward Euler's single
+// stage; par selects the double-buffered potentials, gates and global tables
+// this stage reads (RK4: ST & 1; Euler: the step's parity).
 template <int ST, bool HAS2, bool PAIR>
 __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, const Items &it, int lo, int N,
                                            int nt, int M, long long rec_slot, float dt, float *vst, float *y0,
                                            float *acc, float *ys, const float *prm, const float *iext,
                                            float2 *cur1, float2 *acc1, float4 *cur2, float4 *acc2, float *pst,
-                                           float *gtab, const float *stab) {
+                                           float *gtab, const float *stab, int par) {
+    constexpr bool LAST = ST >= 3;
     const int tid = threadIdx.x, nthr = blockDim.x, Mloc = N * nt;
-    const float *vcur = vst + (ST & 1) * N;
-    float *vnxt = vst + ((ST + 1) & 1) * N;
-    const float *ysc = ys + (ST & 1) * 3 * N;
-    float *ysn = ys + ((ST + 1) & 1) * 3 * N;
+    const float *vcur = vst + par * N;
+    float *vnxt = vst + (par ^ 1) * N;
+    const float *ysc = ys + par * 3 * N;
+    float *ysn = ys + (par ^ 1) * 3 * N;
     if (PAIR) {
         // this stage's gate of every used pair, written by the owners before the last barrier
-        const float4 *src = (const float4 *)(g.gt + (size_t)(ST & 1) * g.mt);
+        const float4 *src = (const float4 *)(g.gt + (size_t)par * g.mt);
         float4 *dst = (float4 *)gtab;
         const int n4 = g.mt >> 2;
 #pragma unroll 4
@@ -106,15 +110,15 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
         __syncthreads();
         sphase_pair(it, gtab, 0);
     } else {
-        sphase<ST, HAS2>(it, GlobalCoef{g.c1 + (size_t)(ST & 1) * M, HAS2 ? g.c2 + (size_t)(ST & 1) * M : nullptr});
+        sphase<ST, HAS2>(it, GlobalCoef{g.c1 + (size_t)par * M, HAS2 ? g.c2 + (size_t)par * M : nullptr});
     }
     __syncthreads();
     // independent work units: potential and gates of each owned neuron, and
     // the gate map of each own (neuron, type) pair
     float *r0p = pst, *s0p = pst + Mloc;
-    float *gout = PAIR ? g.gt + (size_t)((ST + 1) & 1) * g.mt : nullptr;
-    float2 *o1 = g.c1 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt;
-    float4 *o2 = HAS2 ? g.c2 + (size_t)((ST + 1) & 1) * M + (size_t)lo * nt : nullptr;
+    float *gout = PAIR ? g.gt + (size_t)(par ^ 1) * g.mt : nullptr;
+    float2 *o1 = g.c1 + (size_t)(par ^ 1) * M + (size_t)lo * nt;
+    float4 *o2 = HAS2 ? g.c2 + (size_t)(par ^ 1) * M + (size_t)lo * nt : nullptr;
     const int U = 2 * N + Mloc;
     for (int u = tid; u < U; u += nthr) {
         if (u < N) {
@@ -123,7 +127,7 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
             const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
             const float vn = neuron_v<ST>(i, N, V, ysc, y0, acc, prm, iext[i], isyn, dt);
             vnxt[i] = vn;
-            if (ST == 3 && rec_slot >= 0) v.rec[rec_slot * v.N + lo + i] = vn;
+            if (LAST && rec_slot >= 0) v.rec[rec_slot * v.N + lo + i] = vn;
         } else if (u < 2 * N) {
             const int i = u - N;
             neuron_gates<ST>(i, N, vcur[i], ysc, ysn, y0, acc, dt);
@@ -142,7 +146,7 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
                 coef_update<ST, HAS2>(sp, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
                 const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
                 float G;
-                if (ST < 3) {
+                if (!LAST) {
                     G = pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]);
                 } else {
                     const float r0 = r0p[p], s0 = s0p[p];
@@ -159,8 +163,8 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
                 float4 &c2 = HAS2 ? cur2[p] : d4;
                 float4 &a2 = HAS2 ? acc2[p] : d4;
                 coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
-                o1[p] = ST == 3 ? f1 : cur1[p];
-                if (HAS2) o2[p] = ST == 3 ? f2 : cur2[p];
+                o1[p] = LAST ? f1 : cur1[p];
+                if (HAS2) o2[p] = LAST ? f2 : cur2[p];
             }
         }
     }
@@ -256,17 +260,22 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         }
         for (int i = tid; i < N; i += nthr)
             iext[i] = input_current(v, inp[i], inp[N + i], in_pulse, (long long)lo + i, step);
+        if (v.method == PSST_METHOD_EULER) {
+            ok = grid_stage<4, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
+                                           acc1, cur2, acc2, pst, gtab, stab, itn & 1);
+            continue;
+        }
         ok = grid_stage<0, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                       acc1, cur2, acc2, pst, gtab, stab);
+                                       acc1, cur2, acc2, pst, gtab, stab, 0);
         if (ok)
             ok = grid_stage<1, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab);
+                                           acc1, cur2, acc2, pst, gtab, stab, 1);
         if (ok)
             ok = grid_stage<2, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab);
+                                           acc1, cur2, acc2, pst, gtab, stab, 0);
         if (ok)
             ok = grid_stage<3, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab);
+                                           acc1, cur2, acc2, pst, gtab, stab, 1);
     }
     if (!ok) return;  // error recorded; global state keeps its value from before the call
 

@@ -54,11 +54,17 @@ __global__ void __launch_bounds__(INDEP_THREADS) indep_kernel(NetView v, const i
     for (int itn = 0; itn < nsteps; ++itn) {
         const long long step = step0 + itn;
         const float iext = input_current(v, i_const, pulse, step >= pon && step < poff, gi, step);
-        // stage gates alternate between ysa (even stages read) and ysb
-        V = indep_stage<0>(V, ysa, ysb, y0, acc, prm, iext, dt);
-        V = indep_stage<1>(V, ysb, ysa, y0, acc, prm, iext, dt);
-        V = indep_stage<2>(V, ysa, ysb, y0, acc, prm, iext, dt);
-        V = indep_stage<3>(V, ysb, ysa, y0, acc, prm, iext, dt);
+        if (v.method == PSST_METHOD_EULER) {
+            // one stage per step; the gates alternate between ysa and ysb by step
+            if (itn & 1) V = indep_stage<4>(V, ysb, ysa, y0, acc, prm, iext, dt);
+            else V = indep_stage<4>(V, ysa, ysb, y0, acc, prm, iext, dt);
+        } else {
+            // stage gates alternate between ysa (even stages read) and ysb
+            V = indep_stage<0>(V, ysa, ysb, y0, acc, prm, iext, dt);
+            V = indep_stage<1>(V, ysb, ysa, y0, acc, prm, iext, dt);
+            V = indep_stage<2>(V, ysa, ysb, y0, acc, prm, iext, dt);
+            V = indep_stage<3>(V, ysb, ysa, y0, acc, prm, iext, dt);
+        }
         if (rec_phase >= 0) {
             if (rec_phase == 0) v.rec[(((step + 1) / v.rec_stride - 1) % v.rec_cap) * v.N + gi] = V;
             rec_phase = rec_phase + 1 == v.rec_stride ? 0 : rec_phase + 1;

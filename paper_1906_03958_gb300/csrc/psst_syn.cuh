@@ -214,8 +214,11 @@ __device__ __forceinline__ void syn2(float &r, float &s, float w, float we, floa
 
 // S-phase: every item's partial sums (A, B) at stage ST.  Coef supplies
 // r(ci) (float2 r-map) and s(ci) (float4 s-map, w = Kd).
+// ST = 0..3: the stages of classic RK4; ST = 4: the single stage of forward
+// Euler (first and last stage of its step).
 template <int ST, bool HAS2, class Coef>
 __device__ __forceinline__ void sphase(const Items &it, const Coef &cf) {
+    constexpr bool FIRST = ST == 0 || ST == 4;
     const int tid = threadIdx.x, nthr = blockDim.x, K = it.K, n1 = it.n1;
     for (int t = tid; t < n1; t += nthr) {
         float A = 0.0f, B = 0.0f;
@@ -224,11 +227,11 @@ __device__ __forceinline__ void sphase(const Items &it, const Coef &cf) {
             float4 r = it.r[c];
             const float4 w = it.w[c], we = it.we[c];
             const ushort4 id = it.id[c];
-            syn1<ST == 0>(r.x, w.x, we.x, cf.r(id.x), A, B);
-            syn1<ST == 0>(r.y, w.y, we.y, cf.r(id.y), A, B);
-            syn1<ST == 0>(r.z, w.z, we.z, cf.r(id.z), A, B);
-            syn1<ST == 0>(r.w, w.w, we.w, cf.r(id.w), A, B);
-            if (ST == 0) it.r[c] = r;
+            syn1<FIRST>(r.x, w.x, we.x, cf.r(id.x), A, B);
+            syn1<FIRST>(r.y, w.y, we.y, cf.r(id.y), A, B);
+            syn1<FIRST>(r.z, w.z, we.z, cf.r(id.z), A, B);
+            syn1<FIRST>(r.w, w.w, we.w, cf.r(id.w), A, B);
+            if (FIRST) it.r[c] = r;
         }
         it.pa[t] = A;
         it.pb[t] = B;
@@ -242,11 +245,11 @@ __device__ __forceinline__ void sphase(const Items &it, const Coef &cf) {
                 float4 r = it.r[c], s = it.s[c];
                 const float4 w = it.w[c], we = it.we[c];
                 const ushort4 id = it.id[c];
-                syn2<ST == 0>(r.x, s.x, w.x, we.x, cf.r(id.x), cf.s(id.x), A, B);
-                syn2<ST == 0>(r.y, s.y, w.y, we.y, cf.r(id.y), cf.s(id.y), A, B);
-                syn2<ST == 0>(r.z, s.z, w.z, we.z, cf.r(id.z), cf.s(id.z), A, B);
-                syn2<ST == 0>(r.w, s.w, w.w, we.w, cf.r(id.w), cf.s(id.w), A, B);
-                if (ST == 0) {
+                syn2<FIRST>(r.x, s.x, w.x, we.x, cf.r(id.x), cf.s(id.x), A, B);
+                syn2<FIRST>(r.y, s.y, w.y, we.y, cf.r(id.y), cf.s(id.y), A, B);
+                syn2<FIRST>(r.z, s.z, w.z, we.z, cf.r(id.z), cf.s(id.z), A, B);
+                syn2<FIRST>(r.w, s.w, w.w, we.w, cf.r(id.w), cf.s(id.w), A, B);
+                if (FIRST) {
                     it.r[c] = r;
                     it.s[c] = s;
                 }
@@ -446,19 +449,20 @@ __device__ __forceinline__ float pair_gate(bool second, float2 F, float4 F2, flo
 
 // Gate-map update of one (presynaptic neuron j, synapse type tau) pair at
 // stage ST from the stage-ST potential V of j.  cur/acc hold this stage's
-// map and the running RK4 sum; writes the next stage's map into cur (ST < 3)
-// or the step's final map into fin (ST == 3).  The s-map's fourth component
+// map and the running RK4 sum; writes the next stage's map into cur, or at
+// the step's last stage (ST 3, or 4 for Euler) the step's final map into fin.  The s-map's fourth component
 // carries Kd (1 for first-order types, whose s-map is never used).
 template <int ST, bool HAS2>
 __device__ __forceinline__ void coef_update(const float *sp, float V, float dt, float2 &cur, float2 &acc,
                                             float2 &fin, float4 &cur2, float4 &acc2, float4 &fin2) {
+    constexpr bool FIRST = ST == 0 || ST == 4, LAST = ST >= 3;
     constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
     const float cnext = (ST == 2) ? dt : 0.5f * dt;
-    const float dt6 = dt * (1.0f / 6.0f);
+    const float dt6 = ST == 4 ? dt : dt * (1.0f / 6.0f);  // weight of the k-sum at the step's end
     const float T = transmitter(V, sp[SP_VP], sp[SP_KP]);  // table holds 1/Kp
     const float a_ = sp[SP_A] * T, bb = a_ + sp[SP_B];
     float P = 0.0f, Q = 1.0f, U = 0.0f, X = 0.0f, Z = 1.0f;
-    if (ST > 0) {
+    if (!FIRST) {
         P = cur.x;
         Q = cur.y;
         if (HAS2) {
@@ -469,8 +473,8 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, float dt, 
     }
     const float kP = fmaf(-bb, P, a_), kQ = -bb * Q;
     float2 A1 = make_float2(kP, kQ);
-    if (ST > 0) A1 = make_float2(fmaf(WGT, kP, acc.x), fmaf(WGT, kQ, acc.y));
-    if (ST < 3) {
+    if (!FIRST) A1 = make_float2(fmaf(WGT, kP, acc.x), fmaf(WGT, kQ, acc.y));
+    if (!LAST) {
         acc = A1;
         cur = make_float2(cnext * kP, fmaf(cnext, kQ, 1.0f));
     } else {
@@ -481,8 +485,8 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, float dt, 
         const float Kd = sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f;
         const float kU = fmaf(K3, P, -K4 * U), kX = fmaf(K3, Q, -K4 * X), kZ = -K4 * Z;
         float4 A2 = make_float4(kU, kX, kZ, 0.0f);
-        if (ST > 0) A2 = make_float4(fmaf(WGT, kU, acc2.x), fmaf(WGT, kX, acc2.y), fmaf(WGT, kZ, acc2.z), 0.0f);
-        if (ST < 3) {
+        if (!FIRST) A2 = make_float4(fmaf(WGT, kU, acc2.x), fmaf(WGT, kX, acc2.y), fmaf(WGT, kZ, acc2.z), 0.0f);
+        if (!LAST) {
             acc2 = A2;
             cur2 = make_float4(cnext * kU, cnext * kX, fmaf(cnext, kZ, 1.0f), Kd);
         } else {
@@ -497,13 +501,15 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, float dt, 
 // [4][n] (V, m, h, n); the stage gates are double-buffered by stage parity,
 // ysc = [3][n] of this stage (read by both halves), ysn = [3][n] of the next.
 
-// Potential: returns the next stage's V (ST < 3) or the new step-start V.
+// Potential: returns the next stage's V, or after the step's last stage (ST 3,
+// or 4 for Euler) the new step-start V.
 template <int ST>
 __device__ __forceinline__ float neuron_v(int i, int n, float V, const float *ysc, float *y0, float *acc,
                                           const float *prm, float iext, float isyn, float dt) {
+    constexpr bool FIRST = ST == 0 || ST == 4, LAST = ST >= 3;
     constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
     const float cnext = (ST == 2) ? dt : 0.5f * dt;
-    const float dt6 = dt * (1.0f / 6.0f);
+    const float dt6 = ST == 4 ? dt : dt * (1.0f / 6.0f);  // weight of the k-sum at the step's end
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
     // explicit roundings (no contraction left to the compiler), so that every
     // kernel evaluates the same operations in whatever context it is inlined
@@ -514,8 +520,8 @@ __device__ __forceinline__ float neuron_v(int i, int n, float V, const float *ys
     iion = fmaf(prm[NP_GL * n + i], __fsub_rn(V, prm[NP_EL * n + i]), iion);
     iion = fmaf(prm[NP_GKL * n + i], __fsub_rn(V, prm[NP_EKL * n + i]), iion);
     const float d = __fmul_rn(__fsub_rn(__fsub_rn(iext, iion), isyn), prm[NP_C * n + i]);  // row 0: 1/C
-    const float ac = (ST == 0) ? d : fmaf(WGT, d, acc[i]);
-    if (ST < 3) {
+    const float ac = FIRST ? d : fmaf(WGT, d, acc[i]);
+    if (!LAST) {
         acc[i] = ac;
         return fmaf(cnext, d, y0[i]);
     }
@@ -524,13 +530,15 @@ __device__ __forceinline__ float neuron_v(int i, int n, float V, const float *ys
     return yn;
 }
 
-// Gates: writes the next stage's (ST < 3) or the new step-start m, h, n.
+// Gates: writes the next stage's m, h, n, or after the last stage the new
+// step-start ones.
 template <int ST>
 __device__ __forceinline__ void neuron_gates(int i, int n, float V, const float *ysc, float *ysn, float *y0,
                                              float *acc, float dt) {
+    constexpr bool FIRST = ST == 0 || ST == 4, LAST = ST >= 3;
     constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
     const float cnext = (ST == 2) ? dt : 0.5f * dt;
-    const float dt6 = dt * (1.0f / 6.0f);
+    const float dt6 = ST == 4 ? dt : dt * (1.0f / 6.0f);  // weight of the k-sum at the step's end
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
     const Rates q = hh_rates(V);
     float d[3];
@@ -540,9 +548,9 @@ __device__ __forceinline__ void neuron_gates(int i, int n, float V, const float 
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
         const int ix = (x + 1) * n + i;
-        const float ac = (ST == 0) ? d[x] : fmaf(WGT, d[x], acc[ix]);
+        const float ac = FIRST ? d[x] : fmaf(WGT, d[x], acc[ix]);
         float yn;
-        if (ST < 3) {
+        if (!LAST) {
             acc[ix] = ac;
             yn = fmaf(cnext, d[x], y0[ix]);
         } else {

@@ -19,6 +19,7 @@ import numpy as np
 from . import build as _build
 
 MODE_AUTO, MODE_CTA, MODE_GRID = 0, 1, 2
+METHOD_RK4, METHOD_EULER = 0, 1
 OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT",
           -6: "STATE", -7: "UNSUPPORTED"}
@@ -48,7 +49,7 @@ class NetworkDesc(C.Structure):
                 ("noise_amp", C.c_float), ("dt", C.c_float), ("init_state", C.c_void_p),
                 ("rec_stride", C.c_int32), ("rec_capacity", C.c_int64), ("mode", C.c_int32),
                 ("block_threads", C.c_int32), ("item_chunks", C.c_int32), ("device", C.c_int32),
-                ("gate_mode", C.c_int32)]
+                ("gate_mode", C.c_int32), ("method", C.c_int32)]
 
 
 class DeviceNetwork(C.Structure):
@@ -152,7 +153,7 @@ class Network:
 
     def __init__(self, spec, init_state=None, rec_stride: int = 0, rec_capacity: int = 0,
                  mode: int = MODE_AUTO, block_threads: int = 0, item_chunks: int = 0,
-                 device: int | None = None, gate_mode: int = 0):
+                 device: int | None = None, gate_mode: int = 0, method: int = 0):
         lib = load()
         keep = dict(
             off=_arr(spec.net_neuron_off, np.int32), nt=_arr(spec.neuron_type, np.int32),
@@ -177,7 +178,7 @@ class Network:
             noise_amp=float(spec.noise_amp), dt=float(spec.dt), init_state=ptr("init"),
             rec_stride=int(rec_stride), rec_capacity=int(rec_capacity), mode=int(mode),
             block_threads=int(block_threads), item_chunks=int(item_chunks), device=int(device),
-            gate_mode=int(gate_mode))
+            gate_mode=int(gate_mode), method=int(method))
         h = C.c_void_p()
         _check(lib.psst_create_network(C.byref(d), C.byref(h)))
         self._h = h
