@@ -81,6 +81,9 @@ def _desc(spec, **kw):
     ("block_threads", 100, b"block_threads"),
     ("item_chunks", 65, b"item_chunks"),
     ("rec_stride", -1, b"rec_stride"),
+    ("gate_mode", 2, b"gate_mode"),
+    ("method", 2, b"method"),
+    ("mode", 3, b"mode"),
 ])
 def test_invalid_descriptor_rejected_on_host(lib, field, value, needle):
     spec = ng.plain20()
