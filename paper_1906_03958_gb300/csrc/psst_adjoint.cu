@@ -2,7 +2,8 @@
 //
 // Gradient of L = sum_f sum_i dL/dV[f][i] V_i(frame f) over n RK4 steps from
 // the current state, with respect to every synaptic weight and every
-// neuron-type parameter, for batches of networks (one CTA per network).
+// neuron-type parameter, for batches of networks (one cluster of two CTAs per
+// network: one recomputes segments forward, the other sweeps them backward).
 //
 // Gate state.  When all gates of a (presynaptic neuron j, synapse type tau)
 // pair start from the same value -- as they do from rest -- they stay equal

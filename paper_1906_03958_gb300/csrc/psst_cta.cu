@@ -1,26 +1,31 @@
-// Network-resident RK4 integration for batches of small and medium networks.
+// Network-resident RK4 (or Euler) integration for batches of small and
+// medium networks.
 //
 // One network is owned by a cluster of CL CTAs (CL = 1, 2 or 4, chosen per
 // network by its shared-memory footprint) for all of a launch's steps.  Each
 // CTA of the cluster owns a block of rows (postsynaptic neurons): their
 // synapses, as work items in shared memory (psst_syn.cuh), and their neuron
 // state.  Every CTA keeps the stage potential of all N neurons and the gate
-// maps of all (neuron, type) pairs.  One launch per size class integrates
-// all networks of that class, largest first.
+// maps of all used (neuron, type) pairs.  One launch per size class
+// integrates all networks of that class, largest first; the classes run on
+// their own streams.  Networks without synapses are integrated elsewhere
+// (psst_indep.cu).
 //
 // Per RK4 step (classic tableau, Sec. "Brain simulations as computational
-// graphs", RK4 paragraph) and stage s = 0..3:
-//   S-phase   each thread sums w G and wE G over its work items;
+// graphs", RK4 paragraph) and stage s = 0..3 (Euler: one stage):
+//   S-phase   each thread sums its work items (per-pair layout: A = sum w G
+//             with the pair's gate G gathered from the gate table);
 //   barrier   (CTA);
-//   N-phase   the thread of owned neuron i adds its row's item partials
-//             (I_syn,i = V_i A_i - B_i), evaluates the HH right-hand side and
-//             the RK4 stage/combine, and writes the next stage potential to
-//             every CTA of the cluster (distributed shared memory); the other
-//             threads update the gate maps of all pairs from the stage-s
-//             potentials (identical values in every CTA);
+//   N-phase   one work loop over independent units: the potential of each
+//             owned neuron (its row's item partials give I_syn, then the HH
+//             currents and the stage update; the next stage potential goes
+//             to every CTA of the cluster through distributed shared
+//             memory), its gates m, h, n, and the gate map (and per-pair
+//             gate) of every entry from the stage-s potentials (identical
+//             values in every CTA);
 //   barrier   CTA barrier (CL = 1) or cluster barrier (CL > 1).
-// Stage potentials are double-buffered by stage parity, so a CTA can write
-// the next stage's values while a peer still reads this stage's.
+// Stage potentials and gates are double-buffered by parity, so a CTA can
+// write the next stage's values while a peer still reads this stage's.
 //
 // Synaptic gates: a gate's equation dr/dt = a T_j (1 - r) - b r is affine in
 // r with coefficients set by its presynaptic neuron j alone, so each RK4
@@ -28,7 +33,9 @@
 // s^(s) = U_s + X_s r0 + Z_s s0) with the maps propagated once per
 // (neuron, type) and stage; the step-end map is applied lazily at the next
 // step's first stage.  This evaluates the same RK4 map as the textbook stage
-// recursion, with each synapse costing one FMA per stage for its gate.
+// recursion.  When all gates of a pair are equal (from rest) one gate per
+// pair is kept (per-pair layout); else each synapse applies the map to its
+// own gate with one FMA per stage.
 #include <cuda_runtime.h>
 
 #include "psst_device.cuh"
