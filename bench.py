@@ -91,9 +91,15 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources' code (line comments and blank lines
+    dropped, so that a comment edit does not invalidate a capture)."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1906_03958_gb300", "csrc"))):
-        h.update(open(os.path.join(ROOT, "paper_1906_03958_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_1906_03958_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        for line in open(os.path.join(csrc, f), encoding="utf-8"):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
