@@ -170,13 +170,17 @@ int psst_set_barrier_timeout(psst_net *h, int64_t timeout_ns);
    checkpoint recording (those calls launch directly). */
 int psst_set_graph_mode(psst_net *h, int enable);
 
-/* Autotuner: for each size class of a CTA-mode handle, time trial_steps
-   steps with twice, once, half and a quarter of the class's default CTA
-   size, each with the planned number of shared-memory copies of the
-   per-pair gate table and with a single copy (from a copy of the state,
-   recording off; the state is restored), and keep the fastest.  Neither
-   choice changes the summation order, so results stay bitwise identical.
-   Synchronises `stream`.  Grid mode: no-op. */
+/* Autotuner: when the batch needs at most half the GPU's SMs, first time
+   trial_steps steps with each network spread over clusters of at least 1,
+   2 and 4 CTAs (networks large enough) and keep the fastest; then, for each
+   size class of a CTA-mode handle, time trial_steps steps with twice, once,
+   half and a quarter of the class's default CTA size, each with the planned
+   number of shared-memory copies of the per-pair gate table and with a
+   single copy, and keep the fastest.  Trials start from a copy of the state
+   with recording off; the state is restored.  No choice changes the
+   summation order (a larger cluster keeps the work-item size of one CTA),
+   so results stay bitwise identical.  Synchronises `stream`.  Grid mode:
+   no-op. */
 int psst_autotune(psst_net *h, int64_t trial_steps, void *stream);
 
 /* Synchronise `stream` and return the device error word (0 if none), then

@@ -60,6 +60,7 @@ struct SmemCaps {
 // gate uniformity of a network changes (psst_set_state).
 struct PlanInput {
     int n_nets = 0, nt = 0, user_K = 0, user_block = 0;
+    int min_cl = 1;              // smallest cluster for networks of at least 2 * min_cl neurons (autotuned)
     bool force_synapse_gates = false;
     std::vector<int> net_off, n1, n2;
     std::vector<int> tcnt;       // [N][nt] synapses of each type per row
@@ -394,12 +395,20 @@ int plan_network(const PlanInput &in, int b, const SmemCaps &caps, psst::NetPlan
     const int n0 = in.net_off[b], N = in.net_off[b + 1] - n0, nt = in.nt;
     const bool has2 = in.flags[b] & psst::NET_HAS2, pair = in.flags[b] & psst::NET_PAIR;
     const std::vector<int> &n1 = in.n1, &n2 = in.n2;
+    const int *tc = pair ? in.tcnt.data() + (size_t)n0 * nt : nullptr;
+    // a network spread over a larger cluster than it needs keeps the work-item
+    // size of one CTA, so the summation order (and every result) is the same
+    int user_K = in.user_K;
+    if (in.min_cl > 1 && N >= 2 * in.min_cl && user_K == 0) {
+        std::vector<Share> sh1;
+        make_shares(n1.data() + n0, n2.data() + n0, tc, nt, N, 1, 0, sh1, &user_K);
+    }
     for (int cl = 1; cl <= PSST_MAX_CL; cl *= 2) {
         if (cl > 1 && N < 2 * cl) break;
+        if (cl < in.min_cl && N >= 2 * in.min_cl) continue;  // spread over a larger cluster
         std::vector<Share> sh;
         int K = 1;
-        make_shares(n1.data() + n0, n2.data() + n0, pair ? in.tcnt.data() + (size_t)n0 * nt : nullptr, nt, N, cl,
-                    in.user_K, sh, &K);
+        make_shares(n1.data() + n0, n2.data() + n0, tc, nt, N, cl, user_K, sh, &K);
         long long worst = 0;
         const int used = in.pair_off[b + 1] - in.pair_off[b];
         for (int q = 0; q < cl; ++q) worst = std::max(worst, cta_share_bytes(N, nt, used, has2, pair, sh[q], K));
@@ -1053,6 +1062,38 @@ int psst_autotune(psst_net *h, int64_t trial_steps, void *stream) {
     // the record ring may be written by trial steps: trials run with recording off
     const int stride = h->v.rec_stride;
     h->v.rec_stride = 0;
+    // few CTAs for the GPU: try spreading each network over a cluster of 2 or 4
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess && 2LL * h->grid <= sms && !h->classes.empty()) {
+        const int n = (int)std::min<long long>(trial_steps, 1 << 20);
+        float best = 1e30f;
+        int best_cl = h->pin.min_cl;
+        for (int mc = 1; mc <= PSST_MAX_CL && e == cudaSuccess; mc *= 2) {
+            h->pin.min_cl = mc;
+            if (setup_cta(h, h->caps, &e) != PSST_OK) {
+                e = cudaSuccess;
+                continue;
+            }
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // warm-up, then timed
+                e = cudaMemcpyAsync(h->v.state, h->tune_buf, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
+                if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
+                if (e == cudaSuccess && launch_steps(h, 0, n, st) != PSST_OK) e = cudaErrorUnknown;
+                if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+            }
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                best_cl = mc;
+            }
+        }
+        h->pin.min_cl = best_cl;
+        if (e == cudaSuccess && setup_cta(h, h->caps, &e) != PSST_OK && e == cudaSuccess) e = cudaErrorUnknown;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->v.state, h->tune_buf, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    }
     for (size_t ci = 0; e == cudaSuccess && ci < h->classes.size(); ++ci) {
         psst::ClassLaunch &c = h->classes[ci];
         // the class's CTAs per SM are fixed by its shared memory and its

@@ -301,16 +301,40 @@ def test_graph_replay_bitwise_equal_to_direct_launches():
         np.testing.assert_array_equal(a.read_record(), b.read_record())
 
 
-def test_autotune_keeps_results_bitwise():
+@pytest.mark.parametrize("item_chunks", [2, 0])
+def test_autotune_keeps_results_bitwise(item_chunks):
+    # 24 networks need few SMs, so the tuner also tries larger clusters
     spec = ng.batched(n_nets=24, base_seed=700, n_min=20, n_max=300)
     y0 = oracle.rest_state(spec).astype(np.float32)
-    with _net(spec, init_state=y0, item_chunks=2) as a, _net(spec, init_state=y0, item_chunks=2) as b:
+    with _net(spec, init_state=y0, item_chunks=item_chunks) as a, \
+            _net(spec, init_state=y0, item_chunks=item_chunks) as b:
         b.autotune(50)
         np.testing.assert_array_equal(b.get_state_numpy(), y0)  # state restored
         a.integrate(200)
         b.integrate(200)
         a.status(), b.status()
         np.testing.assert_array_equal(a.get_state_numpy(), b.get_state_numpy())
+
+
+def test_forced_cluster_sizes_agree_bitwise():
+    # the antennal lobe alone on 1, 2 and 4 CTAs (the tuner's choices)
+    from paper_1906_03958_gb300 import psst
+    spec = ng.antennal_lobe(seed=91)
+    y0 = oracle.rest_state(spec).astype(np.float32)
+    with _net(spec, init_state=y0, rec_stride=10, rec_capacity=50) as net:
+        net.set_step(9800)
+        net.integrate(400)
+        net.status()
+        want = net.get_state_numpy(), net.read_record()
+    with _net(spec, init_state=y0, rec_stride=10, rec_capacity=50) as net:
+        net.autotune(100)
+        info = net.info()
+        net.set_step(9800)
+        net.integrate(400)
+        net.status()
+        np.testing.assert_array_equal(net.get_state_numpy(), want[0])
+        np.testing.assert_array_equal(net.read_record(), want[1])
+    assert info["n_single_cta_nets"] + info["n_cluster_nets"] == 1
 
 
 def test_pair_gates_agree_with_per_synapse_gates():
