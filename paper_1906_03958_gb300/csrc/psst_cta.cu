@@ -99,8 +99,9 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
         if (u < nown) {
             const int i = u;
             const float V = vcur[r_lo + i];
+            const VPre pre = neuron_v_pre<ST>(i, nown, V, ysc, y0, acc, prm, iext[i]);
             const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
-            const float vn = neuron_v<ST>(i, nown, V, ysc, y0, acc, prm, iext[i], isyn, dt);
+            const float vn = neuron_v_post<ST>(i, pre, isyn, y0, acc, dt);
             vnxt[r_lo + i] = vn;
             if (CL > 1) {
 #pragma unroll

@@ -124,8 +124,9 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
         if (u < N) {
             const int i = u;
             const float V = vcur[i];
+            const VPre pre = neuron_v_pre<ST>(i, N, V, ysc, y0, acc, prm, iext[i]);
             const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
-            const float vn = neuron_v<ST>(i, N, V, ysc, y0, acc, prm, iext[i], isyn, dt);
+            const float vn = neuron_v_post<ST>(i, pre, isyn, y0, acc, dt);
             vnxt[i] = vn;
             if (LAST && rec_slot >= 0) v.rec[rec_slot * v.N + lo + i] = vn;
         } else if (u < 2 * N) {

@@ -501,15 +501,22 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, float dt, 
 // [4][n] (V, m, h, n); the stage gates are double-buffered by stage parity,
 // ysc = [3][n] of this stage (read by both halves), ysn = [3][n] of the next.
 
-// Potential: returns the next stage's V, or after the step's last stage (ST 3,
-// or 4 for Euler) the new step-start V.
+// Potential, in two parts so that everything independent of the synaptic
+// current (the ionic currents, the loads of the RK4 sums) is issued before
+// the row's item partials are summed: neuron_v_pre, then neuron_v_post,
+// which returns the next stage's V, or after the step's last stage (ST 3, or
+// 4 for Euler) the new step-start V.
+struct VPre {
+    float ie;    // I_ext - I_ion
+    float invC;  // 1 / C
+    float y0;    // step-start V
+    float acc;   // RK4 sum of V's stage slopes so far
+};
+
 template <int ST>
-__device__ __forceinline__ float neuron_v(int i, int n, float V, const float *ysc, float *y0, float *acc,
-                                          const float *prm, float iext, float isyn, float dt) {
-    constexpr bool FIRST = ST == 0 || ST == 4, LAST = ST >= 3;
-    constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
-    const float cnext = (ST == 2) ? dt : 0.5f * dt;
-    const float dt6 = ST == 4 ? dt : dt * (1.0f / 6.0f);  // weight of the k-sum at the step's end
+__device__ __forceinline__ VPre neuron_v_pre(int i, int n, float V, const float *ysc, const float *y0,
+                                             const float *acc, const float *prm, float iext) {
+    constexpr bool FIRST = ST == 0 || ST == 4;
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
     // explicit roundings (no contraction left to the compiler), so that every
     // kernel evaluates the same operations in whatever context it is inlined
@@ -519,15 +526,35 @@ __device__ __forceinline__ float neuron_v(int i, int n, float V, const float *ys
     iion = fmaf(__fmul_rn(prm[NP_GK * n + i], n4), __fsub_rn(V, prm[NP_EK * n + i]), iion);
     iion = fmaf(prm[NP_GL * n + i], __fsub_rn(V, prm[NP_EL * n + i]), iion);
     iion = fmaf(prm[NP_GKL * n + i], __fsub_rn(V, prm[NP_EKL * n + i]), iion);
-    const float d = __fmul_rn(__fsub_rn(__fsub_rn(iext, iion), isyn), prm[NP_C * n + i]);  // row 0: 1/C
-    const float ac = FIRST ? d : fmaf(WGT, d, acc[i]);
+    VPre r;
+    r.ie = __fsub_rn(iext, iion);
+    r.invC = prm[NP_C * n + i];  // prm row 0 holds 1/C
+    r.y0 = y0[i];
+    r.acc = FIRST ? 0.0f : acc[i];
+    return r;
+}
+
+template <int ST>
+__device__ __forceinline__ float neuron_v_post(int i, const VPre &p, float isyn, float *y0, float *acc, float dt) {
+    constexpr bool FIRST = ST == 0 || ST == 4, LAST = ST >= 3;
+    constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
+    const float cnext = (ST == 2) ? dt : 0.5f * dt;
+    const float dt6 = ST == 4 ? dt : dt * (1.0f / 6.0f);  // weight of the k-sum at the step's end
+    const float d = __fmul_rn(__fsub_rn(p.ie, isyn), p.invC);
+    const float ac = FIRST ? d : fmaf(WGT, d, p.acc);
     if (!LAST) {
         acc[i] = ac;
-        return fmaf(cnext, d, y0[i]);
+        return fmaf(cnext, d, p.y0);
     }
-    const float yn = fmaf(dt6, ac, y0[i]);
+    const float yn = fmaf(dt6, ac, p.y0);
     y0[i] = yn;
     return yn;
+}
+
+template <int ST>
+__device__ __forceinline__ float neuron_v(int i, int n, float V, const float *ysc, float *y0, float *acc,
+                                          const float *prm, float iext, float isyn, float dt) {
+    return neuron_v_post<ST>(i, neuron_v_pre<ST>(i, n, V, ysc, y0, acc, prm, iext), isyn, y0, acc, dt);
 }
 
 // Gates: writes the next stage's m, h, n, or after the last stage the new
