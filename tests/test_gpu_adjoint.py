@@ -194,3 +194,52 @@ def test_autograd_with_recorded_checkpoints():
             out.append((w.grad.cpu().numpy(), p.grad.cpu().numpy()))
     assert _rel(out[1][0], out[0][0]) <= 1e-5
     assert _rel(out[1][1], out[0][1]) <= 1e-5
+
+
+def _with_duplicate_synapses(spec, seed=9):
+    """The same network with a second synapse (own weight) for a random
+    tenth of the existing ones: rows then hold two synapses of one
+    (presynaptic neuron, type) pair."""
+    rng = np.random.default_rng(seed)
+    N = spec.n_neurons
+    post = np.repeat(np.arange(N), np.diff(spec.row_ptr))
+    dup = rng.random(spec.n_synapses) < 0.1
+    post2 = np.concatenate([post, post[dup]])
+    pre2 = np.concatenate([spec.pre, spec.pre[dup]])
+    w2 = np.concatenate([spec.weight, rng.uniform(0.0, 0.2, int(dup.sum())).astype(np.float32)])
+    t2 = np.concatenate([spec.syn_type, spec.syn_type[dup]])
+    order = np.lexsort((t2, pre2, post2))
+    row_ptr = np.zeros(N + 1, np.int64)
+    np.add.at(row_ptr, post2 + 1, 1)
+    return ng.NetworkSpec(
+        net_neuron_off=spec.net_neuron_off, neuron_type=spec.neuron_type, neuron_params=spec.neuron_params,
+        row_ptr=np.cumsum(row_ptr), pre=pre2[order].astype(np.int32), weight=w2[order].astype(np.float32),
+        syn_type=t2[order].astype(np.int32), syn_params=spec.syn_params, i_const=spec.i_const,
+        pulse_amp=spec.pulse_amp, pulse_on=spec.pulse_on, pulse_off=spec.pulse_off, dt=spec.dt,
+        name=spec.name + "+duplicates")
+
+
+def test_duplicate_synapses_forward_and_adjoint():
+    # two synapses of one pair in a row: the forward's per-pair gates and the
+    # adjoint's column sums (atomic path) against the oracle
+    from paper_1906_03958_gb300 import psst
+    from tests.helpers import step_error
+    _, base = _spec(seed=11)
+    spec = _with_duplicate_synapses(base)
+    N, S = spec.n_neurons, spec.n_synapses
+    assert S > base.n_synapses
+    y32 = oracle.integrate(spec, oracle.rest_state(spec), 30)[0].astype(np.float32)
+    y64, _ = oracle.integrate(spec, y32.astype(np.float64), 1, step0=30)
+    with psst.Network(spec, init_state=y32) as net:
+        assert net.info()["n_pair_gate_nets"] == 1
+        net.set_step(30)
+        net.integrate(1)
+        net.status()
+        assert step_error(net.get_state_numpy(), y64, N, S) <= 1e-5
+    rng = np.random.default_rng(1)
+    nsteps, stride = 300, 10
+    g = rng.standard_normal((nsteps // stride, N))
+    gy64, gw64, gp64 = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, ckpt=100)
+    gw, gp, gy = _gpu_adjoint(spec, nsteps, g, stride)
+    assert _rel(gw, gw64) <= GRAD_TOL
+    assert _rel(gp, gp64) <= GRAD_TOL
