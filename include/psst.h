@@ -139,12 +139,24 @@ typedef struct {
 
 typedef struct psst_net psst_net;
 
+/* Optional device-memory provider for a handle (for example a framework's
+   caching allocator): alloc(bytes, ctx) returns device memory of the
+   handle's device, aligned to at least 256 bytes, or NULL; free(ptr, ctx)
+   gives it back.  Both are called on the thread that calls into the
+   library; the struct is copied at psst_create_network. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} psst_allocator;
+
 /* Validate the description, build the device layout and copy everything to
    the device (synchronous).  Reads the host arrays of *d only during the
    call.  Allocates device memory owned by the handle until
-   psst_destroy_network.  Errors: INVALID_ARG (with a message naming the
-   offending field/index), OOM, CUDA, UNSUPPORTED. */
-int psst_create_network(const psst_network_desc *d, psst_net **out);
+   psst_destroy_network, through *a (NULL: cudaMalloc / cudaFree).  Errors:
+   INVALID_ARG (with a message naming the offending field/index, or an
+   allocator with a NULL function), OOM, CUDA, UNSUPPORTED. */
+int psst_create_network(const psst_network_desc *d, const psst_allocator *a, psst_net **out);
 
 /* Advance every network by n_steps RK4 steps from the current state
    (Sec. "Circumventing memory constraints", item 2: successive calls

@@ -123,10 +123,19 @@ struct psst_net {
         graph_nsteps = 0;
     }
 
+    psst_allocator user_alloc{};  // the caller's device-memory provider, or all NULL (cudaMalloc)
+
     template <class T>
     cudaError_t alloc(T **p, size_t count) {
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        cudaError_t e = cudaSuccess;
+        if (user_alloc.alloc) {
+            q = user_alloc.alloc(bytes, user_alloc.ctx);
+            if (!q) e = cudaErrorMemoryAllocation;
+        } else {
+            e = cudaMalloc(&q, bytes);
+        }
         if (e == cudaSuccess) allocs.push_back(q);
         *p = (T *)q;
         return e;
@@ -163,7 +172,10 @@ struct psst_net {
     void release() {
         drop_graph();
         drop_streams();
-        for (void *p : allocs) cudaFree(p);
+        for (void *p : allocs) {
+            if (user_alloc.free) user_alloc.free(p, user_alloc.ctx);
+            else cudaFree(p);
+        }
         allocs.clear();
     }
 };
@@ -686,11 +698,12 @@ const char *psst_error_string(int code) {
 
 const char *psst_last_error(void) { return g_last_error.c_str(); }
 
-int psst_create_network(const psst_network_desc *d, psst_net **out) {
+int psst_create_network(const psst_network_desc *d, const psst_allocator *a, psst_net **out) {
     if (!out) return fail(PSST_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     int rc = validate(d);
     if (rc) return rc;
+    if (a && (!a->alloc || !a->free)) return fail(PSST_ERR_INVALID_ARG, "allocator: alloc and free must both be set");
     int dev = d->device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(PSST_ERR_CUDA, "no CUDA device");
     DeviceGuard guard(dev);
@@ -762,6 +775,7 @@ int psst_create_network(const psst_network_desc *d, psst_net **out) {
         return fail(PSST_ERR_UNSUPPORTED, "grid mode integrates a single network (got %d)", n_nets);
 
     psst_net *h = new psst_net();
+    if (a) h->user_alloc = *a;
     h->device = dev;
     h->mode = mode;
     h->pin = pin;

@@ -95,7 +95,7 @@ def load(build_if_missing: bool = False):
             _build.build()
         lib = C.CDLL(path)
         P, I32, I64, SZ = C.c_void_p, C.c_int, C.c_int64, C.c_size_t
-        lib.psst_create_network.argtypes = [C.POINTER(NetworkDesc), C.POINTER(P)]
+        lib.psst_create_network.argtypes = [C.POINTER(NetworkDesc), C.POINTER(Allocator), C.POINTER(P)]
         lib.psst_integrate.argtypes = [P, I64, P]
         lib.psst_status.argtypes = [P, P]
         lib.psst_get_state.argtypes = [P, P, SZ, I32, P]
@@ -148,12 +148,48 @@ def _arr(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    """psst_allocator: device-memory provider of a handle."""
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", C.c_void_p)]
+
+
+class TorchAllocator:
+    """Serves a handle's device memory from PyTorch's caching allocator
+    (uint8 tensors kept alive until the library frees them)."""
+
+    def __init__(self, device: int):
+        self.device = device
+        self.blocks = {}
+
+        def _alloc(nbytes, ctx):
+            import torch
+            try:
+                t = torch.empty(int(nbytes), dtype=torch.uint8, device=f"cuda:{self.device}")
+            except RuntimeError:
+                return None
+            p = t.data_ptr()
+            self.blocks[p] = t
+            return p
+
+        def _free(ptr, ctx):
+            self.blocks.pop(ptr, None)
+
+        self._alloc, self._free = _ALLOC_FN(_alloc), _FREE_FN(_free)
+        self.struct = Allocator(self._alloc, self._free, None)
+
+
 class Network:
-    """A batch of networks resident on one GPU (``psst_create_network``)."""
+    """A batch of networks resident on one GPU (``psst_create_network``).
+    ``allocator="torch"`` takes the handle's device memory from PyTorch's
+    caching allocator instead of cudaMalloc."""
 
     def __init__(self, spec, init_state=None, rec_stride: int = 0, rec_capacity: int = 0,
                  mode: int = MODE_AUTO, block_threads: int = 0, item_chunks: int = 0,
-                 device: int | None = None, gate_mode: int = 0, method: int = 0):
+                 device: int | None = None, gate_mode: int = 0, method: int = 0, allocator=None):
         lib = load()
         keep = dict(
             off=_arr(spec.net_neuron_off, np.int32), nt=_arr(spec.neuron_type, np.int32),
@@ -179,8 +215,12 @@ class Network:
             rec_stride=int(rec_stride), rec_capacity=int(rec_capacity), mode=int(mode),
             block_threads=int(block_threads), item_chunks=int(item_chunks), device=int(device),
             gate_mode=int(gate_mode), method=int(method))
+        self._allocator = TorchAllocator(device) if allocator == "torch" else allocator
+        if self._allocator is not None and not isinstance(self._allocator, TorchAllocator):
+            raise ValueError("allocator must be None or 'torch'")
         h = C.c_void_p()
-        _check(lib.psst_create_network(C.byref(d), C.byref(h)))
+        _check(lib.psst_create_network(C.byref(d), C.byref(self._allocator.struct) if self._allocator else None,
+                                       C.byref(h)))
         self._h = h
         self.device = device
         self.N = spec.n_neurons

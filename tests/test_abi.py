@@ -89,7 +89,7 @@ def test_invalid_descriptor_rejected_on_host(lib, field, value, needle):
     spec = ng.plain20()
     d, keep = _desc(spec, **{field: value})
     h = C.c_void_p()
-    rc = lib.psst_create_network(C.byref(d), C.byref(h))
+    rc = lib.psst_create_network(C.byref(d), None, C.byref(h))
     assert rc == -1 and not h.value
     assert needle in lib.psst_last_error()
 
@@ -100,7 +100,7 @@ def test_out_of_range_presynaptic_index_rejected(lib):
     spec.pre[5] = 20  # outside the 20-neuron network
     d, keep = _desc(spec)
     h = C.c_void_p()
-    assert lib.psst_create_network(C.byref(d), C.byref(h)) == -1
+    assert lib.psst_create_network(C.byref(d), None, C.byref(h)) == -1
     assert b"pre[5]" in lib.psst_last_error()
 
 

@@ -378,3 +378,26 @@ def test_set_state_switches_gate_layout():
         b.integrate(200)
         a.status(), b.status()
         np.testing.assert_array_equal(a.get_state_numpy(), b.get_state_numpy())
+
+
+def test_torch_allocator_serves_the_handle():
+    # device memory from PyTorch's caching allocator through psst_allocator:
+    # same results, memory visible to torch while the handle lives
+    import torch
+    spec = ng.concat_specs([ng.antennal_lobe(seed=95), ng.antennal_lobe(seed=96, n_pn=30, n_ln=10)])
+    y0 = oracle.rest_state(spec).astype(np.float32)
+    before = torch.cuda.memory_allocated()
+    with _net(spec, init_state=y0, rec_stride=10, rec_capacity=50, allocator="torch") as a:
+        assert a._allocator.blocks and torch.cuda.memory_allocated() > before
+        a.set_step(9900)
+        a.integrate(300)
+        a.status()
+        got = a.get_state_numpy(), a.read_record()
+        alloc = a._allocator
+    assert not alloc.blocks  # every block handed back at destroy
+    with _net(spec, init_state=y0, rec_stride=10, rec_capacity=50) as b:
+        b.set_step(9900)
+        b.integrate(300)
+        b.status()
+        np.testing.assert_array_equal(got[0], b.get_state_numpy())
+        np.testing.assert_array_equal(got[1], b.read_record())
