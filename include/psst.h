@@ -163,6 +163,8 @@ int psst_create_network(const psst_network_desc *d, const psst_allocator *a, pss
    continue where the previous one stopped; results are bitwise independent
    of how the steps are split into calls).  Asynchronous on `stream`;
    device-side failures (NONFINITE, TIMEOUT) are reported by psst_status.
+   With the environment variable PSST_SYNC set (to anything but "0") the
+   call synchronises `stream` and returns what psst_status would.
    n_steps = 0 is a no-op.  Errors: INVALID_ARG (n_steps < 0), CUDA. */
 int psst_integrate(psst_net *h, int64_t n_steps, void *stream);
 

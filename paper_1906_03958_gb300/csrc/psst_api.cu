@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -1156,7 +1157,22 @@ int psst_autotune(psst_net *h, int64_t trial_steps, void *stream) {
     return e == cudaSuccess ? PSST_OK : cuda_fail(e, "psst_autotune");
 }
 
+// PSST_SYNC set to anything but "0": psst_integrate waits for its work and
+// reports device-side failures itself (debugging aid).
+static bool sync_requested() {
+    const char *s = std::getenv("PSST_SYNC");
+    return s && *s && std::strcmp(s, "0") != 0;
+}
+
+static int integrate_async(psst_net *h, int64_t n_steps, cudaStream_t st);
+
 int psst_integrate(psst_net *h, int64_t n_steps, void *stream) {
+    const int rc = integrate_async(h, n_steps, (cudaStream_t)stream);
+    if (rc || !h || !sync_requested()) return rc;
+    return psst_status(h, stream);
+}
+
+static int integrate_async(psst_net *h, int64_t n_steps, cudaStream_t stream) {
     if (!h) return fail(PSST_ERR_INVALID_ARG, "handle is NULL");
     if (n_steps < 0) return fail(PSST_ERR_INVALID_ARG, "n_steps must be >= 0");
     h->launches = 0;

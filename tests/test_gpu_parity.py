@@ -286,6 +286,25 @@ def test_nonfinite_state_is_reported():
         net.status()  # cleared after being read
 
 
+def test_psst_sync_reports_device_errors_from_integrate(monkeypatch):
+    # PSST_SYNC: psst_integrate waits and returns the device error itself
+    from paper_1906_03958_gb300 import psst
+    spec = ng.plain20()
+    with _net(spec) as net:
+        y = net.get_state_numpy()
+        y[3] = np.nan
+        net.set_state(y)
+        monkeypatch.setenv("PSST_SYNC", "1")
+        with pytest.raises(psst.PsstError) as ei:
+            net.integrate(5)
+        assert ei.value.code == -4
+        net.set_state(np.nan_to_num(y, nan=-65.0))
+        net.integrate(5)  # no error: returns 0 after synchronising
+        monkeypatch.setenv("PSST_SYNC", "0")
+        net.integrate(5)
+        net.status()
+
+
 def test_graph_replay_bitwise_equal_to_direct_launches():
     spec = ng.concat_specs([ng.antennal_lobe(seed=51), ng.antennal_lobe(seed=52, n_pn=30, n_ln=10)])
     y0 = oracle.rest_state(spec).astype(np.float32)
