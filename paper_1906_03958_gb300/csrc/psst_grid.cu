@@ -299,7 +299,11 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
             if (HAS2 && second_order(stab, code)) gs[k] = __ldcg(g.s0g + t);
         }
     } else {
-        store_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.syn_code, stab, GlobalCoef{g.c1, HAS2 ? g.c2 : nullptr});
+        // the last stage wrote the step's final maps into table 0 (RK4: four
+        // stages per step) or into the table of the step count's parity (Euler)
+        const size_t fin = v.method == PSST_METHOD_EULER ? (size_t)(nsteps & 1) : 0;
+        store_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.syn_code, stab,
+                          GlobalCoef{g.c1 + fin * M, HAS2 ? g.c2 + fin * M : nullptr});
     }
     bool bad = false;
     for (int i = tid; i < N; i += nthr) {

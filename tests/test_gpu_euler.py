@@ -22,10 +22,13 @@ def _euler_state(spec, n, step0):
     return oracle.integrate(spec, oracle.rest_state(spec), n, step0=step0, order=1)[0].astype(np.float32)
 
 
-@pytest.mark.parametrize("case", ["al_cta", "sparse_grid", "independent"])
-def test_euler_single_step_error(case):
+@pytest.mark.parametrize("case,gate_mode", [("al_cta", 0), ("al_cta", 1), ("al_cta_random_gates", 0),
+                                            ("sparse_grid", 0), ("sparse_grid", 1), ("independent", 0)])
+def test_euler_single_step_error(case, gate_mode):
+    # per-pair and per-synapse gate layouts (gate_mode 1, or a state whose
+    # pair gates differ), CTA and grid modes, independent neurons
     from paper_1906_03958_gb300 import psst
-    if case == "al_cta":
+    if case.startswith("al_cta"):
         spec, mode, step0 = ng.antennal_lobe(seed=81), psst.MODE_CTA, 9980
     elif case == "sparse_grid":
         spec, mode, step0 = ng.sparse_large(seed=82, n_e=1600, n_i=400), psst.MODE_GRID, 300
@@ -33,8 +36,14 @@ def test_euler_single_step_error(case):
         spec, mode, step0 = ng.independent(2000, seed=83, n_nets=2, rate_hz=200.0), psst.MODE_CTA, 1990
     N, S = spec.n_neurons, spec.n_synapses
     y32 = _euler_state(spec, 40, step0)
+    if case == "al_cta_random_gates":
+        rng = np.random.default_rng(7)
+        y32[4 * N:4 * N + S] = rng.uniform(0.0, 1.0, S).astype(np.float32)
+        y32[4 * N + S:] = rng.uniform(0.0, 1.0, S).astype(np.float32)
     y64, _ = oracle.integrate(spec, y32.astype(np.float64), 1, step0=step0 + 40, order=1)
-    with _net(spec, init_state=y32, mode=mode) as net:
+    with _net(spec, init_state=y32, mode=mode, gate_mode=gate_mode) as net:
+        if case == "al_cta_random_gates" or gate_mode == 1:
+            assert net.info()["n_pair_gate_nets"] == 0
         net.set_step(step0 + 40)
         net.integrate(1)
         net.status()
@@ -42,14 +51,19 @@ def test_euler_single_step_error(case):
     assert step_error(got, y64, N, S) <= STEP_TOL
 
 
-def test_euler_cta_equals_grid_and_chunked_and_graph_bitwise():
+@pytest.mark.parametrize("gate_mode", [0, 1])
+def test_euler_cta_equals_grid_and_chunked_and_graph_bitwise(gate_mode):
+    # odd and even step counts per call (the grid's final gate maps sit in the
+    # table of the step count's parity)
     from paper_1906_03958_gb300 import psst
     spec = ng.antennal_lobe(seed=84)
     y0 = oracle.rest_state(spec).astype(np.float32)
     out = []
     for mode, chunks, graph in ((psst.MODE_CTA, [301], False), (psst.MODE_GRID, [301], False),
+                                (psst.MODE_GRID, [100, 101, 100], False),
                                 (psst.MODE_CTA, [100, 100, 101], False), (psst.MODE_CTA, [43] * 7, True)):
-        with _net(spec, init_state=y0, mode=mode, item_chunks=2, rec_stride=5, rec_capacity=100) as net:
+        with _net(spec, init_state=y0, mode=mode, item_chunks=2, rec_stride=5, rec_capacity=100,
+                  gate_mode=gate_mode) as net:
             net.set_graph_mode(graph)
             net.set_step(9900)
             for c in chunks:
