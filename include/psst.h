@@ -117,6 +117,10 @@ typedef struct {
                                       its synapses' gates are equal (bitwise-identical results,
                                       less work), else one per synapse; 1: always one per synapse */
     int32_t method;                /* PSST_METHOD_RK4 (0) or PSST_METHOD_EULER; psst_adjoint needs RK4 */
+    int32_t min_cluster;           /* CTA mode: spread every network of at least 2 x min_cluster neurons
+                                      over a cluster of at least min_cluster CTAs (1, 2 or 4; same
+                                      results, shorter steps when SMs are idle); 0 = chosen by
+                                      psst_autotune (default 1) */
 } psst_network_desc;
 
 typedef struct {

@@ -61,7 +61,8 @@ struct SmemCaps {
 // gate uniformity of a network changes (psst_set_state).
 struct PlanInput {
     int n_nets = 0, nt = 0, user_K = 0, user_block = 0;
-    int min_cl = 1;              // smallest cluster for networks of at least 2 * min_cl neurons (autotuned)
+    int min_cl = 1;              // smallest cluster for networks of at least 2 * min_cl neurons
+    bool tune_cl = true;         // psst_autotune may choose min_cl
     bool force_synapse_gates = false;
     std::vector<int> net_off, n1, n2;
     std::vector<int> tcnt;       // [N][nt] synapses of each type per row
@@ -276,6 +277,8 @@ int validate(const psst_network_desc *d) {
     }
     if (d->mode < PSST_MODE_AUTO || d->mode > PSST_MODE_GRID) return fail(PSST_ERR_INVALID_ARG, "unknown mode");
     if (d->gate_mode < 0 || d->gate_mode > 1) return fail(PSST_ERR_INVALID_ARG, "gate_mode must be 0 or 1");
+    if (d->min_cluster != 0 && d->min_cluster != 1 && d->min_cluster != 2 && d->min_cluster != 4)
+        return fail(PSST_ERR_INVALID_ARG, "min_cluster must be 0, 1, 2 or 4");
     if (d->method != PSST_METHOD_RK4 && d->method != PSST_METHOD_EULER)
         return fail(PSST_ERR_INVALID_ARG, "method must be PSST_METHOD_RK4 (0) or PSST_METHOD_EULER (1)");
     return PSST_OK;
@@ -721,6 +724,8 @@ int psst_create_network(const psst_network_desc *d, const psst_allocator *a, pss
     pin.user_K = d->item_chunks;
     pin.user_block = d->block_threads;
     pin.force_synapse_gates = d->gate_mode == 1;
+    pin.min_cl = d->min_cluster > 0 ? d->min_cluster : 1;
+    pin.tune_cl = d->min_cluster == 0;
     pin.net_off.assign(d->net_neuron_off, d->net_neuron_off + n_nets + 1);
     pin.net_syn.resize(n_nets);
     for (int b = 0; b < n_nets; ++b)
@@ -1080,7 +1085,7 @@ int psst_autotune(psst_net *h, int64_t trial_steps, void *stream) {
     // few CTAs for the GPU: try spreading each network over a cluster of 2 or 4
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    if (e == cudaSuccess && 2LL * h->grid <= sms && !h->classes.empty()) {
+    if (e == cudaSuccess && h->pin.tune_cl && 2LL * h->grid <= sms && !h->classes.empty()) {
         const int n = (int)std::min<long long>(trial_steps, 1 << 20);
         float best = 1e30f;
         int best_cl = h->pin.min_cl;

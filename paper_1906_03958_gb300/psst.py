@@ -49,7 +49,7 @@ class NetworkDesc(C.Structure):
                 ("noise_amp", C.c_float), ("dt", C.c_float), ("init_state", C.c_void_p),
                 ("rec_stride", C.c_int32), ("rec_capacity", C.c_int64), ("mode", C.c_int32),
                 ("block_threads", C.c_int32), ("item_chunks", C.c_int32), ("device", C.c_int32),
-                ("gate_mode", C.c_int32), ("method", C.c_int32)]
+                ("gate_mode", C.c_int32), ("method", C.c_int32), ("min_cluster", C.c_int32)]
 
 
 class DeviceNetwork(C.Structure):
@@ -189,7 +189,8 @@ class Network:
 
     def __init__(self, spec, init_state=None, rec_stride: int = 0, rec_capacity: int = 0,
                  mode: int = MODE_AUTO, block_threads: int = 0, item_chunks: int = 0,
-                 device: int | None = None, gate_mode: int = 0, method: int = 0, allocator=None):
+                 device: int | None = None, gate_mode: int = 0, method: int = 0, allocator=None,
+                 min_cluster: int = 0):
         lib = load()
         keep = dict(
             off=_arr(spec.net_neuron_off, np.int32), nt=_arr(spec.neuron_type, np.int32),
@@ -214,7 +215,7 @@ class Network:
             noise_amp=float(spec.noise_amp), dt=float(spec.dt), init_state=ptr("init"),
             rec_stride=int(rec_stride), rec_capacity=int(rec_capacity), mode=int(mode),
             block_threads=int(block_threads), item_chunks=int(item_chunks), device=int(device),
-            gate_mode=int(gate_mode), method=int(method))
+            gate_mode=int(gate_mode), method=int(method), min_cluster=int(min_cluster))
         self._allocator = TorchAllocator(device) if allocator == "torch" else allocator
         if self._allocator is not None and not isinstance(self._allocator, TorchAllocator):
             raise ValueError("allocator must be None or 'torch'")

@@ -84,6 +84,7 @@ def _desc(spec, **kw):
     ("gate_mode", 2, b"gate_mode"),
     ("method", 2, b"method"),
     ("mode", 3, b"mode"),
+    ("min_cluster", 3, b"min_cluster"),
 ])
 def test_invalid_descriptor_rejected_on_host(lib, field, value, needle):
     spec = ng.plain20()

@@ -335,25 +335,27 @@ def test_autotune_keeps_results_bitwise(item_chunks):
         np.testing.assert_array_equal(a.get_state_numpy(), b.get_state_numpy())
 
 
-def test_forced_cluster_sizes_agree_bitwise():
-    # the antennal lobe alone on 1, 2 and 4 CTAs (the tuner's choices)
-    from paper_1906_03958_gb300 import psst
-    spec = ng.antennal_lobe(seed=91)
+@pytest.mark.parametrize("gate_mode", [0, 1])
+def test_forced_cluster_sizes_agree_bitwise(gate_mode):
+    # the antennal lobe and a small batch on clusters of at least 1, 2 and 4
+    # CTAs, and as the tuner chooses: the same results bit for bit
+    spec = ng.concat_specs([ng.antennal_lobe(seed=91), ng.antennal_lobe(seed=92, n_pn=45, n_ln=15)])
     y0 = oracle.rest_state(spec).astype(np.float32)
-    with _net(spec, init_state=y0, rec_stride=10, rec_capacity=50) as net:
-        net.set_step(9800)
-        net.integrate(400)
-        net.status()
-        want = net.get_state_numpy(), net.read_record()
-    with _net(spec, init_state=y0, rec_stride=10, rec_capacity=50) as net:
-        net.autotune(100)
-        info = net.info()
-        net.set_step(9800)
-        net.integrate(400)
-        net.status()
-        np.testing.assert_array_equal(net.get_state_numpy(), want[0])
-        np.testing.assert_array_equal(net.read_record(), want[1])
-    assert info["n_single_cta_nets"] + info["n_cluster_nets"] == 1
+    out = []
+    for mc, tune in ((1, False), (2, False), (4, False), (0, True)):
+        with _net(spec, init_state=y0, rec_stride=10, rec_capacity=50, min_cluster=mc, gate_mode=gate_mode) as net:
+            if tune:
+                net.autotune(100)
+            info = net.info()
+            if mc > 1:
+                assert info["n_cluster_nets"] == 2 and info["n_single_cta_nets"] == 0
+            net.set_step(9800)
+            net.integrate(400)
+            net.status()
+            out.append((net.get_state_numpy(), net.read_record()))
+    for y, rec in out[1:]:
+        np.testing.assert_array_equal(y, out[0][0])
+        np.testing.assert_array_equal(rec, out[0][1])
 
 
 def test_pair_gates_agree_with_per_synapse_gates():
