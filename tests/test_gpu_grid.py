@@ -44,16 +44,18 @@ def test_grid_single_step_error():
         assert step_error(got, y64, N, S) <= STEP_TOL
 
 
-def test_grid_equals_cta_mode_bitwise():
+@pytest.mark.parametrize("gate_mode", [0, 1])
+def test_grid_equals_cta_mode_bitwise(gate_mode):
     # dense-in-one-CTA and spread-over-the-GPU evaluate the same per-row sums
-    # in the same order, so the two representations agree exactly
+    # in the same order, so the two representations agree exactly (both gate
+    # layouts, with second-order GABA_B gates)
     from paper_1906_03958_gb300 import psst
     spec = ng.antennal_lobe(seed=41)
     y0 = oracle.rest_state(spec).astype(np.float32)
     out = []
     for mode in (psst.MODE_CTA, psst.MODE_GRID):
         with _net(spec, init_state=y0, mode=mode, block_threads=256, item_chunks=2,
-                  rec_stride=5, rec_capacity=100) as net:
+                  rec_stride=5, rec_capacity=100, gate_mode=gate_mode) as net:
             net.set_step(9950)
             net.integrate(300)
             net.status()
