@@ -71,10 +71,10 @@ def lib():
             _lib.orc_steady_gates.argtypes = [C.c_double, P]
             _lib.orc_vjp.argtypes = [C.POINTER(_Net), P, P, P, P, P]
             _lib.orc_linear_adjoint.restype = C.c_int
-            _lib.orc_linear_adjoint.argtypes = [C.c_int64, P, P, C.c_double, C.c_int64, P]
+            _lib.orc_linear_adjoint.argtypes = [C.c_int64, P, P, C.c_double, C.c_int64, P, C.c_int]
             _lib.orc_adjoint.restype = C.c_int
             _lib.orc_adjoint.argtypes = [C.POINTER(_Net), P, C.c_int64, C.c_int64, C.c_int64, P, P, P, P,
-                                         C.c_int64]
+                                         C.c_int64, C.c_int]
             _lib.orc_rates_deriv.argtypes = [C.c_double, P]
             _lib.orc_transmitter.restype = C.c_double
             _lib.orc_transmitter.argtypes = [C.c_double, C.c_double, C.c_double]
@@ -184,18 +184,19 @@ def vjp(spec, y, v, step: int = 0):
     return u, gw, gnp.reshape(-1, 9)
 
 
-def linear_adjoint(A, y0, h: float, nsteps: int, lam_T) -> np.ndarray:
+def linear_adjoint(A, y0, h: float, nsteps: int, lam_T, order: int = 4) -> np.ndarray:
     A = np.ascontiguousarray(A, np.float64)
     y0 = np.ascontiguousarray(y0, np.float64)
     lam = np.array(lam_T, np.float64, copy=True)
-    if lib().orc_linear_adjoint(len(y0), _ptr(A), _ptr(y0), float(h), int(nsteps), _ptr(lam)):
+    if lib().orc_linear_adjoint(len(y0), _ptr(A), _ptr(y0), float(h), int(nsteps), _ptr(lam), int(order)):
         raise MemoryError("oracle linear adjoint")
     return lam
 
 
-def adjoint(spec, y0, nsteps: int, dLdV, rec_stride: int, step0: int = 0, ckpt: int = 100):
+def adjoint(spec, y0, nsteps: int, dLdV, rec_stride: int, step0: int = 0, ckpt: int = 100, order: int = 4):
     """Gradient of L = sum_f sum_i dLdV[f, i] V_i(frame f) over the RK4
-    trajectory; returns (dL/dy0, dL/dw, dL/dnparams[n_types, 9])."""
+    (order 4) or Euler (order 1) trajectory; returns (dL/dy0, dL/dw,
+    dL/dnparams[n_types, 9])."""
     net = as_net(spec)
     y0 = np.ascontiguousarray(y0, np.float64)
     dLdV = np.ascontiguousarray(dLdV, np.float64)
@@ -203,7 +204,7 @@ def adjoint(spec, y0, nsteps: int, dLdV, rec_stride: int, step0: int = 0, ckpt: 
     gw = np.zeros(net.S, np.float64)
     gnp = np.zeros(net.nparams.size, np.float64)
     if lib().orc_adjoint(C.byref(net.c), _ptr(y0), int(step0), int(nsteps), int(rec_stride), _ptr(dLdV),
-                         _ptr(gy), _ptr(gw), _ptr(gnp), int(ckpt)):
+                         _ptr(gy), _ptr(gw), _ptr(gnp), int(ckpt), int(order)):
         raise MemoryError("oracle adjoint")
     return gy, gw, gnp.reshape(-1, 9)
 

@@ -437,6 +437,25 @@ static void rk4_adjoint_step(int64_t d, double hstep, rhs_fn f, vjp_fn g, void *
     for (int64_t i = 0; i < d; ++i) lam[i] += Ysum[i] + Yb[i];
 }
 
+/* Reverse of one forward-Euler step, Eq. (euler): y_{n+1} = y_n + h f(y_n),
+   so lam_n = lam + J(y_n)^T (h lam), with the parameter terms
+   (df/dtheta)^T (h lam) added by the vjp callback. */
+static void euler_adjoint_step(int64_t d, double hstep, vjp_fn g, void *ctx, const double *y, double *lam,
+                               double *work)
+{
+    double *kb = work, *Yb = work + d;
+    for (int64_t i = 0; i < d; ++i) kb[i] = hstep * lam[i];
+    g(ctx, y, kb, Yb);
+    for (int64_t i = 0; i < d; ++i) lam[i] += Yb[i];
+}
+
+static void adjoint_step(int order, int64_t d, double hstep, rhs_fn f, vjp_fn g, void *ctx, const double *y,
+                         double *lam, double *work)
+{
+    if (order == 1) euler_adjoint_step(d, hstep, g, ctx, y, lam, work);
+    else rk4_adjoint_step(d, hstep, f, g, ctx, y, lam, work);
+}
+
 static void lin_vjp(void *c, const double *y, const double *v, double *u)
 {
     const lin_ctx *L = (const lin_ctx *)c;
@@ -448,9 +467,11 @@ static void lin_vjp(void *c, const double *y, const double *v, double *u)
     }
 }
 
-/* Adjoint of nsteps RK4 steps of dy/dt = A y: lam (adjoint of y at the end)
-   is carried back to the adjoint of the initial state. */
-int orc_linear_adjoint(int64_t d, const double *A, const double *y0, double h, int64_t nsteps, double *lam)
+/* Adjoint of nsteps RK4 (order 4) or Euler (order 1) steps of dy/dt = A y:
+   lam (adjoint of y at the end) is carried back to the adjoint of the
+   initial state. */
+int orc_linear_adjoint(int64_t d, const double *A, const double *y0, double h, int64_t nsteps, double *lam,
+                       int order)
 {
     double *traj = (double *)malloc(sizeof(double) * (size_t)d * (size_t)(nsteps + 1));
     double *work = (double *)malloc(sizeof(double) * 8 * (size_t)d);
@@ -459,10 +480,10 @@ int orc_linear_adjoint(int64_t d, const double *A, const double *y0, double h, i
     memcpy(traj, y0, sizeof(double) * (size_t)d);
     for (int64_t k = 0; k < nsteps; ++k) {
         memcpy(traj + (k + 1) * d, traj + k * d, sizeof(double) * (size_t)d);
-        rk4_step(d, h, lin_rhs, &c, traj + (k + 1) * d, work);
+        take_step(order, d, h, lin_rhs, &c, traj + (k + 1) * d, work);
     }
     for (int64_t k = nsteps - 1; k >= 0; --k)
-        rk4_adjoint_step(d, h, lin_rhs, lin_vjp, &c, traj + k * d, lam, work);
+        adjoint_step(order, d, h, lin_rhs, lin_vjp, &c, traj + k * d, lam, work);
     free(traj);
     free(work);
     return 0;
@@ -487,10 +508,11 @@ static void net_vjp(void *c, const double *y, const double *v, double *u)
    index step0; frame f is the state after global step k with
    k % rec_stride == 0, in order).  Outputs the adjoint of y0 (grad_y0[dim]),
    dL/dw (grad_w[S]) and dL/d(neuron-type parameters) (grad_np, row per
-   type).  Memory: states are kept every `ckpt` steps and each segment is
-   recomputed.  Returns 0, or -1 on allocation failure. */
+   type), for RK4 (order 4) or Euler (order 1) steps.  Memory: states are
+   kept every `ckpt` steps and each segment is recomputed.  Returns 0, or -1
+   on allocation failure. */
 int orc_adjoint(const orc_net *net, const double *y0, int64_t step0, int64_t nsteps, int64_t rec_stride,
-                const double *dLdV, double *grad_y0, double *grad_w, double *grad_np, int64_t ckpt)
+                const double *dLdV, double *grad_y0, double *grad_w, double *grad_np, int64_t ckpt, int order)
 {
     const int64_t d = 4 * net->N + 2 * net->S;
     if (ckpt < 1) ckpt = 1;
@@ -511,7 +533,7 @@ int orc_adjoint(const orc_net *net, const double *y0, int64_t step0, int64_t nst
         memcpy(y, y0, sizeof(double) * (size_t)d);
         for (int64_t k = 0; k < nsteps; ++k) {
             orc_input(net, step0 + k, iext);
-            rk4_step(d, net->dt, net_rhs, &fc, y, work);
+            take_step(order, d, net->dt, net_rhs, &fc, y, work);
             if ((k + 1) % ckpt == 0) memcpy(cks + ((k + 1) / ckpt) * d, y, sizeof(double) * (size_t)d);
         }
     }
@@ -535,11 +557,11 @@ int orc_adjoint(const orc_net *net, const double *y0, int64_t step0, int64_t nst
         for (int64_t k = k0; k < k1 - 1; ++k) {
             memcpy(seg + (k - k0 + 1) * d, seg + (k - k0) * d, sizeof(double) * (size_t)d);
             orc_input(net, step0 + k, iext);
-            rk4_step(d, net->dt, net_rhs, &fc, seg + (k - k0 + 1) * d, work);
+            take_step(order, d, net->dt, net_rhs, &fc, seg + (k - k0 + 1) * d, work);
         }
         for (int64_t k = k1 - 1; k >= k0; --k) {
             orc_input(net, step0 + k, iext);
-            rk4_adjoint_step(d, net->dt, net_rhs_adj, net_vjp, &ac, seg + (k - k0) * d, lam, work);
+            adjoint_step(order, d, net->dt, net_rhs_adj, net_vjp, &ac, seg + (k - k0) * d, lam, work);
             /* state y_{step0+k} is a frame when its global index qualifies */
             if (rec_stride > 0 && k > 0 && (step0 + k) % rec_stride == 0 && frame >= 0) {
                 for (int64_t i = 0; i < net->N; ++i) lam[i] += dLdV[frame * net->N + i];
