@@ -116,7 +116,7 @@ typedef struct {
     int32_t gate_mode;             /* 0: one gate per (presynaptic neuron, type) pair whenever all
                                       its synapses' gates are equal (bitwise-identical results,
                                       less work), else one per synapse; 1: always one per synapse */
-    int32_t method;                /* PSST_METHOD_RK4 (0) or PSST_METHOD_EULER; psst_adjoint needs RK4 */
+    int32_t method;                /* PSST_METHOD_RK4 (0) or PSST_METHOD_EULER (1) */
     int32_t min_cluster;           /* CTA mode: spread every network of at least 2 x min_cluster neurons
                                       over a cluster of at least min_cluster CTAs (1, 2 or 4; same
                                       results, shorter steps when SMs are idle); 0 = chosen by
@@ -240,8 +240,9 @@ int psst_set_neuron_params(psst_net *h, const float *p, size_t n, int on_device,
    (ceil(max_steps / every) full states) is allocated here. */
 int psst_record_checkpoints(psst_net *h, int32_t every, int64_t max_steps);
 
-/* Discrete adjoint of the RK4 map (no counterpart in the paper; the
-   differentiated form).  For the n_steps steps that a psst_integrate call
+/* Discrete adjoint of the integration map -- RK4, or forward Euler
+   (Eq. euler) when the handle's method is PSST_METHOD_EULER -- (no
+   counterpart in the paper; the differentiated form).  For the n_steps steps that a psst_integrate call
    made now would take -- from the current state and step index -- computes
    the gradient of
        L = sum_f sum_i dL_dV[f][i] * V_i(frame f)
@@ -257,8 +258,7 @@ int psst_record_checkpoints(psst_net *h, int32_t every, int64_t max_steps);
    ckpt_every = 0 differentiates instead the span of the last psst_integrate
    call, whose checkpoints were recorded (psst_record_checkpoints); n_steps
    must equal that call's; PSST_ERR_STATE if no such checkpoints exist.
-   Preconditions: CTA mode and method PSST_METHOD_RK4 (else
-   PSST_ERR_UNSUPPORTED); every network fits one CTA for the adjoint; all
+   Preconditions: CTA mode (else PSST_ERR_UNSUPPORTED); every network fits one CTA for the adjoint; all
    gates of a (presynaptic neuron, synapse type) pair hold the same value at
    the start (true from rest), else the device reports PSST_ERR_UNSUPPORTED
    through psst_status.  Each network runs on a cluster of two CTAs (forward

@@ -2,8 +2,8 @@
 function of the synaptic weights and the neuron-type table.
 
 Forward runs ``psst_integrate`` (recording V every ``rec_stride`` steps of
-the network); backward runs the discrete RK4 adjoint ``psst_adjoint`` from
-the same starting state.  Both are CUDA kernels of the library.
+the network); backward runs the discrete adjoint ``psst_adjoint`` of the
+network's method (RK4 or forward Euler) from the same starting state.  Both are CUDA kernels of the library.
 """
 from __future__ import annotations
 

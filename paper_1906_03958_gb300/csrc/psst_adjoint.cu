@@ -1,6 +1,7 @@
-// Discrete adjoint of the RK4 network map (the differentiated form).
+// Discrete adjoint of the RK4 or forward-Euler network map (the
+// differentiated form).
 //
-// Gradient of L = sum_f sum_i dL/dV[f][i] V_i(frame f) over n RK4 steps from
+// Gradient of L = sum_f sum_i dL/dV[f][i] V_i(frame f) over n steps from
 // the current state, with respect to every synaptic weight and every
 // neuron-type parameter, for batches of networks (one cluster of two CTAs per
 // network: one recomputes segments forward, the other sweeps them backward).
@@ -20,8 +21,10 @@
 //   kb2 = h/3 lam + h/2 Yb3, Yb2 = J(Y2)^T kb2
 //   kb1 = h/6 lam + h/2 Yb2, Yb1 = J(Y1)^T kb1
 //   lam_n = lam + Yb1 + Yb2 + Yb3 + Yb4;  theta_bar += sum_s (df/dtheta)^T kb_s.
+// Forward Euler (Eq. euler) is the one-stage case: kb1 = h lam,
+// lam_n = lam + J(y_n)^T kb1.
 // States are checkpointed every `ckpt` steps in a first forward pass; each
-// segment is recomputed forward, keeping every step's four stages in global
+// segment is recomputed forward, keeping every step's stages in global
 // memory, then swept backward from those stages.
 //
 // Jacobian-transpose product at a stage (q_i = kbV_i / C_i,
@@ -36,7 +39,7 @@
 // The column sums go through per-warp partial rows summed in warp order when
 // no row holds two synapses of one pair (fixed order, reproducible), else
 // through shared-memory atomics (order not fixed).  The weight gradients are
-// summed over each step's four stages in one pass, into an FP32 partial per
+// summed over each step's stages in one pass, into an FP32 partial per
 // segment, then into an FP64 total.
 #include <cuda_runtime.h>
 
@@ -127,9 +130,10 @@ struct AdjNet {
 
 // ---------------------------------------------------------------- forward
 
-// Forward of one RK4 step of the reduced model from S.y (step `step`),
-// storing the four stages' values; on return S.y holds the next state.
-template <bool STORE>
+// Forward of one step of the reduced model from S.y (step `step`) with NST
+// stages (4: RK4, 1: forward Euler), storing the stages' values; on return
+// S.y holds the next state.
+template <bool STORE, int NST>
 __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, const float *stab, long long step,
                          float dt) {
     const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M;
@@ -154,7 +158,7 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
     }
     __syncthreads();
 #pragma unroll 1
-    for (int st = 0; st < 4; ++st) {
+    for (int st = 0; st < NST; ++st) {
         const float *G = S.sG + st * M;
         // synaptic sums per item
         const int K = a.K, ni = a.n_items;
@@ -180,7 +184,7 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
         __syncthreads();
         const float WGT = (st == 0 || st == 3) ? 1.0f : 2.0f;
         const float cnext = (st == 2) ? dt : 0.5f * dt;
-        const float dt6 = dt * (1.0f / 6.0f);
+        const float dt6 = NST == 1 ? dt : dt * (1.0f / 6.0f);  // h b_s of the last stage's sum
         for (int i = tid; i < N; i += nthr) {
             float A = 0.0f, B = 0.0f;
             for (int it = S.ib[i]; it < S.ib[i + 1]; ++it) {
@@ -207,7 +211,7 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
             for (int x = 0; x < 4; ++x) {
                 const int ix = x * N + i;
                 const float ac = (st == 0) ? d[x] : fmaf(WGT, d[x], S.acc[ix]);
-                if (st < 3) {
+                if (st < NST - 1) {
                     S.acc[ix] = ac;
                     stg[x][(st + 1) * N + i] = fmaf(cnext, d[x], S.y[ix]);
                 } else {
@@ -226,7 +230,7 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
                 const float ar = (st == 0) ? dr : fmaf(WGT, dr, S.acc[ir]);
                 const float as = (st == 0) ? ds : fmaf(WGT, ds, S.acc[is]);
                 float rn, sn;
-                if (st < 3) {
+                if (st < NST - 1) {
                     S.acc[ir] = ar;
                     S.acc[is] = as;
                     rn = fmaf(cnext, dr, S.y[ir]);
@@ -288,15 +292,18 @@ __device__ __forceinline__ void column_sums(const AdjNet &a, const AdjSmem &S, i
     }
 }
 
-// Reverse of the step whose stages fwd_step<true> just stored: lam holds the
-// adjoint of y_{n+1} on entry and of y_n on exit (before the frame term).
+// Reverse of the step whose NST stages fwd_step<true, NST> just stored: lam
+// holds the adjoint of y_{n+1} on entry and of y_n on exit (before the frame
+// term).
+template <int NST>
 __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, float dt, float4 *gpart) {
     const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M, K = a.K, ni = a.n_items;
     const int D = 4 * N + 2 * M;
-    const float cb[4] = {dt / 6.0f, dt / 3.0f, dt / 3.0f, dt / 6.0f};  // h b_s
-    const float ca[4] = {0.5f * dt, 0.5f * dt, dt, 0.0f};             // h a_{s+1,s}
+    // h b_s and h a_{s+1,s} (Euler: b_1 = 1, no later stage)
+    const float cb[4] = {NST == 1 ? dt : dt / 6.0f, dt / 3.0f, dt / 3.0f, dt / 6.0f};
+    const float ca[4] = {0.5f * dt, 0.5f * dt, dt, 0.0f};
 #pragma unroll 1
-    for (int st = 3; st >= 0; --st) {
+    for (int st = NST - 1; st >= 0; --st) {
         // A) owners: stage adjoint kb, neuron-local products, parameter gradients
         for (int i = tid; i < N; i += nthr) {
             const float Vs = S.sV[st * N + i], ms = S.sm[st * N + i], hs = S.sh[st * N + i], ns = S.sn[st * N + i];
@@ -304,7 +311,7 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, f
 #pragma unroll
             for (int x = 0; x < 4; ++x) {
                 const int ix = x * N + i;
-                kb[x] = cb[st] * S.lam[ix] + (st < 3 ? ca[st] * S.yprev[ix] : 0.0f);
+                kb[x] = cb[st] * S.lam[ix] + (st < NST - 1 ? ca[st] * S.yprev[ix] : 0.0f);
             }
             const float *P = S.prm;
             const float invC = P[NP_C * N + i];
@@ -351,8 +358,8 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, f
                 const float C = S.csum[p];
                 S.csum[p] = 0.0f;
                 const int ir = 4 * N + p, is = 4 * N + M + p;
-                const float kbr = cb[st] * S.lam[ir] + (st < 3 ? ca[st] * S.yprev[ir] : 0.0f);
-                const float kbs = cb[st] * S.lam[is] + (st < 3 ? ca[st] * S.yprev[is] : 0.0f);
+                const float kbr = cb[st] * S.lam[ir] + (st < NST - 1 ? ca[st] * S.yprev[ir] : 0.0f);
+                const float kbs = cb[st] * S.lam[is] + (st < NST - 1 ? ca[st] * S.yprev[is] : 0.0f);
                 const float rs = S.sr[st * M + p], ss = S.ss[st * M + p];
                 const float T = transmitter(Vs, sp[SP_VP], sp[SP_KP]);
                 const float dT = T * (1.0f - T) * sp[SP_KP];  // table holds 1/Kp
@@ -394,7 +401,7 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, f
             const float E = S.Ep[p];
             float acc = 0.0f;
 #pragma unroll
-            for (int st = 0; st < 4; ++st) {
+            for (int st = 0; st < NST; ++st) {
                 const float2 abv = S.ab[st * N + i];
                 acc = fmaf(S.sG[st * M + p], fmaf(E, abv.y, -abv.x), acc);
             }
@@ -452,6 +459,34 @@ __device__ void load_reduced(const NetView &v, const AdjNet &a, const AdjSmem &S
     }
 }
 
+// Floats a step keeps in a segment buffer: the NST stages' values of V, m, h,
+// n, A and f_V per neuron and r, s, G per pair.
+__host__ __device__ inline long long adj_step_floats(int nst, long long N, long long M) {
+    return (long long)nst * (6 * N + 3 * M);
+}
+
+// Copy of stage 0 of the stage arrays (sV .. sfv, each [4][len]) to or from
+// a compact block of 6N + 3M floats (the one-stage method's step record).
+template <bool TO_BLOCK>
+__device__ void copy_stage0(float *stages, float *blk, int N, int M) {
+    const int tot = 6 * N + 3 * M;
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+        int at;
+        if (q < 4 * N) {
+            at = 4 * N * (q / N) + q % N;  // V, m, h, n
+        } else if (q < 4 * N + 3 * M) {
+            const int r = q - 4 * N;
+            at = 16 * N + 4 * M * (r / M) + r % M;  // r, s, G
+        } else {
+            const int r = q - 4 * N - 3 * M;
+            at = 16 * N + 12 * M + 4 * N * (r / N) + r % N;  // A, f_V
+        }
+        if (TO_BLOCK) blk[q] = stages[at];
+        else stages[at] = blk[q];
+    }
+}
+
+template <int NST>
 __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av, long long step0, int nsteps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float stab[PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM];
@@ -577,8 +612,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         return;
     }
 
-    // the four stages' arrays form one contiguous block (sV .. sfv)
+    // the stage arrays form one contiguous block (sV .. sfv) of stage_floats;
+    // a step keeps step_floats of it (all of it for RK4, stage 0 for Euler)
     const int stage_floats = 4 * (6 * N + 3 * M);
+    const int step_floats = (int)adj_step_floats(NST, N, M);
     float4 *stage_blk = (float4 *)S.sV;
     const int ckpt = av.ckpt_every;
     const float dt = v.dt;
@@ -587,7 +624,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     const bool fwd_cta = cluster_rank() == 0;
     float *ck = av.ckpt + av.ck_off[a.b];
     float *seg0 = av.seg + av.seg_off[a.b];
-    const long long seg_buf = (long long)min(ckpt, nsteps) * stage_floats;  // floats of one segment buffer
+    const long long seg_buf = (long long)min(ckpt, nsteps) * step_floats;  // floats of one segment buffer
     float4 *gpart = av.gpart + av.slot_off[a.b] / 4;
     double *gtot = av.gtot + av.slot_off[a.b];
     if (!fwd_cta) {
@@ -599,7 +636,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         for (int n = 0; n < nsteps; ++n) {
             if (n % ckpt == 0)
                 for (int q = tid; q < a.R; q += nthr) ck[(long long)(n / ckpt) * a.R + q] = S.y[q];
-            fwd_step<false>(v, a, S, stab, step0 + n, dt);
+            fwd_step<false, NST>(v, a, S, stab, step0 + n, dt);
         }
     }
     // frames: global steps k in (step0, step0 + nsteps] with k % stride == 0
@@ -623,9 +660,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         }
         float *seg = seg0 + (long long)(c & 1) * seg_buf;
         for (int n = k0; n < k1; ++n) {
-            fwd_step<true>(v, a, S, stab, step0 + n, dt);
-            float4 *dst = (float4 *)(seg + (long long)(n - k0) * stage_floats);
-            for (int q = tid; q < stage_floats / 4; q += nthr) dst[q] = stage_blk[q];
+            fwd_step<true, NST>(v, a, S, stab, step0 + n, dt);
+            float *dst = seg + (long long)(n - k0) * step_floats;
+            if (NST == 4) {
+                for (int q = tid; q < stage_floats / 4; q += nthr) ((float4 *)dst)[q] = stage_blk[q];
+            } else {
+                copy_stage0<true>(S.sV, dst, N, M);
+            }
             __syncthreads();
         }
     };
@@ -634,10 +675,14 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         const int k0 = c * ckpt, k1 = min(k0 + ckpt, nsteps);
         const float *seg = seg0 + (long long)(c & 1) * seg_buf;
         for (int n = k1 - 1; n >= k0; --n) {
-            const float4 *src = (const float4 *)(seg + (long long)(n - k0) * stage_floats);
-            for (int q = tid; q < stage_floats / 4; q += nthr) stage_blk[q] = src[q];
+            const float *src = seg + (long long)(n - k0) * step_floats;
+            if (NST == 4) {
+                for (int q = tid; q < stage_floats / 4; q += nthr) stage_blk[q] = ((const float4 *)src)[q];
+            } else {
+                copy_stage0<false>(S.sV, (float *)src, N, M);
+            }
             __syncthreads();
-            rev_step(a, S, stab, dt, gpart);
+            rev_step<NST>(a, S, stab, dt, gpart);
             if (stride > 0 && n > 0 && (step0 + n) % stride == 0 && frame >= 0) {
                 for (int i = tid; i < N; i += nthr) S.lam[i] += dl[(long long)frame * v.N + a.n0 + i];
                 --frame;
@@ -697,13 +742,19 @@ __global__ void adj_reduce_types(const int *neuron_type, long long N, const doub
 
 }  // namespace
 
+long long adj_segment_floats(int method, int N, int nt) {
+    return adj_step_floats(method == PSST_METHOD_EULER ? 1 : 4, N, (long long)N * nt);
+}
+
 long long adj_smem_need(int N, int nt, int n_items, int K, bool col_warp) {
     return adj_smem_bytes(N, N * nt, n_items, K) + (col_warp ? 4LL * (ADJ_THREADS / 32) * N * nt + 16 : 0);
 }
 
 cudaError_t adj_launch(const NetView &v, const AdjView &av, long long step0, int nsteps, int smem, int n_types,
                        float *grad_np, cudaStream_t stream) {
-    cudaError_t e = cudaFuncSetAttribute(adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // RK4 (four stages a step) or forward Euler (one)
+    void (*kern)(NetView, AdjView, long long, int) = v.method == PSST_METHOD_EULER ? adj_kernel<1> : adj_kernel<4>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     // one cluster of two CTAs per network: forward recompute and reverse sweep
     cudaLaunchConfig_t cfg = {};
@@ -718,7 +769,7 @@ cudaError_t adj_launch(const NetView &v, const AdjView &av, long long step0, int
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, adj_kernel, v, av, step0, nsteps);
+    e = cudaLaunchKernelEx(&cfg, kern, v, av, step0, nsteps);
     if (e != cudaSuccess) return e;
     adj_reduce_types<<<n_types, 32, 0, stream>>>(v.neuron_type, v.N, av.gp_neuron, n_types, grad_np);
     return cudaGetLastError();

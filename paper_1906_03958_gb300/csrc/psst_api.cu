@@ -1350,8 +1350,6 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
                  float *grad_w, float *grad_neuron_params, float *grad_state0, void *stream) {
     if (!h || !grad_w || !grad_neuron_params) return fail(PSST_ERR_INVALID_ARG, "NULL argument");
     if (h->mode != PSST_MODE_CTA) return fail(PSST_ERR_UNSUPPORTED, "the adjoint runs in CTA mode only");
-    if (h->v.method != PSST_METHOD_RK4)
-        return fail(PSST_ERR_UNSUPPORTED, "the adjoint is the discrete adjoint of the RK4 map (method RK4 only)");
     if (n_steps < 1 || n_steps > (1LL << 30)) return fail(PSST_ERR_INVALID_ARG, "n_steps must be in 1..2^30");
     const bool recorded = ckpt_every == 0;
     if (recorded) {
@@ -1434,11 +1432,11 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         long long ck_total = 0, seg_total = 0;
         for (int b = 0; b < n_nets; ++b) {
             const long long N = off[b + 1] - off[b], R = 4 * N + 2 * N * nt;
-            const long long stage_floats = 4 * (6 * N + 3 * N * nt);  // four stages of one step
+            const long long step_floats = psst::adj_segment_floats(h->v.method, (int)N, nt);  // one step's stages
             ck[b] = ck_total;
             sg[b] = seg_total;
             ck_total += nck * R;
-            seg_total += 2LL * std::min<long long>(ckpt_every, n_steps) * stage_floats;  // two buffers
+            seg_total += 2LL * std::min<long long>(ckpt_every, n_steps) * step_floats;  // two buffers
         }
         if (ck_total > h->adj_ck_cap) {
             e = h->alloc(&h->adj_ckpt, (size_t)ck_total);

@@ -88,12 +88,112 @@ def test_euler_trajectory_tracks_oracle_euler():
     assert np.max(np.abs(rec32 - rec64)) < 1e-2
 
 
-def test_adjoint_requires_rk4():
+GRAD_TOL = 1e-3
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30)
+
+
+def _diff_spec(seed, sets=1):
+    _, spec = ng.differentiated(n_sets=sets, seed=seed, n_pn=12, n_ln=4)
+    spec.pulse_on[:] = 5
+    spec.pulse_off[:] = 10_000
+    return spec
+
+
+def _euler_adjoint(spec, nsteps, dLdV, stride, ckpt=50, step0=0):
     import torch
-    from paper_1906_03958_gb300 import psst
-    spec = ng.antennal_lobe(seed=86, n_pn=12, n_ln=4)
-    with _net(spec, rec_stride=1, rec_capacity=10) as net:
-        net.integrate(10)
-        with pytest.raises(psst.PsstError) as ei:
-            net.adjoint(10, torch.zeros((10, spec.n_neurons), device="cuda"), 5)
-        assert ei.value.code == -7
+    with _net(spec, rec_stride=stride, rec_capacity=nsteps // stride + 1) as net:
+        net.set_step(step0)
+        gw, gp, gy = net.adjoint(nsteps, torch.from_numpy(dLdV.astype(np.float32)).cuda(), ckpt)
+        net.status()
+        return gw.cpu().numpy(), gp.cpu().numpy(), gy.cpu().numpy()
+
+
+@pytest.mark.parametrize("sets,ckpt", [(1, 100), (3, 64)])
+def test_euler_adjoint_matches_oracle_euler_adjoint(sets, ckpt):
+    # discrete adjoint of the Euler map (one stage, kb = h lam) against the
+    # oracle's FP64 Euler adjoint, for one network and a batch of three
+    spec = _diff_spec(seed=87 + sets, sets=sets)
+    rng = np.random.default_rng(sets)
+    nsteps, stride = 800, 8
+    g = rng.standard_normal((nsteps // stride, spec.n_neurons))
+    gy64, gw64, gp64 = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, ckpt=ckpt, order=1)
+    gw, gp, gy = _euler_adjoint(spec, nsteps, g, stride, ckpt=ckpt)
+    for b in range(spec.n_nets):
+        s0, s1 = spec.row_ptr[spec.net_neuron_off[b]], spec.row_ptr[spec.net_neuron_off[b + 1]]
+        assert _rel(gw[s0:s1], gw64[s0:s1]) <= GRAD_TOL
+        assert _rel(gp[2 * b:2 * b + 2], gp64[2 * b:2 * b + 2]) <= GRAD_TOL
+    N = spec.n_neurons
+    assert _rel(gy.ravel(), gy64[:4 * N]) <= GRAD_TOL
+    # not the RK4 adjoint: the two maps' gradients differ by more than the bar
+    _, gw_rk4, _ = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, ckpt=ckpt, order=4)
+    assert _rel(gw_rk4, gw64) > 10 * GRAD_TOL
+
+
+def test_euler_adjoint_vs_fp64_finite_differences():
+    # weights and conductances, central differences with h = 1e-6 max(1, |theta|)
+    # on the FP64 Euler map; the differences' own rounding noise,
+    # 4 eps sum|terms of L| / h, is admitted on top of the bar
+    spec = _diff_spec(seed=90)
+    net = oracle.OracleNet(spec)
+    rng = np.random.default_rng(5)
+    nsteps, stride = 500, 5
+    g = rng.standard_normal((nsteps // stride, spec.n_neurons))
+    y0 = oracle.rest_state(net)
+    gw, gp, _ = _euler_adjoint(spec, nsteps, g, stride)
+
+    def loss():
+        _, rec = oracle.integrate(net, y0, nsteps, rec_stride=stride, order=1)
+        return float(np.sum(rec * g))
+
+    def fd(arr, idx):
+        x0 = arr[idx]
+        h = 1e-6 * max(1.0, abs(x0))
+        arr[idx] = x0 + h
+        lp = loss()
+        arr[idx] = x0 - h
+        lm = loss()
+        arr[idx] = x0
+        return (lp - lm) / (2 * h)
+
+    _, rec = oracle.integrate(net, y0, nsteps, rec_stride=stride, order=1)
+    fd_noise = 4.0 * np.finfo(float).eps * float(np.sum(np.abs(rec * g))) / 1e-6
+    nz = np.nonzero(net.w)[0]
+    coords = [("w", int(k)) for k in rng.choice(nz, 4, replace=False)] + \
+             [("w", int(k)) for k in rng.choice(np.nonzero(net.w == 0)[0], 2, replace=False)]
+    P = net.nparams.reshape(-1, 9)
+    coords += [("p", (0, 1)), ("p", (0, 2)), ("p", (1, 3)), ("p", (1, 7))]
+    scale_w = np.abs(gw).max()
+    for kind, idx in coords:
+        if kind == "w":
+            want, got, scale = fd(net.w, idx), gw[idx], scale_w
+        else:
+            want, got, scale = fd(P, idx), gp[idx], abs(fd(P, idx))
+        assert abs(got - want) <= GRAD_TOL * max(abs(want), 1e-2 * scale) + fd_noise, (kind, idx, got, want)
+
+
+def test_euler_adjoint_checkpoint_spacing_step_offset_and_recorded_span():
+    import torch
+    spec = _diff_spec(seed=91, sets=2)
+    rng = np.random.default_rng(6)
+    nsteps, stride, step0 = 240, 4, 2
+    frames = (step0 + nsteps) // stride - step0 // stride
+    g = rng.standard_normal((frames, spec.n_neurons))
+    a = _euler_adjoint(spec, nsteps, g, stride, ckpt=7, step0=step0)
+    b = _euler_adjoint(spec, nsteps, g, stride, ckpt=240, step0=step0)
+    for x, y in zip(a, b):
+        assert _rel(x, y) <= 1e-5
+    _, gw64, _ = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, step0=step0, order=1)
+    assert _rel(a[0], gw64) <= GRAD_TOL
+    # the span of an Euler integrate call whose checkpoints were recorded
+    gt = torch.from_numpy(g.astype(np.float32)).cuda()
+    with _net(spec, rec_stride=stride, rec_capacity=frames) as net:
+        net.set_step(step0)
+        net.record_checkpoints(60, nsteps)
+        net.integrate(nsteps)
+        rec = net.adjoint(nsteps, gt, 0)
+        net.status()
+        assert _rel(rec[0].cpu().numpy(), a[0]) <= 1e-5
+        assert _rel(rec[1].cpu().numpy(), a[1]) <= 1e-5
