@@ -14,15 +14,16 @@
 // Per RK4 step (classic tableau, Sec. "Brain simulations as computational
 // graphs", RK4 paragraph) and stage s = 0..3 (Euler: one stage):
 //   S-phase   each thread sums its work items (per-pair layout: A = sum w G
-//             with the pair's gate G gathered from the gate table);
+//             with the pair's gate G gathered from the gate table), after
+//             the owned neurons' gates m, h, n (on the highest threads);
 //   barrier   (CTA);
 //   N-phase   one work loop over independent units: the potential of each
 //             owned neuron (its row's item partials give I_syn, then the HH
 //             currents and the stage update; the next stage potential goes
 //             to every CTA of the cluster through distributed shared
-//             memory), its gates m, h, n, and the gate map (and per-pair
-//             gate) of every entry from the stage-s potentials (identical
-//             values in every CTA);
+//             memory), and the gate map (and per-pair gate) of every entry
+//             from the stage-s potentials (identical values in every CTA);
+//             the potentials take whole warps;
 //   barrier   CTA barrier (CL = 1) or cluster barrier (CL > 1).
 // Stage potentials and gates are double-buffered by parity, so a CTA can
 // write the next stage's values while a peer still reads this stage's.
@@ -89,14 +90,22 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
     // gate-map entries: every (neuron, type) pair, or the used pairs (PAIR)
     float *r0p = pst, *s0p = pst + M;
     const unsigned short *pof = (const unsigned short *)(pst + 2 * M);
+    // The gates m, h, n of the owned neurons need only this stage's
+    // potentials: they are computed before the S-phase (on the highest
+    // threads), where their latency overlaps the S-phase's loads, and leave
+    // the N-phase fewer units.
+    for (int i = nthr - 1 - tid; i < nown; i += nthr)
+        neuron_gates<ST>(i, nown, vcur[r_lo + i], ysc, ysn, y0, acc, dt);
     if (PAIR) sphase_pair(it, Gt, lrep);
     else sphase<ST, HAS2>(it, SmemCoef{FIRST ? fin1 : cur1, FIRST ? fin2 : cur2});
     __syncthreads();
-    // independent work units: potential of each owned neuron, its gates, and
-    // the gate map (and per-pair gate) of each entry
-    const int U = 2 * nown + M;
+    // independent work units: potential of each owned neuron and the gate
+    // map (and per-pair gate) of each entry; the potentials take whole warps
+    const int nw = (nown + 31) & ~31;
+    const int U = nw + M;
     for (int u = tid; u < U; u += nthr) {
-        if (u < nown) {
+        if (u < nw) {
+            if (u >= nown) continue;
             const int i = u;
             const float V = vcur[r_lo + i];
             const VPre pre = neuron_v_pre<ST>(i, nown, V, ysc, y0, acc, prm, iext[i]);
@@ -108,11 +117,8 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
                 for (unsigned q = 1; q < CL; ++q) st_peer(vnxt + r_lo + i, (rank + q) % CL, vn);
             }
             if (LAST && rec_slot >= 0) v.rec[rec_slot * v.N + n0 + r_lo + i] = vn;
-        } else if (u < 2 * nown) {
-            const int i = u - nown;
-            neuron_gates<ST>(i, nown, vcur[r_lo + i], ysc, ysn, y0, acc, dt);
         } else {
-            const int p = u - 2 * nown;
+            const int p = u - nw;
             float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
             float4 &c2 = HAS2 ? cur2[p] : d4;
             float4 &a2 = HAS2 ? acc2[p] : d4;

@@ -100,6 +100,8 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
     float *vnxt = vst + (par ^ 1) * N;
     const float *ysc = ys + par * 3 * N;
     float *ysn = ys + (par ^ 1) * 3 * N;
+    // gates m, h, n of the owned neurons before the S-phase (as in the CTA kernel)
+    for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates<ST>(i, N, vcur[i], ysc, ysn, y0, acc, dt);
     if (PAIR) {
         // this stage's gate of every used pair, written by the owners before the last barrier
         const float4 *src = (const float4 *)(g.gt + (size_t)par * g.mt);
@@ -113,15 +115,17 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
         sphase<ST, HAS2>(it, GlobalCoef{g.c1 + (size_t)par * M, HAS2 ? g.c2 + (size_t)par * M : nullptr});
     }
     __syncthreads();
-    // independent work units: potential and gates of each owned neuron, and
-    // the gate map of each own (neuron, type) pair
+    // independent work units: potential of each owned neuron and the gate map
+    // of each own (neuron, type) pair; the potentials take whole warps
     float *r0p = pst, *s0p = pst + Mloc;
     float *gout = PAIR ? g.gt + (size_t)(par ^ 1) * g.mt : nullptr;
     float2 *o1 = g.c1 + (size_t)(par ^ 1) * M + (size_t)lo * nt;
     float4 *o2 = HAS2 ? g.c2 + (size_t)(par ^ 1) * M + (size_t)lo * nt : nullptr;
-    const int U = 2 * N + Mloc;
+    const int nw = (N + 31) & ~31;
+    const int U = nw + Mloc;
     for (int u = tid; u < U; u += nthr) {
-        if (u < N) {
+        if (u < nw) {
+            if (u >= N) continue;
             const int i = u;
             const float V = vcur[i];
             const VPre pre = neuron_v_pre<ST>(i, N, V, ysc, y0, acc, prm, iext[i]);
@@ -129,11 +133,8 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
             const float vn = neuron_v_post<ST>(i, pre, isyn, y0, acc, dt);
             vnxt[i] = vn;
             if (LAST && rec_slot >= 0) v.rec[rec_slot * v.N + lo + i] = vn;
-        } else if (u < 2 * N) {
-            const int i = u - N;
-            neuron_gates<ST>(i, N, vcur[i], ysc, ysn, y0, acc, dt);
         } else {
-            const int p = u - 2 * N;
+            const int p = u - nw;
             if (PAIR) {
                 // gate of an own used pair for the next stage (same operations as
                 // the per-synapse path), published in the other table
