@@ -134,7 +134,13 @@ struct psst_net {
         cudaError_t e = cudaSuccess;
         if (user_alloc.alloc) {
             q = user_alloc.alloc(bytes, user_alloc.ctx);
-            if (!q) e = cudaErrorMemoryAllocation;
+            if (!q) {
+                e = cudaErrorMemoryAllocation;
+            } else if ((uintptr_t)q & 255u) {  // the kernels' vector and 64-bit accesses need the documented alignment
+                user_alloc.free(q, user_alloc.ctx);
+                q = nullptr;
+                e = cudaErrorMisalignedAddress;
+            }
         } else {
             e = cudaMalloc(&q, bytes);
         }

@@ -58,7 +58,7 @@ enum : uint8_t { NET_HAS2 = 1, NET_PAIR = 2 };  // NET_PAIR: all gates of each (
 struct GridView {
     float2 *c1;                  // [2][N * n_stypes] gate maps (r), double-buffered by stage parity
     float4 *c2;                  // [2][N * n_stypes] gate maps (s), second-order networks only
-    unsigned *bar;               // [2] barrier arrival counter and generation
+    unsigned *bar;               // [2]: the barrier's 64-bit arrival count (8-byte aligned)
     const int *row_split;        // [gridDim.x + 1] first row owned by each CTA
     const int *items;            // [2][gridDim.x] first- and second-order work items of each CTA
     int K;                       // 4-synapse chunks per work item

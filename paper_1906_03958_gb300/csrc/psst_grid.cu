@@ -36,30 +36,32 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned x;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(x) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+    unsigned long long x;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(x) : "l"(p) : "memory");
     return x;
 }
 
-// Device-wide barrier over gridDim.x co-resident CTAs.  bar[0] counts
-// arrivals, bar[1] is the generation.  Returns false (after recording the
-// error) when the wait ran out of time or another CTA already failed.
+// Device-wide barrier over gridDim.x co-resident CTAs.  bar holds a 64-bit
+// arrival count, zeroed before each launch, that only grows: barrier k of a
+// launch is passed when the count reaches (k + 1) gridDim.x, and the count a
+// CTA finds on arriving tells it k (no CTA arrives at barrier k + 1 before
+// all have arrived at k).  One atomic and one polled load per CTA.  Returns
+// false (after recording the error) when the wait ran out of time or
+// another CTA already failed.
 __device__ bool grid_barrier(unsigned *bar, unsigned long long timeout_ns, int *err) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned gen = ld_acquire(bar + 1);
+        unsigned long long *cnt = reinterpret_cast<unsigned long long *>(bar);
+        const unsigned long long G = gridDim.x;
         __threadfence();
-        const unsigned prev = atomicAdd(bar, 1u);
+        const unsigned long long prev = atomicAdd(cnt, 1ull);
+        const unsigned long long target = (prev / G + 1) * G;
         int ok = 1;
-        if (prev == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        if (prev + 1 != target) {
             const unsigned long long t0 = globaltimer();
-            while (ld_acquire(bar + 1) == gen) {
+            while (ld_acquire64(cnt) < target) {
                 if (*(volatile int *)err != 0) {
                     ok = 0;
                     break;

@@ -35,7 +35,7 @@ constexpr int kMaxGrid = 512;  // CTAs of one launch (one per SM)
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Scratch layout (byte offsets).
-constexpr size_t kOffBar = 0;         // unsigned[2]: barrier counter and generation
+constexpr size_t kOffBar = 0;         // unsigned[2]: the grid barrier's 64-bit arrival count
 constexpr size_t kOffFlag = 8;        // unsigned: network holds second-order synapses
 constexpr size_t kOffPulse = 16;      // long long[2]: pulse window
 constexpr size_t kOffSplit = 256;     // int[kMaxGrid + 1]: first row of each CTA
