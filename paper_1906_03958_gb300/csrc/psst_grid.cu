@@ -42,35 +42,46 @@ __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long l
     return x;
 }
 
-// Device-wide barrier over gridDim.x co-resident CTAs.  bar holds a 64-bit
-// arrival count, zeroed before each launch, that only grows: barrier k of a
-// launch is passed when the count reaches (k + 1) gridDim.x, and the count a
-// CTA finds on arriving tells it k (no CTA arrives at barrier k + 1 before
-// all have arrived at k).  One atomic and one polled load per CTA.  Returns
-// false (after recording the error) when the wait ran out of time or
-// another CTA already failed.
-__device__ bool grid_barrier(unsigned *bar, unsigned long long timeout_ns, int *err) {
-    __shared__ int s_ok;
+// Device-wide barrier over gridDim.x co-resident CTAs, in two halves so
+// that work on a CTA's own data can run while the others arrive.  bar holds
+// a 64-bit arrival count, zeroed before each launch, that only grows:
+// barrier k of a launch is passed when the count reaches (k + 1) gridDim.x,
+// and the count a CTA finds on arriving tells it k.  Every grid_arrive is
+// followed by its grid_wait before the CTA arrives again, so no CTA arrives
+// at barrier k + 1 before all have arrived at k.
+//
+// grid_arrive: after the phase's global writes; returns the count to wait
+// for (in thread 0).
+__device__ unsigned long long grid_arrive(unsigned *bar) {
     __syncthreads();
+    unsigned long long target = 0;
     if (threadIdx.x == 0) {
-        unsigned long long *cnt = reinterpret_cast<unsigned long long *>(bar);
         const unsigned long long G = gridDim.x;
         __threadfence();
-        const unsigned long long prev = atomicAdd(cnt, 1ull);
-        const unsigned long long target = (prev / G + 1) * G;
+        const unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long *>(bar), 1ull);
+        target = (prev / G + 1) * G;
+    }
+    return target;
+}
+
+// grid_wait: before the next phase's global reads.  Returns false (after
+// recording the error) when the wait ran out of time or another CTA already
+// failed.
+__device__ bool grid_wait(unsigned *bar, unsigned long long target, unsigned long long timeout_ns, int *err) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        const unsigned long long *cnt = reinterpret_cast<const unsigned long long *>(bar);
         int ok = 1;
-        if (prev + 1 != target) {
-            const unsigned long long t0 = globaltimer();
-            while (ld_acquire64(cnt) < target) {
-                if (*(volatile int *)err != 0) {
-                    ok = 0;
-                    break;
-                }
-                if (globaltimer() - t0 > timeout_ns) {
-                    set_error(err, PSST_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
+        const unsigned long long t0 = globaltimer();
+        while (ld_acquire64(cnt) < target) {
+            if (*(volatile int *)err != 0) {
+                ok = 0;
+                break;
+            }
+            if (globaltimer() - t0 > timeout_ns) {
+                set_error(err, PSST_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
         }
         __threadfence();
@@ -78,6 +89,10 @@ __device__ bool grid_barrier(unsigned *bar, unsigned long long timeout_ns, int *
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ bool grid_barrier(unsigned *bar, unsigned long long timeout_ns, int *err) {
+    return grid_wait(bar, grid_arrive(bar), timeout_ns, err);
 }
 
 struct GlobalCoef {
@@ -89,21 +104,25 @@ struct GlobalCoef {
 
 // One stage: ST = 0..3 of classic RK4, or ST = 4, forward Euler's single
 // stage; par selects the double-buffered potentials, gates and global tables
-// this stage reads (RK4: ST & 1; Euler: the step's parity).
+// this stage reads (RK4: ST & 1; Euler: the step's parity).  On entry the
+// owned neurons' gates m, h, n of this stage are done and tgt is the barrier
+// count to wait for; on return the CTA has arrived at the stage's closing
+// barrier (tgt updated) and, when `more`, computed the next stage's gates.
 template <int ST, bool HAS2, bool PAIR>
 __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, const Items &it, int lo, int N,
                                            int nt, int M, long long rec_slot, float dt, float *vst, float *y0,
                                            float *acc, float *ys, const float *prm, const float *iext,
                                            float2 *cur1, float2 *acc1, float4 *cur2, float4 *acc2, float *pst,
-                                           float *gtab, const float *stab, int par) {
+                                           float *gtab, const float *stab, int par, unsigned long long &tgt,
+                                           bool more) {
     constexpr bool LAST = ST >= 3;
     const int tid = threadIdx.x, nthr = blockDim.x, Mloc = N * nt;
     const float *vcur = vst + par * N;
     float *vnxt = vst + (par ^ 1) * N;
     const float *ysc = ys + par * 3 * N;
     float *ysn = ys + (par ^ 1) * 3 * N;
-    // gates m, h, n of the owned neurons before the S-phase (as in the CTA kernel)
-    for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates<ST>(i, N, vcur[i], ysc, ysn, y0, acc, dt);
+    // the other CTAs' gates and maps of this stage are published
+    if (!grid_wait(g.bar, tgt, g.timeout_ns, v.err)) return false;
     if (PAIR) {
         // this stage's gate of every used pair, written by the owners before the last barrier
         const float4 *src = (const float4 *)(g.gt + (size_t)par * g.mt);
@@ -172,7 +191,15 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
             }
         }
     }
-    return grid_barrier(g.bar, g.timeout_ns, v.err);
+    tgt = grid_arrive(g.bar);
+    if (more) {
+        // the next stage's gates of the owned neurons (own data only) while
+        // the other CTAs arrive; that stage reads this one's ysn and vnxt
+        constexpr int NX = ST == 4 ? 4 : (ST + 1) & 3;
+        float *ysx = ys + par * 3 * N;
+        for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates<NX>(i, N, vnxt[i], ysn, ysx, y0, acc, dt);
+    }
+    return true;
 }
 
 template <bool HAS2, bool PAIR>
@@ -249,9 +276,20 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         }
         load_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.weight, v.syn_code, stab, tmp);
     }
-    bool ok = grid_barrier(g.bar, g.timeout_ns, v.err);
-
     const float dt = v.dt;
+    unsigned long long tgt = grid_arrive(g.bar);
+    // the first stage's gates (own data) while the other CTAs finish setting up
+    {
+        const float *ysc = ys, *vcur = vst;
+        float *ysn = ys + 3 * N;
+        if (nsteps > 0) {
+            if (v.method == PSST_METHOD_EULER)
+                for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates<4>(i, N, vcur[i], ysc, ysn, y0, acc, dt);
+            else
+                for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates<0>(i, N, vcur[i], ysc, ysn, y0, acc, dt);
+        }
+    }
+    bool ok = true;
     // record: phase of (step + 1) modulo the stride, advanced once per step
     int rec_phase = v.rec_stride > 0 ? (int)((step0 + 1) % v.rec_stride) : -1;
     for (int itn = 0; ok && itn < nsteps; ++itn) {
@@ -264,23 +302,27 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         }
         for (int i = tid; i < N; i += nthr)
             iext[i] = input_current(v, inp[i], inp[N + i], in_pulse, (long long)lo + i, step);
+        const bool more = itn + 1 < nsteps;
         if (v.method == PSST_METHOD_EULER) {
             ok = grid_stage<4, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab, itn & 1);
+                                           acc1, cur2, acc2, pst, gtab, stab, itn & 1, tgt, more);
             continue;
         }
         ok = grid_stage<0, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                       acc1, cur2, acc2, pst, gtab, stab, 0);
+                                       acc1, cur2, acc2, pst, gtab, stab, 0, tgt, true);
         if (ok)
             ok = grid_stage<1, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab, 1);
+                                           acc1, cur2, acc2, pst, gtab, stab, 1, tgt, true);
         if (ok)
             ok = grid_stage<2, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab, 0);
+                                           acc1, cur2, acc2, pst, gtab, stab, 0, tgt, true);
         if (ok)
             ok = grid_stage<3, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab, 1);
+                                           acc1, cur2, acc2, pst, gtab, stab, 1, tgt, more);
+        // the next step's input currents (own data) run before stage 0's wait
     }
+    // the last stage's (or the setup's) barrier
+    if (ok) ok = grid_wait(g.bar, tgt, g.timeout_ns, v.err);
     if (!ok) return;  // error recorded; global state keeps its value from before the call
 
     if (PAIR) {
