@@ -59,11 +59,11 @@ def lib():
             P = C.c_void_p
             _lib.orc_integrate.restype = C.c_int64
             _lib.orc_integrate.argtypes = [C.POINTER(_Net), P, C.c_int64, C.c_int64, C.c_int,
-                                           C.c_int64, P, C.c_int64]
+                                           C.c_int64, P, C.c_int64, P]
             _lib.orc_rhs.argtypes = [C.POINTER(_Net), P, P, P]
             _lib.orc_input.argtypes = [C.POINTER(_Net), C.c_int64, P]
             _lib.orc_linear_integrate.restype = C.c_int
-            _lib.orc_linear_integrate.argtypes = [C.c_int64, P, P, C.c_double, C.c_int64, C.c_int]
+            _lib.orc_linear_integrate.argtypes = [C.c_int64, P, P, C.c_double, C.c_int64, C.c_int, P]
             _lib.orc_philox4x32_10.argtypes = [P, P, P]
             _lib.orc_noise_event.restype = C.c_int
             _lib.orc_noise_event.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int64]
@@ -71,10 +71,10 @@ def lib():
             _lib.orc_steady_gates.argtypes = [C.c_double, P]
             _lib.orc_vjp.argtypes = [C.POINTER(_Net), P, P, P, P, P]
             _lib.orc_linear_adjoint.restype = C.c_int
-            _lib.orc_linear_adjoint.argtypes = [C.c_int64, P, P, C.c_double, C.c_int64, P, C.c_int]
+            _lib.orc_linear_adjoint.argtypes = [C.c_int64, P, P, C.c_double, C.c_int64, P, C.c_int, P]
             _lib.orc_adjoint.restype = C.c_int
             _lib.orc_adjoint.argtypes = [C.POINTER(_Net), P, C.c_int64, C.c_int64, C.c_int64, P, P, P, P,
-                                         C.c_int64, C.c_int]
+                                         C.c_int64, C.c_int, P]
             _lib.orc_rates_deriv.argtypes = [C.c_double, P]
             _lib.orc_transmitter.restype = C.c_double
             _lib.orc_transmitter.argtypes = [C.c_double, C.c_double, C.c_double]
@@ -83,6 +83,31 @@ def lib():
 
 def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
+
+
+def _method(order: int, tableau):
+    """(order, table) for the C entry points: order 4 (classic RK4) or 1
+    (forward Euler), or with tableau = (a, b) the explicit Runge-Kutta map
+    Y_1 = y, Y_s = y + h a[s-2] k_{s-1}, y' = y + h sum_s b[s-1] k_s
+    (a: the n_stages - 1 coefficients a_{s,s-1}; b: the n_stages weights).
+    The table array must outlive the call."""
+    if tableau is None:
+        if order not in (1, 4):
+            raise ValueError("order must be 4 or 1 (or give a tableau)")
+        return int(order), None
+    a, b = (np.atleast_1d(np.asarray(x, np.float64)) for x in tableau)
+    ns = len(b)
+    if not 1 <= ns <= 4 or len(a) != ns - 1:
+        raise ValueError("a tableau has 1..4 stages and n_stages - 1 coupling coefficients")
+    tab = np.zeros(8, np.float64)
+    tab[0] = ns
+    tab[1:ns] = a
+    tab[4:4 + ns] = b
+    return 0, tab
+
+
+def _tp(tab):
+    return None if tab is None else _ptr(tab)
 
 
 class OracleNet:
@@ -128,15 +153,17 @@ def rest_state(spec, V0: float = -65.0) -> np.ndarray:
     return y
 
 
-def integrate(spec, y0, nsteps: int, step0: int = 0, order: int = 4, rec_stride: int = 0):
-    """Returns (y_final, rec[frames, N])."""
+def integrate(spec, y0, nsteps: int, step0: int = 0, order: int = 4, rec_stride: int = 0, tableau=None):
+    """Returns (y_final, rec[frames, N]).  order 4: RK4, 1: forward Euler;
+    tableau = (a, b): that explicit Runge-Kutta map (see _method)."""
+    order, tab = _method(order, tableau)
     net = as_net(spec)
     y = np.array(y0, np.float64, copy=True)
     assert y.shape == (net.dim,)
     cap = nsteps // rec_stride + 1 if rec_stride > 0 else 0
     rec = np.zeros((max(cap, 1), net.N), np.float64)
-    got = lib().orc_integrate(C.byref(net.c), _ptr(y), int(step0), int(nsteps), int(order),
-                              int(rec_stride), _ptr(rec), int(cap))
+    got = lib().orc_integrate(C.byref(net.c), _ptr(y), int(step0), int(nsteps), order,
+                              int(rec_stride), _ptr(rec), int(cap), _tp(tab))
     if got < 0:
         raise MemoryError("oracle integrate")
     return y, rec[:got]
@@ -158,10 +185,11 @@ def input_current(spec, step: int) -> np.ndarray:
     return iext
 
 
-def linear_integrate(A, y0, h: float, nsteps: int, order: int = 4) -> np.ndarray:
+def linear_integrate(A, y0, h: float, nsteps: int, order: int = 4, tableau=None) -> np.ndarray:
+    order, tab = _method(order, tableau)
     A = np.ascontiguousarray(A, np.float64)
     y = np.array(y0, np.float64, copy=True)
-    if lib().orc_linear_integrate(len(y), _ptr(A), _ptr(y), float(h), int(nsteps), int(order)):
+    if lib().orc_linear_integrate(len(y), _ptr(A), _ptr(y), float(h), int(nsteps), order, _tp(tab)):
         raise MemoryError("oracle linear integrate")
     return y
 
@@ -184,19 +212,22 @@ def vjp(spec, y, v, step: int = 0):
     return u, gw, gnp.reshape(-1, 9)
 
 
-def linear_adjoint(A, y0, h: float, nsteps: int, lam_T, order: int = 4) -> np.ndarray:
+def linear_adjoint(A, y0, h: float, nsteps: int, lam_T, order: int = 4, tableau=None) -> np.ndarray:
+    order, tab = _method(order, tableau)
     A = np.ascontiguousarray(A, np.float64)
     y0 = np.ascontiguousarray(y0, np.float64)
     lam = np.array(lam_T, np.float64, copy=True)
-    if lib().orc_linear_adjoint(len(y0), _ptr(A), _ptr(y0), float(h), int(nsteps), _ptr(lam), int(order)):
+    if lib().orc_linear_adjoint(len(y0), _ptr(A), _ptr(y0), float(h), int(nsteps), _ptr(lam), order, _tp(tab)):
         raise MemoryError("oracle linear adjoint")
     return lam
 
 
-def adjoint(spec, y0, nsteps: int, dLdV, rec_stride: int, step0: int = 0, ckpt: int = 100, order: int = 4):
+def adjoint(spec, y0, nsteps: int, dLdV, rec_stride: int, step0: int = 0, ckpt: int = 100, order: int = 4,
+            tableau=None):
     """Gradient of L = sum_f sum_i dLdV[f, i] V_i(frame f) over the RK4
-    (order 4) or Euler (order 1) trajectory; returns (dL/dy0, dL/dw,
-    dL/dnparams[n_types, 9])."""
+    (order 4), Euler (order 1) or tableau trajectory; returns (dL/dy0,
+    dL/dw, dL/dnparams[n_types, 9])."""
+    order, tab = _method(order, tableau)
     net = as_net(spec)
     y0 = np.ascontiguousarray(y0, np.float64)
     dLdV = np.ascontiguousarray(dLdV, np.float64)
@@ -204,7 +235,7 @@ def adjoint(spec, y0, nsteps: int, dLdV, rec_stride: int, step0: int = 0, ckpt: 
     gw = np.zeros(net.S, np.float64)
     gnp = np.zeros(net.nparams.size, np.float64)
     if lib().orc_adjoint(C.byref(net.c), _ptr(y0), int(step0), int(nsteps), int(rec_stride), _ptr(dLdV),
-                         _ptr(gy), _ptr(gw), _ptr(gnp), int(ckpt), int(order)):
+                         _ptr(gy), _ptr(gw), _ptr(gnp), int(ckpt), order, _tp(tab)):
         raise MemoryError("oracle adjoint")
     return gy, gw, gnp.reshape(-1, 9)
 

@@ -14,10 +14,13 @@
  *     constraints", item 1: synaptic variables stored sparsely);
  *   - the recursion X_{i+1} = F(X_i, t_i, eps_i) with eps_i read as the step
  *     dt and F the classic fourth-order Runge-Kutta map (Sec. "Brain
- *     simulations ...", RK4 paragraph) or forward Euler (Eq. euler);
+ *     simulations ...", RK4 paragraph), forward Euler (Eq. euler), or an
+ *     explicit Runge-Kutta map of a given tableau whose stage s uses only
+ *     the slope of stage s-1 (the family both of the paper's methods
+ *     belong to);
  *   - the Philox4x32-10 counter-based generator of Salmon et al., SC'11,
  *     used for shot-noise input;
- *   - the discrete adjoint (transpose) of the RK4 map over the full
+ *   - the discrete adjoint (transpose) of each of these maps over the full
  *     per-synapse state, with the Jacobian-transpose products of the
  *     right-hand side derived by hand, giving gradients of a voltage-trace
  *     functional with respect to the initial state, the weights and the
@@ -216,9 +219,34 @@ static void euler_step(int64_t d, double h, rhs_fn f, void *ctx, double *y, doub
     for (int64_t i = 0; i < d; ++i) y[i] = y[i] + h * work[i];
 }
 
-static void take_step(int order, int64_t d, double h, rhs_fn f, void *ctx, double *y, double *work)
+/* Explicit Runge-Kutta map of a tableau whose only nonzero coupling
+   coefficients are a_{s,s-1}.  tab = {n_stages (1..4), a_2, a_3, a_4,
+   b_1, b_2, b_3, b_4}:
+     Y_1 = y,  Y_s = y + h a_s k_{s-1},  k_s = f(Y_s),
+     y_{n+1} = y + h sum_s b_s k_s. */
+static void tab_step(const double *tab, int64_t d, double h, rhs_fn f, void *ctx, double *y, double *work)
 {
-    if (order == 1) euler_step(d, h, f, ctx, y, work);
+    const int ns = (int)tab[0];
+    double *k = work, *Y = work + d, *sum = work + 2 * d;
+    for (int64_t i = 0; i < d; ++i) {
+        Y[i] = y[i];
+        sum[i] = 0.0;
+    }
+    for (int st = 1; st <= ns; ++st) {
+        if (st > 1)
+            for (int64_t i = 0; i < d; ++i) Y[i] = y[i] + h * tab[st - 1] * k[i];
+        f(ctx, Y, k);
+        for (int64_t i = 0; i < d; ++i) sum[i] += tab[3 + st] * k[i];
+    }
+    for (int64_t i = 0; i < d; ++i) y[i] = y[i] + h * sum[i];
+}
+
+/* order 4: classic RK4; order 1: forward Euler; order 0: the tableau tab */
+static void take_step(int order, const double *tab, int64_t d, double h, rhs_fn f, void *ctx, double *y,
+                      double *work)
+{
+    if (order == 0) tab_step(tab, d, h, f, ctx, y, work);
+    else if (order == 1) euler_step(d, h, f, ctx, y, work);
     else rk4_step(d, h, f, ctx, y, work);
 }
 
@@ -238,12 +266,13 @@ static void lin_rhs(void *c, const double *y, double *dy)
 
 /* dy/dt = A y, nsteps steps of size h, through the same stepper the network
    integration uses.  Returns 0, or -1 if out of memory. */
-int orc_linear_integrate(int64_t d, const double *A, double *y, double h, int64_t nsteps, int order)
+int orc_linear_integrate(int64_t d, const double *A, double *y, double h, int64_t nsteps, int order,
+                         const double *tab)
 {
     double *work = (double *)malloc(sizeof(double) * 5 * (size_t)d);
     if (!work) return -1;
     lin_ctx c = {d, A};
-    for (int64_t k = 0; k < nsteps; ++k) take_step(order, d, h, lin_rhs, &c, y, work);
+    for (int64_t k = 0; k < nsteps; ++k) take_step(order, tab, d, h, lin_rhs, &c, y, work);
     free(work);
     return 0;
 }
@@ -265,7 +294,7 @@ static void net_rhs(void *c, const double *y, double *dy)
    rec_cap frames have been written.  Returns the number of frames written,
    or -1 on allocation failure. */
 int64_t orc_integrate(const orc_net *net, double *y, int64_t step0, int64_t nsteps, int order,
-                      int64_t rec_stride, double *rec, int64_t rec_cap)
+                      int64_t rec_stride, double *rec, int64_t rec_cap, const double *tab)
 {
     const int64_t d = 4 * net->N + 2 * net->S;
     double *work = (double *)malloc(sizeof(double) * (5 * (size_t)d + (size_t)net->N + 1));
@@ -275,7 +304,7 @@ int64_t orc_integrate(const orc_net *net, double *y, int64_t step0, int64_t nste
     int64_t frames = 0;
     for (int64_t k = step0; k < step0 + nsteps; ++k) {
         orc_input(net, k, iext);
-        take_step(order, d, net->dt, net_rhs, &c, y, work);
+        take_step(order, tab, d, net->dt, net_rhs, &c, y, work);
         if (rec_stride > 0 && (k + 1) % rec_stride == 0 && frames < rec_cap) {
             memcpy(rec + frames * net->N, y, sizeof(double) * (size_t)net->N);
             ++frames;
@@ -449,10 +478,38 @@ static void euler_adjoint_step(int64_t d, double hstep, vjp_fn g, void *ctx, con
     for (int64_t i = 0; i < d; ++i) lam[i] += Yb[i];
 }
 
-static void adjoint_step(int order, int64_t d, double hstep, rhs_fn f, vjp_fn g, void *ctx, const double *y,
-                         double *lam, double *work)
+/* Reverse of one step of tab_step's map: with the stages Y_s recomputed
+   forward, the stage adjoints are, for s = n_stages down to 1,
+     kb_s = h b_s lam + h a_{s+1} Yb_{s+1}  (the second term absent for the
+            last stage),   Yb_s = J(Y_s)^T kb_s,
+   and lam_n = lam + sum_s Yb_s; the vjp callback adds (df/dtheta)^T kb_s. */
+static void tab_adjoint_step(const double *tab, int64_t d, double hstep, rhs_fn f, vjp_fn g, void *ctx,
+                             const double *y, double *lam, double *work)
 {
-    if (order == 1) euler_adjoint_step(d, hstep, g, ctx, y, lam, work);
+    const int ns = (int)tab[0];
+    double *Ys = work, *k = work + 4 * d, *kb = work + 5 * d, *Yb = work + 6 * d, *Ysum = work + 7 * d;
+    for (int64_t i = 0; i < d; ++i) Ys[i] = y[i];
+    for (int st = 2; st <= ns; ++st) {
+        f(ctx, Ys + (st - 2) * d, k);
+        for (int64_t i = 0; i < d; ++i) Ys[(st - 1) * d + i] = y[i] + hstep * tab[st - 1] * k[i];
+    }
+    for (int64_t i = 0; i < d; ++i) Ysum[i] = 0.0;
+    for (int st = ns; st >= 1; --st) {
+        for (int64_t i = 0; i < d; ++i) {
+            kb[i] = hstep * tab[3 + st] * lam[i];
+            if (st < ns) kb[i] += hstep * tab[st] * Yb[i];
+        }
+        g(ctx, Ys + (st - 1) * d, kb, Yb);
+        for (int64_t i = 0; i < d; ++i) Ysum[i] += Yb[i];
+    }
+    for (int64_t i = 0; i < d; ++i) lam[i] += Ysum[i];
+}
+
+static void adjoint_step(int order, const double *tab, int64_t d, double hstep, rhs_fn f, vjp_fn g, void *ctx,
+                         const double *y, double *lam, double *work)
+{
+    if (order == 0) tab_adjoint_step(tab, d, hstep, f, g, ctx, y, lam, work);
+    else if (order == 1) euler_adjoint_step(d, hstep, g, ctx, y, lam, work);
     else rk4_adjoint_step(d, hstep, f, g, ctx, y, lam, work);
 }
 
@@ -467,11 +524,11 @@ static void lin_vjp(void *c, const double *y, const double *v, double *u)
     }
 }
 
-/* Adjoint of nsteps RK4 (order 4) or Euler (order 1) steps of dy/dt = A y:
+/* Adjoint of nsteps RK4 (order 4), Euler (order 1) or tableau (order 0, tab) steps of dy/dt = A y:
    lam (adjoint of y at the end) is carried back to the adjoint of the
    initial state. */
 int orc_linear_adjoint(int64_t d, const double *A, const double *y0, double h, int64_t nsteps, double *lam,
-                       int order)
+                       int order, const double *tab)
 {
     double *traj = (double *)malloc(sizeof(double) * (size_t)d * (size_t)(nsteps + 1));
     double *work = (double *)malloc(sizeof(double) * 8 * (size_t)d);
@@ -480,10 +537,10 @@ int orc_linear_adjoint(int64_t d, const double *A, const double *y0, double h, i
     memcpy(traj, y0, sizeof(double) * (size_t)d);
     for (int64_t k = 0; k < nsteps; ++k) {
         memcpy(traj + (k + 1) * d, traj + k * d, sizeof(double) * (size_t)d);
-        take_step(order, d, h, lin_rhs, &c, traj + (k + 1) * d, work);
+        take_step(order, tab, d, h, lin_rhs, &c, traj + (k + 1) * d, work);
     }
     for (int64_t k = nsteps - 1; k >= 0; --k)
-        adjoint_step(order, d, h, lin_rhs, lin_vjp, &c, traj + k * d, lam, work);
+        adjoint_step(order, tab, d, h, lin_rhs, lin_vjp, &c, traj + k * d, lam, work);
     free(traj);
     free(work);
     return 0;
@@ -508,11 +565,12 @@ static void net_vjp(void *c, const double *y, const double *v, double *u)
    index step0; frame f is the state after global step k with
    k % rec_stride == 0, in order).  Outputs the adjoint of y0 (grad_y0[dim]),
    dL/dw (grad_w[S]) and dL/d(neuron-type parameters) (grad_np, row per
-   type), for RK4 (order 4) or Euler (order 1) steps.  Memory: states are
+   type), for RK4 (order 4), Euler (order 1) or tableau (order 0, tab) steps.  Memory: states are
    kept every `ckpt` steps and each segment is recomputed.  Returns 0, or -1
    on allocation failure. */
 int orc_adjoint(const orc_net *net, const double *y0, int64_t step0, int64_t nsteps, int64_t rec_stride,
-                const double *dLdV, double *grad_y0, double *grad_w, double *grad_np, int64_t ckpt, int order)
+                const double *dLdV, double *grad_y0, double *grad_w, double *grad_np, int64_t ckpt, int order,
+                const double *tab)
 {
     const int64_t d = 4 * net->N + 2 * net->S;
     if (ckpt < 1) ckpt = 1;
@@ -533,7 +591,7 @@ int orc_adjoint(const orc_net *net, const double *y0, int64_t step0, int64_t nst
         memcpy(y, y0, sizeof(double) * (size_t)d);
         for (int64_t k = 0; k < nsteps; ++k) {
             orc_input(net, step0 + k, iext);
-            take_step(order, d, net->dt, net_rhs, &fc, y, work);
+            take_step(order, tab, d, net->dt, net_rhs, &fc, y, work);
             if ((k + 1) % ckpt == 0) memcpy(cks + ((k + 1) / ckpt) * d, y, sizeof(double) * (size_t)d);
         }
     }
@@ -557,11 +615,11 @@ int orc_adjoint(const orc_net *net, const double *y0, int64_t step0, int64_t nst
         for (int64_t k = k0; k < k1 - 1; ++k) {
             memcpy(seg + (k - k0 + 1) * d, seg + (k - k0) * d, sizeof(double) * (size_t)d);
             orc_input(net, step0 + k, iext);
-            take_step(order, d, net->dt, net_rhs, &fc, seg + (k - k0 + 1) * d, work);
+            take_step(order, tab, d, net->dt, net_rhs, &fc, seg + (k - k0 + 1) * d, work);
         }
         for (int64_t k = k1 - 1; k >= k0; --k) {
             orc_input(net, step0 + k, iext);
-            adjoint_step(order, d, net->dt, net_rhs_adj, net_vjp, &ac, seg + (k - k0) * d, lam, work);
+            adjoint_step(order, tab, d, net->dt, net_rhs_adj, net_vjp, &ac, seg + (k - k0) * d, lam, work);
             /* state y_{step0+k} is a frame when its global index qualifies */
             if (rec_stride > 0 && k > 0 && (step0 + k) % rec_stride == 0 && frame >= 0) {
                 for (int64_t i = 0; i < net->N; ++i) lam[i] += dLdV[frame * net->N + i];

@@ -91,13 +91,17 @@ def test_linear_adjoint_closed_form(order):
                                atol=1e-13)
 
 
-def _loss(net, y0, nsteps, g, stride, step0=0, order=4):
-    _, rec = oracle.integrate(net, y0, nsteps, step0=step0, rec_stride=stride, order=order)
+def _loss(net, y0, nsteps, g, stride, step0=0, order=4, tableau=None):
+    _, rec = oracle.integrate(net, y0, nsteps, step0=step0, rec_stride=stride, order=order, tableau=tableau)
     return float(np.sum(rec * g))
 
 
-@pytest.mark.parametrize("order", [4, 1])
-def test_trajectory_gradient_vs_fd(order):
+# Heun's third-order method: a_21 = 1/3, a_32 = 2/3, b = (1/4, 0, 3/4)
+HEUN3 = ([1.0 / 3.0, 2.0 / 3.0], [0.25, 0.0, 0.75])
+
+
+@pytest.mark.parametrize("order,tableau", [(4, None), (1, None), (0, HEUN3)])
+def test_trajectory_gradient_vs_fd(order, tableau):
     spec = _small_al(seed=4)
     net = oracle.OracleNet(spec)
     rng = np.random.default_rng(2)
@@ -106,14 +110,14 @@ def test_trajectory_gradient_vs_fd(order):
     nsteps, stride, step0 = 400, 10, 3
     frames = sum(1 for k in range(step0 + 1, step0 + nsteps + 1) if k % stride == 0)
     g = rng.standard_normal((frames, net.N))
-    gy, gw, gnp = oracle.adjoint(net, y0, nsteps, g, stride, step0=step0, ckpt=37, order=order)
+    gy, gw, gnp = oracle.adjoint(net, y0, nsteps, g, stride, step0=step0, ckpt=37, order=order, tableau=tableau)
 
     def fd(setter, x0):
         h = 1e-6 * max(1.0, abs(x0))
         setter(x0 + h)
-        lp = _loss(net, y0, nsteps, g, stride, step0, order)
+        lp = _loss(net, y0, nsteps, g, stride, step0, order, tableau)
         setter(x0 - h)
-        lm = _loss(net, y0, nsteps, g, stride, step0, order)
+        lm = _loss(net, y0, nsteps, g, stride, step0, order, tableau)
         setter(x0)
         return (lp - lm) / (2 * h)
 
@@ -121,7 +125,7 @@ def test_trajectory_gradient_vs_fd(order):
     # central differences with step h carry a rounding error of about
     # eps * sum|terms of L| / h (h = 1e-6 relative: ~1e-6 absolute here),
     # which the bound for the smallest weight gradients must admit
-    _, rec = oracle.integrate(net, y0, nsteps, step0=step0, rec_stride=stride, order=order)
+    _, rec = oracle.integrate(net, y0, nsteps, step0=step0, rec_stride=stride, order=order, tableau=tableau)
     fd_noise = 4.0 * np.finfo(float).eps * float(np.sum(np.abs(rec * g))) / 1e-6
     for k in rng.choice(net.S, 10, replace=False):
         want = fd(lambda x: net.w.__setitem__(k, x), net.w[k])

@@ -1,6 +1,6 @@
 """Plants plausible mistakes in a copy of the oracle (CPU only) and checks
-that the pins in test_oracle_pins.py and test_oracle_adjoint.py catch every
-one of them.
+that the pins in test_oracle_pins.py, test_oracle_adjoint.py and
+test_oracle_tableau.py catch every one of them.
 
 The Philox round structure is deliberately absent: it is pinned only
 statistically, so its parity with the published generator is unpinned.
@@ -43,6 +43,14 @@ MUTANTS = [
     ("out[3] = r[3] * (1.0 - r[3]) / 10.0;", "out[3] = r[3] * (1.0 - r[3]) / 20.0;"),  # constant
     ("gp[P_GK] += -q * n4 * (V[i] - p[P_EK]);", "gp[P_GK] += q * n4 * (V[i] - p[P_EK]);"),  # sign
     ("if (g) g->gw[k] += -q * G * (V[i] - E);", "if (g) g->gw[k] += -q * (V[i] - E);"),  # dropped factor
+    # tableau map and its adjoint
+    ("Y[i] = y[i] + h * tab[st - 1] * k[i];", "Y[i] = y[i] + h * tab[st] * k[i];"),  # coefficient index
+    ("sum[i] += tab[3 + st] * k[i];", "sum[i] += k[i];"),                  # dropped weight
+    ("if (st < ns) kb[i] += hstep * tab[st] * Yb[i];",
+     "if (st < ns) kb[i] += hstep * tab[st - 1] * Yb[i];"),                # coupling index
+    ("kb[i] = hstep * tab[3 + st] * lam[i];", "kb[i] = hstep * lam[i];"),  # dropped weight
+    ("Ys[(st - 1) * d + i] = y[i] + hstep * tab[st - 1] * k[i];",
+     "Ys[(st - 1) * d + i] = y[i] + hstep * k[i];"),                       # dropped coefficient
 ]
 
 
@@ -60,6 +68,7 @@ def test_pins_catch_planted_mistake(tmp_path, old, new):
     assert text.count(old) == 1, old
     src.write_text(text.replace(old, new))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py"],
+                        "tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py",
+                        "tests/test_oracle_tableau.py"],
                        cwd=tmp_path, capture_output=True, text=True)
     assert r.returncode != 0, "mutant survived: " + new + "\n" + r.stdout[-400:]
