@@ -64,6 +64,12 @@ extern "C" {
    Euler's method, Eq. euler, and the fourth-order Runge-Kutta method). */
 #define PSST_METHOD_RK4 0    /* classic RK4 (c = 0, 1/2, 1/2, 1; b = 1/6, 1/3, 1/3, 1/6) */
 #define PSST_METHOD_EULER 1  /* forward Euler: y_{n+1} = y_n + dt f(y_n, t_n) */
+#define PSST_METHOD_TABLEAU 2 /* explicit Runge-Kutta map of the family both methods belong to, given by
+                                 rk_stages, rk_a and rk_b: Y_1 = y, Y_s = y + dt a_s k_{s-1},
+                                 k_s = f(Y_s), y_{n+1} = y + dt sum_s b_s k_s (e.g. midpoint,
+                                 Heun, Ralston, Heun's third-order method; the classic RK4 and
+                                 the one-stage b = 1 tableau give PSST_METHOD_RK4 and _EULER bit
+                                 for bit) */
 
 /* Execution modes. */
 #define PSST_MODE_AUTO 0  /* CTA mode when every network fits one CTA, else grid */
@@ -116,11 +122,14 @@ typedef struct {
     int32_t gate_mode;             /* 0: one gate per (presynaptic neuron, type) pair whenever all
                                       its synapses' gates are equal (bitwise-identical results,
                                       less work), else one per synapse; 1: always one per synapse */
-    int32_t method;                /* PSST_METHOD_RK4 (0) or PSST_METHOD_EULER (1) */
+    int32_t method;                /* PSST_METHOD_RK4 (0), PSST_METHOD_EULER (1) or PSST_METHOD_TABLEAU (2) */
     int32_t min_cluster;           /* CTA mode: spread every network of at least 2 x min_cluster neurons
                                       over a cluster of at least min_cluster CTAs (1, 2 or 4; same
                                       results, shorter steps when SMs are idle); 0 = chosen by
                                       psst_autotune (default 1) */
+    int32_t rk_stages;             /* PSST_METHOD_TABLEAU: stages (1..4); ignored otherwise */
+    float rk_a[3];                 /* a_2, a_3, a_4: stage s+1 starts at y + dt a_{s+1} k_s (finite) */
+    float rk_b[4];                 /* b_1 .. b_{rk_stages}: weights of the step (finite, not all 0) */
 } psst_network_desc;
 
 typedef struct {
@@ -240,9 +249,9 @@ int psst_set_neuron_params(psst_net *h, const float *p, size_t n, int on_device,
    (ceil(max_steps / every) full states) is allocated here. */
 int psst_record_checkpoints(psst_net *h, int32_t every, int64_t max_steps);
 
-/* Discrete adjoint of the integration map -- RK4, or forward Euler
-   (Eq. euler) when the handle's method is PSST_METHOD_EULER -- (no
-   counterpart in the paper; the differentiated form).  For the n_steps steps that a psst_integrate call
+/* Discrete adjoint of the integration map -- RK4, forward Euler (Eq. euler)
+   or the handle's tableau, by its method -- (no counterpart in the paper;
+   the differentiated form).  For the n_steps steps that a psst_integrate call
    made now would take -- from the current state and step index -- computes
    the gradient of
        L = sum_f sum_i dL_dV[f][i] * V_i(frame f)

@@ -22,7 +22,8 @@
 //   kb1 = h/6 lam + h/2 Yb2, Yb1 = J(Y1)^T kb1
 //   lam_n = lam + Yb1 + Yb2 + Yb3 + Yb4;  theta_bar += sum_s (df/dtheta)^T kb_s.
 // Forward Euler (Eq. euler) is the one-stage case: kb1 = h lam,
-// lam_n = lam + J(y_n)^T kb1.
+// lam_n = lam + J(y_n)^T kb1.  A tableau (stage s starts at
+// y + h a_s k_{s-1}, weights b_s) has kb_s = h b_s lam + h a_{s+1} Yb_{s+1}.
 // States are checkpointed every `ckpt` steps in a first forward pass; each
 // segment is recomputed forward, keeping every step's stages in global
 // memory, then swept backward from those stages.
@@ -131,9 +132,9 @@ struct AdjNet {
 // ---------------------------------------------------------------- forward
 
 // Forward of one step of the reduced model from S.y (step `step`) with NST
-// stages (4: RK4, 1: forward Euler), storing the stages' values; on return
-// S.y holds the next state.
-template <bool STORE, int NST>
+// stages (4: RK4, 1: forward Euler; TAB: the handle's tableau of NST
+// stages), storing the stages' values; on return S.y holds the next state.
+template <bool STORE, int NST, bool TAB>
 __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, const float *stab, long long step,
                          float dt) {
     const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M;
@@ -182,9 +183,10 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
             S.pb[it] = B;
         }
         __syncthreads();
-        const float WGT = (st == 0 || st == 3) ? 1.0f : 2.0f;
-        const float cnext = (st == 2) ? dt : 0.5f * dt;
-        const float dt6 = NST == 1 ? dt : dt * (1.0f / 6.0f);  // h b_s of the last stage's sum
+        const float WGT = TAB ? v.rk_w[st] : (st == 0 || st == 3) ? 1.0f : 2.0f;
+        const float cnext = TAB ? (st < 3 ? v.rk_c[st] * dt : 0.0f) : (st == 2) ? dt : 0.5f * dt;
+        const float dt6 = TAB ? v.rk_beta * dt : NST == 1 ? dt : dt * (1.0f / 6.0f);  // scale of the step's sum
+        const float W0 = TAB ? v.rk_w[0] : 1.0f;  // weight of the first stage's slope
         for (int i = tid; i < N; i += nthr) {
             float A = 0.0f, B = 0.0f;
             for (int it = S.ib[i]; it < S.ib[i + 1]; ++it) {
@@ -210,7 +212,7 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
 #pragma unroll
             for (int x = 0; x < 4; ++x) {
                 const int ix = x * N + i;
-                const float ac = (st == 0) ? d[x] : fmaf(WGT, d[x], S.acc[ix]);
+                const float ac = (st == 0) ? W0 * d[x] : fmaf(WGT, d[x], S.acc[ix]);
                 if (st < NST - 1) {
                     S.acc[ix] = ac;
                     stg[x][(st + 1) * N + i] = fmaf(cnext, d[x], S.y[ix]);
@@ -227,8 +229,8 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
                 const float dr = sp[SP_A] * T * (1.0f - rs) - sp[SP_B] * rs;
                 const float ds = sp[SP_KIND] != 0.0f ? sp[SP_K3] * rs - sp[SP_K4] * ss : 0.0f;
                 const int ir = 4 * N + p, is = 4 * N + M + p;
-                const float ar = (st == 0) ? dr : fmaf(WGT, dr, S.acc[ir]);
-                const float as = (st == 0) ? ds : fmaf(WGT, ds, S.acc[is]);
+                const float ar = (st == 0) ? W0 * dr : fmaf(WGT, dr, S.acc[ir]);
+                const float as = (st == 0) ? W0 * ds : fmaf(WGT, ds, S.acc[is]);
                 float rn, sn;
                 if (st < NST - 1) {
                     S.acc[ir] = ar;
@@ -292,16 +294,15 @@ __device__ __forceinline__ void column_sums(const AdjNet &a, const AdjSmem &S, i
     }
 }
 
-// Reverse of the step whose NST stages fwd_step<true, NST> just stored: lam
-// holds the adjoint of y_{n+1} on entry and of y_n on exit (before the frame
-// term).
+// Reverse of the step whose NST stages fwd_step<true, NST, .> just stored:
+// lam holds the adjoint of y_{n+1} on entry and of y_n on exit (before the
+// frame term).  cb[s] = h b_s, ca[s] = h a_{s+1} (the factor of stage s's
+// slope in stage s+1's start).
 template <int NST>
-__device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, float dt, float4 *gpart) {
+__device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, const float *cb, const float *ca,
+                         float4 *gpart) {
     const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M, K = a.K, ni = a.n_items;
     const int D = 4 * N + 2 * M;
-    // h b_s and h a_{s+1,s} (Euler: b_1 = 1, no later stage)
-    const float cb[4] = {NST == 1 ? dt : dt / 6.0f, dt / 3.0f, dt / 3.0f, dt / 6.0f};
-    const float ca[4] = {0.5f * dt, 0.5f * dt, dt, 0.0f};
 #pragma unroll 1
     for (int st = NST - 1; st >= 0; --st) {
         // A) owners: stage adjoint kb, neuron-local products, parameter gradients
@@ -465,28 +466,29 @@ __host__ __device__ inline long long adj_step_floats(int nst, long long N, long 
     return (long long)nst * (6 * N + 3 * M);
 }
 
-// Copy of stage 0 of the stage arrays (sV .. sfv, each [4][len]) to or from
-// a compact block of 6N + 3M floats (the one-stage method's step record).
+// Copy of the first nst stages of the stage arrays (sV .. sfv, each
+// [4][len], stage-major) to or from a compact block of nst (6N + 3M) floats
+// (the step record of a method with fewer than four stages).
 template <bool TO_BLOCK>
-__device__ void copy_stage0(float *stages, float *blk, int N, int M) {
-    const int tot = 6 * N + 3 * M;
+__device__ void copy_stages(float *stages, float *blk, int N, int M, int nst) {
+    const int nN = nst * N, nM = nst * M, tot = 6 * nN + 3 * nM;
     for (int q = threadIdx.x; q < tot; q += blockDim.x) {
         int at;
-        if (q < 4 * N) {
-            at = 4 * N * (q / N) + q % N;  // V, m, h, n
-        } else if (q < 4 * N + 3 * M) {
-            const int r = q - 4 * N;
-            at = 16 * N + 4 * M * (r / M) + r % M;  // r, s, G
+        if (q < 4 * nN) {
+            at = 4 * N * (q / nN) + q % nN;  // V, m, h, n
+        } else if (q < 4 * nN + 3 * nM) {
+            const int r = q - 4 * nN;
+            at = 16 * N + 4 * M * (r / nM) + r % nM;  // r, s, G
         } else {
-            const int r = q - 4 * N - 3 * M;
-            at = 16 * N + 12 * M + 4 * N * (r / N) + r % N;  // A, f_V
+            const int r = q - 4 * nN - 3 * nM;
+            at = 16 * N + 12 * M + 4 * N * (r / nN) + r % nN;  // A, f_V
         }
         if (TO_BLOCK) blk[q] = stages[at];
         else stages[at] = blk[q];
     }
 }
 
-template <int NST>
+template <int NST, bool TAB>
 __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av, long long step0, int nsteps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float stab[PSST_MAX_SYN_TYPES * PSST_SYN_NPARAM];
@@ -613,12 +615,20 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     }
 
     // the stage arrays form one contiguous block (sV .. sfv) of stage_floats;
-    // a step keeps step_floats of it (all of it for RK4, stage 0 for Euler)
+    // a step keeps step_floats of it (its NST stages)
     const int stage_floats = 4 * (6 * N + 3 * M);
     const int step_floats = (int)adj_step_floats(NST, N, M);
     float4 *stage_blk = (float4 *)S.sV;
     const int ckpt = av.ckpt_every;
     const float dt = v.dt;
+    // h b_s and h a_{s+1} of the method (RK4; Euler: b_1 = 1; or the tableau)
+    float cb[4] = {NST == 1 ? dt : dt / 6.0f, dt / 3.0f, dt / 3.0f, dt / 6.0f};
+    float ca[4] = {0.5f * dt, 0.5f * dt, dt, 0.0f};
+    if (TAB)
+        for (int q = 0; q < 4; ++q) {
+            cb[q] = v.rk_beta * v.rk_w[q] * dt;
+            ca[q] = q < 3 ? v.rk_c[q] * dt : 0.0f;
+        }
     // the two CTAs of the network's cluster: rank 0 recomputes segments
     // forward, rank 1 sweeps them backward and owns the gradients
     const bool fwd_cta = cluster_rank() == 0;
@@ -636,7 +646,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         for (int n = 0; n < nsteps; ++n) {
             if (n % ckpt == 0)
                 for (int q = tid; q < a.R; q += nthr) ck[(long long)(n / ckpt) * a.R + q] = S.y[q];
-            fwd_step<false, NST>(v, a, S, stab, step0 + n, dt);
+            fwd_step<false, NST, TAB>(v, a, S, stab, step0 + n, dt);
         }
     }
     // frames: global steps k in (step0, step0 + nsteps] with k % stride == 0
@@ -660,12 +670,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         }
         float *seg = seg0 + (long long)(c & 1) * seg_buf;
         for (int n = k0; n < k1; ++n) {
-            fwd_step<true, NST>(v, a, S, stab, step0 + n, dt);
+            fwd_step<true, NST, TAB>(v, a, S, stab, step0 + n, dt);
             float *dst = seg + (long long)(n - k0) * step_floats;
             if (NST == 4) {
                 for (int q = tid; q < stage_floats / 4; q += nthr) ((float4 *)dst)[q] = stage_blk[q];
             } else {
-                copy_stage0<true>(S.sV, dst, N, M);
+                copy_stages<true>(S.sV, dst, N, M, NST);
             }
             __syncthreads();
         }
@@ -679,10 +689,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
             if (NST == 4) {
                 for (int q = tid; q < stage_floats / 4; q += nthr) stage_blk[q] = ((const float4 *)src)[q];
             } else {
-                copy_stage0<false>(S.sV, (float *)src, N, M);
+                copy_stages<false>(S.sV, (float *)src, N, M, NST);
             }
             __syncthreads();
-            rev_step<NST>(a, S, stab, dt, gpart);
+            rev_step<NST>(a, S, stab, cb, ca, gpart);
             if (stride > 0 && n > 0 && (step0 + n) % stride == 0 && frame >= 0) {
                 for (int i = tid; i < N; i += nthr) S.lam[i] += dl[(long long)frame * v.N + a.n0 + i];
                 --frame;
@@ -742,8 +752,9 @@ __global__ void adj_reduce_types(const int *neuron_type, long long N, const doub
 
 }  // namespace
 
-long long adj_segment_floats(int method, int N, int nt) {
-    return adj_step_floats(method == PSST_METHOD_EULER ? 1 : 4, N, (long long)N * nt);
+long long adj_segment_floats(int method, int rk_ns, int N, int nt) {
+    const int nst = method == PSST_METHOD_EULER ? 1 : method == PSST_METHOD_TABLEAU ? rk_ns : 4;
+    return adj_step_floats(nst, N, (long long)N * nt);
 }
 
 long long adj_smem_need(int N, int nt, int n_items, int K, bool col_warp) {
@@ -752,8 +763,14 @@ long long adj_smem_need(int N, int nt, int n_items, int K, bool col_warp) {
 
 cudaError_t adj_launch(const NetView &v, const AdjView &av, long long step0, int nsteps, int smem, int n_types,
                        float *grad_np, cudaStream_t stream) {
-    // RK4 (four stages a step) or forward Euler (one)
-    void (*kern)(NetView, AdjView, long long, int) = v.method == PSST_METHOD_EULER ? adj_kernel<1> : adj_kernel<4>;
+    // RK4 (four stages a step), forward Euler (one) or a tableau of 1..4 stages
+    void (*kern)(NetView, AdjView, long long, int) = v.method == PSST_METHOD_EULER ? adj_kernel<1, false>
+                                                                                    : adj_kernel<4, false>;
+    if (v.method == PSST_METHOD_TABLEAU)
+        kern = v.rk_ns == 1   ? adj_kernel<1, true>
+               : v.rk_ns == 2 ? adj_kernel<2, true>
+               : v.rk_ns == 3 ? adj_kernel<3, true>
+                              : adj_kernel<4, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     // one cluster of two CTAs per network: forward recompute and reverse sweep

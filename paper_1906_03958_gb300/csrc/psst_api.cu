@@ -285,8 +285,19 @@ int validate(const psst_network_desc *d) {
     if (d->gate_mode < 0 || d->gate_mode > 1) return fail(PSST_ERR_INVALID_ARG, "gate_mode must be 0 or 1");
     if (d->min_cluster != 0 && d->min_cluster != 1 && d->min_cluster != 2 && d->min_cluster != 4)
         return fail(PSST_ERR_INVALID_ARG, "min_cluster must be 0, 1, 2 or 4");
-    if (d->method != PSST_METHOD_RK4 && d->method != PSST_METHOD_EULER)
-        return fail(PSST_ERR_INVALID_ARG, "method must be PSST_METHOD_RK4 (0) or PSST_METHOD_EULER (1)");
+    if (d->method != PSST_METHOD_RK4 && d->method != PSST_METHOD_EULER && d->method != PSST_METHOD_TABLEAU)
+        return fail(PSST_ERR_INVALID_ARG,
+                    "method must be PSST_METHOD_RK4 (0), PSST_METHOD_EULER (1) or PSST_METHOD_TABLEAU (2)");
+    if (d->method == PSST_METHOD_TABLEAU) {
+        if (d->rk_stages < 1 || d->rk_stages > 4) return fail(PSST_ERR_INVALID_ARG, "rk_stages must be 1..4");
+        bool any = false;
+        for (int q = 0; q < d->rk_stages; ++q) {
+            if (!std::isfinite(d->rk_b[q]) || (q > 0 && !std::isfinite(d->rk_a[q - 1])))
+                return fail(PSST_ERR_INVALID_ARG, "rk_a / rk_b must be finite (stage %d)", q + 1);
+            any |= d->rk_b[q] != 0.0f;
+        }
+        if (!any) return fail(PSST_ERR_INVALID_ARG, "rk_b must not be all zero");
+    }
     return PSST_OK;
 }
 
@@ -804,6 +815,16 @@ int psst_create_network(const psst_network_desc *d, const psst_allocator *a, pss
     v.noise_amp = d->noise_amp;
     v.dt = d->dt;
     v.method = d->method;
+    if (d->method == PSST_METHOD_TABLEAU) {
+        // weights relative to the first nonzero b (the classic RK4 tableau
+        // then gives the RK4 kernels' own weights 1, 2, 2, 1 and scale 1/6)
+        v.rk_ns = d->rk_stages;
+        int q0 = 0;
+        while (d->rk_b[q0] == 0.0f) ++q0;
+        v.rk_beta = d->rk_b[q0];
+        for (int q = 0; q < 4; ++q) v.rk_w[q] = q < d->rk_stages ? d->rk_b[q] / v.rk_beta : 0.0f;
+        for (int q = 0; q < 3; ++q) v.rk_c[q] = q + 1 < d->rk_stages ? d->rk_a[q] : 0.0f;
+    }
     v.rec_stride = d->rec_stride;
     v.rec_cap = d->rec_stride > 0 ? d->rec_capacity : 0;
 
@@ -1438,7 +1459,7 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         long long ck_total = 0, seg_total = 0;
         for (int b = 0; b < n_nets; ++b) {
             const long long N = off[b + 1] - off[b], R = 4 * N + 2 * N * nt;
-            const long long step_floats = psst::adj_segment_floats(h->v.method, (int)N, nt);  // one step's stages
+            const long long step_floats = psst::adj_segment_floats(h->v.method, h->v.rk_ns, (int)N, nt);  // one step's stages
             ck[b] = ck_total;
             sg[b] = seg_total;
             ck_total += nck * R;

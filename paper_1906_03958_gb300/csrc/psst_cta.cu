@@ -72,17 +72,19 @@ struct SmemCoef {
     __device__ __forceinline__ float4 s(int i) const { return t2[i]; }
 };
 
-// One stage: ST = 0..3 of classic RK4, or ST = 4, the single stage of forward
-// Euler.  par selects the double-buffered stage potentials and gates read by
-// this stage (RK4: ST & 1; Euler: the step's parity).
+// One stage of kind ST (psst_syn.cuh: 0..3 classic RK4, 4 forward Euler,
+// 8..23 a tableau's stages).  par selects the double-buffered stage
+// potentials and gates read by this stage: the parity of the stage's index
+// counted over the launch.
 template <int ST, int CL, bool HAS2, bool PAIR>
 __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0, int N, int nt, int M, int r_lo,
                                       int nown, unsigned rank, long long rec_slot, float dt, float *vst, float *y0,
                                       float *acc, float *ys, const float *prm, const float *iext, float2 *cur1,
                                       float2 *acc1, float2 *fin1, float4 *cur2, float4 *acc2, float4 *fin2,
                                       float *pst, float *Gt, int lrep, const float *stab, int par) {
-    constexpr bool FIRST = ST == 0 || ST == 4, LAST = ST >= 3;
+    constexpr bool FIRST = stage_first(ST), LAST = stage_last(ST);
     const int tid = threadIdx.x, nthr = blockDim.x;
+    const StageCoef sc = stage_coef<ST>(v, dt);
     const float *vcur = vst + par * N;
     float *vnxt = vst + (par ^ 1) * N;
     const float *ysc = ys + par * 3 * nown;
@@ -95,7 +97,7 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
     // threads), where their latency overlaps the S-phase's loads, and leave
     // the N-phase fewer units.
     for (int i = nthr - 1 - tid; i < nown; i += nthr)
-        neuron_gates<ST>(i, nown, vcur[r_lo + i], ysc, ysn, y0, acc, dt);
+        neuron_gates<ST>(i, nown, vcur[r_lo + i], ysc, ysn, y0, acc, sc);
     if (PAIR) sphase_pair(it, Gt, lrep);
     else sphase<ST, HAS2>(it, SmemCoef{FIRST ? fin1 : cur1, FIRST ? fin2 : cur2});
     __syncthreads();
@@ -110,7 +112,7 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
             const float V = vcur[r_lo + i];
             const VPre pre = neuron_v_pre<ST>(i, nown, V, ysc, y0, acc, prm, iext[i]);
             const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
-            const float vn = neuron_v_post<ST>(i, pre, isyn, y0, acc, dt);
+            const float vn = neuron_v_post<ST>(i, pre, isyn, y0, acc, sc);
             vnxt[r_lo + i] = vn;
             if (CL > 1) {
 #pragma unroll
@@ -125,7 +127,7 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
             float4 &f2 = HAS2 ? fin2[p] : d4;
             const int ci = PAIR ? (int)pof[p] : p;  // (neuron, type) pair of the entry
             const float *sp = stab + (ci % nt) * 9;
-            coef_update<ST, HAS2>(sp, vcur[ci / nt], dt, cur1[p], acc1[p], fin1[p], c2, a2, f2);
+            coef_update<ST, HAS2>(sp, vcur[ci / nt], sc, cur1[p], acc1[p], fin1[p], c2, a2, f2);
             if (PAIR) {
                 // the pair's gate for the next stage (same operations as the per-synapse path)
                 const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
@@ -244,6 +246,21 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         if (v.method == PSST_METHOD_EULER) {
             stage<4, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm,
                                      iext, cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, itn & 1);
+            continue;
+        }
+        if (v.method == PSST_METHOD_TABLEAU) {
+            // stage s of step itn reads parity (itn * n + s) & 1
+#define PSST_TAB_STAGE(n, s)                                                                                    \
+    stage<tableau_stage(n, s), CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, \
+                                               ys, prm, iext, cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep,   \
+                                               stab, (itn * (n) + (s)) & 1)
+            switch (v.rk_ns) {
+            case 1: PSST_TAB_STAGE(1, 0); break;
+            case 2: PSST_TAB_STAGE(2, 0); PSST_TAB_STAGE(2, 1); break;
+            case 3: PSST_TAB_STAGE(3, 0); PSST_TAB_STAGE(3, 1); PSST_TAB_STAGE(3, 2); break;
+            default: PSST_TAB_STAGE(4, 0); PSST_TAB_STAGE(4, 1); PSST_TAB_STAGE(4, 2); PSST_TAB_STAGE(4, 3); break;
+            }
+#undef PSST_TAB_STAGE
             continue;
         }
         stage<0, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,

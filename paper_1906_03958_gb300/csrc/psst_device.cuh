@@ -49,7 +49,11 @@ struct NetView {
     const int *pair_tix;         // [N * n_stypes] or null
     const int *pair_of;          // [used pairs of all networks]
     const int *pair_off;         // [n_nets + 1]
-    int method;                  // PSST_METHOD_RK4 or PSST_METHOD_EULER
+    int method;                  // PSST_METHOD_RK4, _EULER or _TABLEAU
+    // PSST_METHOD_TABLEAU: stages, next-stage factors a_{s+1} (s < rk_ns - 1),
+    // the step weights as w_s = b_s / rk_beta with rk_beta the first nonzero b
+    int rk_ns;
+    float rk_c[3], rk_w[4], rk_beta;
 };
 
 enum : uint8_t { NET_HAS2 = 1, NET_PAIR = 2 };  // NET_PAIR: all gates of each (pre, type) pair equal

@@ -102,9 +102,10 @@ struct GlobalCoef {
     __device__ __forceinline__ float4 s(int i) const { return __ldcg(t2 + i); }
 };
 
-// One stage: ST = 0..3 of classic RK4, or ST = 4, forward Euler's single
-// stage; par selects the double-buffered potentials, gates and global tables
-// this stage reads (RK4: ST & 1; Euler: the step's parity).  On entry the
+// One stage of kind ST (psst_syn.cuh: 0..3 classic RK4, 4 forward Euler,
+// 8..23 a tableau's stages); par selects the double-buffered potentials,
+// gates and global tables this stage reads (the parity of the stage's index
+// counted over the launch).  On entry the
 // owned neurons' gates m, h, n of this stage are done and tgt is the barrier
 // count to wait for; on return the CTA has arrived at the stage's closing
 // barrier (tgt updated) and, when `more`, computed the next stage's gates.
@@ -115,7 +116,8 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
                                            float2 *cur1, float2 *acc1, float4 *cur2, float4 *acc2, float *pst,
                                            float *gtab, const float *stab, int par, unsigned long long &tgt,
                                            bool more) {
-    constexpr bool LAST = ST >= 3;
+    constexpr bool LAST = stage_last(ST);
+    const StageCoef sc = stage_coef<ST>(v, dt);
     const int tid = threadIdx.x, nthr = blockDim.x, Mloc = N * nt;
     const float *vcur = vst + par * N;
     float *vnxt = vst + (par ^ 1) * N;
@@ -151,7 +153,7 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
             const float V = vcur[i];
             const VPre pre = neuron_v_pre<ST>(i, N, V, ysc, y0, acc, prm, iext[i]);
             const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
-            const float vn = neuron_v_post<ST>(i, pre, isyn, y0, acc, dt);
+            const float vn = neuron_v_post<ST>(i, pre, isyn, y0, acc, sc);
             vnxt[i] = vn;
             if (LAST && rec_slot >= 0) v.rec[rec_slot * v.N + lo + i] = vn;
         } else {
@@ -166,7 +168,7 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
                 float4 &c2 = HAS2 ? cur2[p] : d4;
                 float4 &a2 = HAS2 ? acc2[p] : d4;
                 const float *sp = stab + (p % nt) * 9;
-                coef_update<ST, HAS2>(sp, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
+                coef_update<ST, HAS2>(sp, vcur[p / nt], sc, cur1[p], acc1[p], f1, c2, a2, f2);
                 const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
                 float G;
                 if (!LAST) {
@@ -185,7 +187,7 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
                 float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;
                 float4 &c2 = HAS2 ? cur2[p] : d4;
                 float4 &a2 = HAS2 ? acc2[p] : d4;
-                coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], dt, cur1[p], acc1[p], f1, c2, a2, f2);
+                coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], sc, cur1[p], acc1[p], f1, c2, a2, f2);
                 o1[p] = LAST ? f1 : cur1[p];
                 if (HAS2) o2[p] = LAST ? f2 : cur2[p];
             }
@@ -195,9 +197,11 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
     if (more) {
         // the next stage's gates of the owned neurons (own data only) while
         // the other CTAs arrive; that stage reads this one's ysn and vnxt
-        constexpr int NX = ST == 4 ? 4 : (ST + 1) & 3;
+        // after a step's last stage comes the first stage of the next step
+        constexpr int NX = !LAST ? ST + 1 : ST >= 8 ? ST - (ST & 3) : ST == 4 ? 4 : 0;
+        const StageCoef sx = stage_coef<NX>(v, dt);
         float *ysx = ys + par * 3 * N;
-        for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates<NX>(i, N, vnxt[i], ysn, ysx, y0, acc, dt);
+        for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates<NX>(i, N, vnxt[i], ysn, ysx, y0, acc, sx);
     }
     return true;
 }
@@ -283,10 +287,22 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         const float *ysc = ys, *vcur = vst;
         float *ysn = ys + 3 * N;
         if (nsteps > 0) {
-            if (v.method == PSST_METHOD_EULER)
-                for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates<4>(i, N, vcur[i], ysc, ysn, y0, acc, dt);
-            else
-                for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates<0>(i, N, vcur[i], ysc, ysn, y0, acc, dt);
+#define PSST_FIRST_GATES(K)                                                                                     \
+    for (int i = nthr - 1 - tid; i < N; i += nthr)                                                              \
+        neuron_gates<K>(i, N, vcur[i], ysc, ysn, y0, acc, stage_coef<K>(v, dt))
+            if (v.method == PSST_METHOD_EULER) {
+                PSST_FIRST_GATES(4);
+            } else if (v.method == PSST_METHOD_TABLEAU) {
+                switch (v.rk_ns) {
+                case 1: PSST_FIRST_GATES(tableau_stage(1, 0)); break;
+                case 2: PSST_FIRST_GATES(tableau_stage(2, 0)); break;
+                case 3: PSST_FIRST_GATES(tableau_stage(3, 0)); break;
+                default: PSST_FIRST_GATES(tableau_stage(4, 0)); break;
+                }
+            } else {
+                PSST_FIRST_GATES(0);
+            }
+#undef PSST_FIRST_GATES
         }
     }
     bool ok = true;
@@ -306,6 +322,22 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         if (v.method == PSST_METHOD_EULER) {
             ok = grid_stage<4, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
                                            acc1, cur2, acc2, pst, gtab, stab, itn & 1, tgt, more);
+            continue;
+        }
+        if (v.method == PSST_METHOD_TABLEAU) {
+            // stage s of step itn reads parity (itn * n + s) & 1
+#define PSST_TAB_STAGE(n, s)                                                                                    \
+    if (ok)                                                                                                     \
+        ok = grid_stage<tableau_stage(n, s), HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys,  \
+                                                         prm, iext, cur1, acc1, cur2, acc2, pst, gtab, stab,      \
+                                                         (itn * (n) + (s)) & 1, tgt, (s) + 1 < (n) || more)
+            switch (v.rk_ns) {
+            case 1: PSST_TAB_STAGE(1, 0); break;
+            case 2: PSST_TAB_STAGE(2, 0); PSST_TAB_STAGE(2, 1); break;
+            case 3: PSST_TAB_STAGE(3, 0); PSST_TAB_STAGE(3, 1); PSST_TAB_STAGE(3, 2); break;
+            default: PSST_TAB_STAGE(4, 0); PSST_TAB_STAGE(4, 1); PSST_TAB_STAGE(4, 2); PSST_TAB_STAGE(4, 3); break;
+            }
+#undef PSST_TAB_STAGE
             continue;
         }
         ok = grid_stage<0, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
@@ -344,9 +376,10 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
             if (HAS2 && second_order(stab, code)) gs[k] = __ldcg(g.s0g + t);
         }
     } else {
-        // the last stage wrote the step's final maps into table 0 (RK4: four
-        // stages per step) or into the table of the step count's parity (Euler)
-        const size_t fin = v.method == PSST_METHOD_EULER ? (size_t)(nsteps & 1) : 0;
+        // the last stage wrote the step's final maps into the table of the
+        // launch's stage count's parity (RK4: four stages per step, table 0)
+        const long long nst = v.method == PSST_METHOD_EULER ? 1 : v.method == PSST_METHOD_TABLEAU ? v.rk_ns : 4;
+        const size_t fin = (size_t)((nsteps * nst) & 1);
         store_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.syn_code, stab,
                           GlobalCoef{g.c1 + fin * M, HAS2 ? g.c2 + fin * M : nullptr});
     }

@@ -1,4 +1,4 @@
-// RK4 integration of networks without synapses: every neuron is an
+// Integration (RK4, Euler or a tableau) of networks without synapses: every neuron is an
 // independent ODE system (the uncoupled systems of the paper's Fig. 2b
 // benchmark), so no stage needs a barrier.  One thread owns one neuron for
 // all steps of a launch, with its state, its RK4 sums and its parameters in
@@ -18,12 +18,14 @@ namespace {
 
 constexpr int INDEP_THREADS = 256;
 
-// One RK4 stage of one neuron; ysc/ysn are this and the next stage's gates.
+// One stage of kind ST (psst_syn.cuh) of one neuron; ysc/ysn are this and
+// the next stage's gates.
 template <int ST>
-__device__ __forceinline__ float indep_stage(float V, const float *ysc, float *ysn, float *y0, float *acc,
-                                             const float *prm, float iext, float dt) {
-    neuron_gates<ST>(0, 1, V, ysc, ysn, y0, acc, dt);
-    return neuron_v<ST>(0, 1, V, ysc, y0, acc, prm, iext, 0.0f, dt);
+__device__ __forceinline__ float indep_stage(const NetView &v, float V, const float *ysc, float *ysn, float *y0,
+                                             float *acc, const float *prm, float iext, float dt) {
+    const StageCoef sc = stage_coef<ST>(v, dt);
+    neuron_gates<ST>(0, 1, V, ysc, ysn, y0, acc, sc);
+    return neuron_v<ST>(0, 1, V, ysc, y0, acc, prm, iext, 0.0f, sc);
 }
 
 // Thread t integrates neuron ind_neuron[t] of network ind_net[t] for nsteps
@@ -56,14 +58,26 @@ __global__ void __launch_bounds__(INDEP_THREADS) indep_kernel(NetView v, const i
         const float iext = input_current(v, i_const, pulse, step >= pon && step < poff, gi, step);
         if (v.method == PSST_METHOD_EULER) {
             // one stage per step; the gates alternate between ysa and ysb by step
-            if (itn & 1) V = indep_stage<4>(V, ysb, ysa, y0, acc, prm, iext, dt);
-            else V = indep_stage<4>(V, ysa, ysb, y0, acc, prm, iext, dt);
+            if (itn & 1) V = indep_stage<4>(v, V, ysb, ysa, y0, acc, prm, iext, dt);
+            else V = indep_stage<4>(v, V, ysa, ysb, y0, acc, prm, iext, dt);
+        } else if (v.method == PSST_METHOD_TABLEAU) {
+            // stage s of step itn reads the gates of parity (itn * n + s) & 1
+#define PSST_TAB_STAGE(n, s)                                                                                    \
+    V = (((itn * (n) + (s)) & 1) ? indep_stage<tableau_stage(n, s)>(v, V, ysb, ysa, y0, acc, prm, iext, dt)         \
+                                 : indep_stage<tableau_stage(n, s)>(v, V, ysa, ysb, y0, acc, prm, iext, dt))
+            switch (v.rk_ns) {
+            case 1: PSST_TAB_STAGE(1, 0); break;
+            case 2: PSST_TAB_STAGE(2, 0); PSST_TAB_STAGE(2, 1); break;
+            case 3: PSST_TAB_STAGE(3, 0); PSST_TAB_STAGE(3, 1); PSST_TAB_STAGE(3, 2); break;
+            default: PSST_TAB_STAGE(4, 0); PSST_TAB_STAGE(4, 1); PSST_TAB_STAGE(4, 2); PSST_TAB_STAGE(4, 3); break;
+            }
+#undef PSST_TAB_STAGE
         } else {
             // stage gates alternate between ysa (even stages read) and ysb
-            V = indep_stage<0>(V, ysa, ysb, y0, acc, prm, iext, dt);
-            V = indep_stage<1>(V, ysb, ysa, y0, acc, prm, iext, dt);
-            V = indep_stage<2>(V, ysa, ysb, y0, acc, prm, iext, dt);
-            V = indep_stage<3>(V, ysb, ysa, y0, acc, prm, iext, dt);
+            V = indep_stage<0>(v, V, ysa, ysb, y0, acc, prm, iext, dt);
+            V = indep_stage<1>(v, V, ysb, ysa, y0, acc, prm, iext, dt);
+            V = indep_stage<2>(v, V, ysa, ysb, y0, acc, prm, iext, dt);
+            V = indep_stage<3>(v, V, ysb, ysa, y0, acc, prm, iext, dt);
         }
         if (rec_phase >= 0) {
             if (rec_phase == 0) v.rec[(((step + 1) / v.rec_stride - 1) % v.rec_cap) * v.N + gi] = V;

@@ -34,8 +34,9 @@ cudaError_t grid_launch(const NetView &v, const GridView &g, long long step0, in
 
 // Discrete adjoint (psst_adjoint.cu).
 long long adj_smem_need(int N, int nt, int n_items, int K, bool col_warp);
-// Floats one step keeps in an adjoint segment buffer (RK4: four stages; Euler: one).
-long long adj_segment_floats(int method, int N, int nt);
+// Floats one step keeps in an adjoint segment buffer (its stages: RK4 four,
+// Euler one, a tableau rk_ns).
+long long adj_segment_floats(int method, int rk_ns, int N, int nt);
 cudaError_t adj_launch(const NetView &v, const AdjView &av, long long step0, int nsteps, int smem, int n_types,
                        float *grad_np, cudaStream_t stream);
 

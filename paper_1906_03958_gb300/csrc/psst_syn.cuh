@@ -207,18 +207,54 @@ __device__ __forceinline__ void syn2(float &r, float &s, float w, float we, floa
         s = ss;
     }
     const float s2 = ss * ss, s4 = s2 * s2;
-    const float g = __fdividef(s4, s4 + F2.w);
+    const float g = __fdividef(s4, __fadd_rn(s4, F2.w));  // no contraction into an FMA: same bits everywhere
     A = fmaf(w, g, A);
     B = fmaf(we, g, B);
 }
 
+// Stage kinds ST: 0..3 the stages of classic RK4, 4 the single stage of
+// forward Euler (first and last stage of its step), and 4 (n + 1) + s
+// (8..23) stage s of an n-stage tableau (PSST_METHOD_TABLEAU), whose
+// coefficients are read at run time.
+__host__ __device__ constexpr bool stage_first(int ST) { return ST >= 8 ? (ST & 3) == 0 : (ST == 0 || ST == 4); }
+__host__ __device__ constexpr bool stage_last(int ST) { return ST >= 8 ? (ST & 3) == (ST >> 2) - 2 : ST >= 3; }
+__host__ __device__ constexpr int tableau_stage(int n, int s) { return 4 * (n + 1) + s; }
+
+// Coefficients of stage ST: w, the weight of its slope in the step's sum
+// (relative to the first nonzero weight); cn = dt a_{s+1}, the factor of the
+// slope in the next stage's start; fin = dt times the scale of the sum at
+// the step's end.  RK4: w = 1, 2, 2, 1, cn = dt/2, dt/2, dt, fin = dt/6.
+struct StageCoef {
+    float w, cn, fin;
+};
+
+template <int ST>
+__device__ __forceinline__ StageCoef stage_coef(const NetView &v, float dt) {
+    StageCoef c;
+    if (ST >= 8) {
+        constexpr int s = ST & 3;
+        c.w = v.rk_w[s];
+        c.cn = s < 3 ? v.rk_c[s < 3 ? s : 0] * dt : 0.0f;
+        c.fin = v.rk_beta * dt;
+    } else {
+        c.w = (ST == 1 || ST == 2) ? 2.0f : 1.0f;
+        c.cn = (ST == 2) ? dt : 0.5f * dt;
+        c.fin = ST == 4 ? dt : dt * (1.0f / 6.0f);
+    }
+    return c;
+}
+
+// The first stage's term of the step's sum (RK4 and Euler: weight 1).
+template <int ST>
+__device__ __forceinline__ float first_term(const StageCoef &c, float d) {
+    return ST >= 8 ? __fmul_rn(c.w, d) : d;
+}
+
 // S-phase: every item's partial sums (A, B) at stage ST.  Coef supplies
 // r(ci) (float2 r-map) and s(ci) (float4 s-map, w = Kd).
-// ST = 0..3: the stages of classic RK4; ST = 4: the single stage of forward
-// Euler (first and last stage of its step).
 template <int ST, bool HAS2, class Coef>
 __device__ __forceinline__ void sphase(const Items &it, const Coef &cf) {
-    constexpr bool FIRST = ST == 0 || ST == 4;
+    constexpr bool FIRST = stage_first(ST);
     const int tid = threadIdx.x, nthr = blockDim.x, K = it.K, n1 = it.n1;
     for (int t = tid; t < n1; t += nthr) {
         float A = 0.0f, B = 0.0f;
@@ -444,23 +480,24 @@ __device__ __forceinline__ float pair_gate(bool second, float2 F, float4 F2, flo
     if (!second) return rr;
     const float ss = fmaf(F2.z, s0, fmaf(F2.y, r0, F2.x));
     const float s2 = ss * ss, s4 = s2 * s2;
-    return __fdividef(s4, s4 + F2.w);
+    return __fdividef(s4, __fadd_rn(s4, F2.w));
 }
 
 // Gate-map update of one (presynaptic neuron j, synapse type tau) pair at
 // stage ST from the stage-ST potential V of j.  cur/acc hold this stage's
 // map and the running RK4 sum; writes the next stage's map into cur, or at
-// the step's last stage (ST 3, or 4 for Euler) the step's final map into fin.  The s-map's fourth component
-// carries Kd (1 for first-order types, whose s-map is never used).
+// the step's last stage the step's final map into fin.  The s-map's fourth
+// component carries Kd (1 for first-order types, whose s-map is never used).
 template <int ST, bool HAS2>
-__device__ __forceinline__ void coef_update(const float *sp, float V, float dt, float2 &cur, float2 &acc,
-                                            float2 &fin, float4 &cur2, float4 &acc2, float4 &fin2) {
-    constexpr bool FIRST = ST == 0 || ST == 4, LAST = ST >= 3;
-    constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
-    const float cnext = (ST == 2) ? dt : 0.5f * dt;
-    const float dt6 = ST == 4 ? dt : dt * (1.0f / 6.0f);  // weight of the k-sum at the step's end
+__device__ __forceinline__ void coef_update(const float *sp, float V, const StageCoef &sc, float2 &cur,
+                                            float2 &acc, float2 &fin, float4 &cur2, float4 &acc2, float4 &fin2) {
+    constexpr bool FIRST = stage_first(ST), LAST = stage_last(ST);
+    const float WGT = sc.w, cnext = sc.cn, dt6 = sc.fin;
     const float T = transmitter(V, sp[SP_VP], sp[SP_KP]);  // table holds 1/Kp
-    const float a_ = sp[SP_A] * T, bb = a_ + sp[SP_B];
+    // explicit roundings: no product is contracted into an FMA or folded
+    // with a constant stage weight, so every kernel and stage kind (constant
+    // or run-time coefficients) gets the same bits
+    const float a_ = __fmul_rn(sp[SP_A], T), bb = __fadd_rn(a_, sp[SP_B]);
     float P = 0.0f, Q = 1.0f, U = 0.0f, X = 0.0f, Z = 1.0f;
     if (!FIRST) {
         P = cur.x;
@@ -471,8 +508,8 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, float dt, 
             Z = cur2.z;
         }
     }
-    const float kP = fmaf(-bb, P, a_), kQ = -bb * Q;
-    float2 A1 = make_float2(kP, kQ);
+    const float kP = fmaf(-bb, P, a_), kQ = __fmul_rn(-bb, Q);
+    float2 A1 = make_float2(first_term<ST>(sc, kP), first_term<ST>(sc, kQ));
     if (!FIRST) A1 = make_float2(fmaf(WGT, kP, acc.x), fmaf(WGT, kQ, acc.y));
     if (!LAST) {
         acc = A1;
@@ -483,8 +520,9 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, float dt, 
     if (HAS2) {
         const float K3 = sp[SP_K3], K4 = sp[SP_K4];
         const float Kd = sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f;
-        const float kU = fmaf(K3, P, -K4 * U), kX = fmaf(K3, Q, -K4 * X), kZ = -K4 * Z;
-        float4 A2 = make_float4(kU, kX, kZ, 0.0f);
+        const float kU = fmaf(K3, P, __fmul_rn(-K4, U)), kX = fmaf(K3, Q, __fmul_rn(-K4, X));
+        const float kZ = __fmul_rn(-K4, Z);
+        float4 A2 = make_float4(first_term<ST>(sc, kU), first_term<ST>(sc, kX), first_term<ST>(sc, kZ), 0.0f);
         if (!FIRST) A2 = make_float4(fmaf(WGT, kU, acc2.x), fmaf(WGT, kX, acc2.y), fmaf(WGT, kZ, acc2.z), 0.0f);
         if (!LAST) {
             acc2 = A2;
@@ -516,7 +554,7 @@ struct VPre {
 template <int ST>
 __device__ __forceinline__ VPre neuron_v_pre(int i, int n, float V, const float *ysc, const float *y0,
                                              const float *acc, const float *prm, float iext) {
-    constexpr bool FIRST = ST == 0 || ST == 4;
+    constexpr bool FIRST = stage_first(ST);
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
     // explicit roundings (no contraction left to the compiler), so that every
     // kernel evaluates the same operations in whatever context it is inlined
@@ -535,13 +573,12 @@ __device__ __forceinline__ VPre neuron_v_pre(int i, int n, float V, const float 
 }
 
 template <int ST>
-__device__ __forceinline__ float neuron_v_post(int i, const VPre &p, float isyn, float *y0, float *acc, float dt) {
-    constexpr bool FIRST = ST == 0 || ST == 4, LAST = ST >= 3;
-    constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
-    const float cnext = (ST == 2) ? dt : 0.5f * dt;
-    const float dt6 = ST == 4 ? dt : dt * (1.0f / 6.0f);  // weight of the k-sum at the step's end
+__device__ __forceinline__ float neuron_v_post(int i, const VPre &p, float isyn, float *y0, float *acc,
+                                              const StageCoef &sc) {
+    constexpr bool FIRST = stage_first(ST), LAST = stage_last(ST);
+    const float WGT = sc.w, cnext = sc.cn, dt6 = sc.fin;
     const float d = __fmul_rn(__fsub_rn(p.ie, isyn), p.invC);
-    const float ac = FIRST ? d : fmaf(WGT, d, p.acc);
+    const float ac = FIRST ? first_term<ST>(sc, d) : fmaf(WGT, d, p.acc);
     if (!LAST) {
         acc[i] = ac;
         return fmaf(cnext, d, p.y0);
@@ -553,19 +590,17 @@ __device__ __forceinline__ float neuron_v_post(int i, const VPre &p, float isyn,
 
 template <int ST>
 __device__ __forceinline__ float neuron_v(int i, int n, float V, const float *ysc, float *y0, float *acc,
-                                          const float *prm, float iext, float isyn, float dt) {
-    return neuron_v_post<ST>(i, neuron_v_pre<ST>(i, n, V, ysc, y0, acc, prm, iext), isyn, y0, acc, dt);
+                                          const float *prm, float iext, float isyn, const StageCoef &sc) {
+    return neuron_v_post<ST>(i, neuron_v_pre<ST>(i, n, V, ysc, y0, acc, prm, iext), isyn, y0, acc, sc);
 }
 
 // Gates: writes the next stage's m, h, n, or after the last stage the new
 // step-start ones.
 template <int ST>
 __device__ __forceinline__ void neuron_gates(int i, int n, float V, const float *ysc, float *ysn, float *y0,
-                                             float *acc, float dt) {
-    constexpr bool FIRST = ST == 0 || ST == 4, LAST = ST >= 3;
-    constexpr float WGT = (ST == 0 || ST == 3) ? 1.0f : 2.0f;
-    const float cnext = (ST == 2) ? dt : 0.5f * dt;
-    const float dt6 = ST == 4 ? dt : dt * (1.0f / 6.0f);  // weight of the k-sum at the step's end
+                                             float *acc, const StageCoef &sc) {
+    constexpr bool FIRST = stage_first(ST), LAST = stage_last(ST);
+    const float WGT = sc.w, cnext = sc.cn, dt6 = sc.fin;
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
     const Rates q = hh_rates(V);
     float d[3];
@@ -575,7 +610,7 @@ __device__ __forceinline__ void neuron_gates(int i, int n, float V, const float 
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
         const int ix = (x + 1) * n + i;
-        const float ac = FIRST ? d[x] : fmaf(WGT, d[x], acc[ix]);
+        const float ac = FIRST ? first_term<ST>(sc, d[x]) : fmaf(WGT, d[x], acc[ix]);
         float yn;
         if (!LAST) {
             acc[ix] = ac;

@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build
 
 MODE_AUTO, MODE_CTA, MODE_GRID = 0, 1, 2
-METHOD_RK4, METHOD_EULER = 0, 1
+METHOD_RK4, METHOD_EULER, METHOD_TABLEAU = 0, 1, 2
 OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT",
           -6: "STATE", -7: "UNSUPPORTED"}
@@ -49,7 +49,8 @@ class NetworkDesc(C.Structure):
                 ("noise_amp", C.c_float), ("dt", C.c_float), ("init_state", C.c_void_p),
                 ("rec_stride", C.c_int32), ("rec_capacity", C.c_int64), ("mode", C.c_int32),
                 ("block_threads", C.c_int32), ("item_chunks", C.c_int32), ("device", C.c_int32),
-                ("gate_mode", C.c_int32), ("method", C.c_int32), ("min_cluster", C.c_int32)]
+                ("gate_mode", C.c_int32), ("method", C.c_int32), ("min_cluster", C.c_int32),
+                ("rk_stages", C.c_int32), ("rk_a", C.c_float * 3), ("rk_b", C.c_float * 4)]
 
 
 class DeviceNetwork(C.Structure):
@@ -185,13 +186,23 @@ class TorchAllocator:
 class Network:
     """A batch of networks resident on one GPU (``psst_create_network``).
     ``allocator="torch"`` takes the handle's device memory from PyTorch's
-    caching allocator instead of cudaMalloc."""
+    caching allocator instead of cudaMalloc.  ``tableau=(a, b)`` integrates
+    with that explicit Runge-Kutta map (METHOD_TABLEAU: a = the n - 1
+    coefficients a_{s+1} of the stages' starts y + dt a_{s+1} k_s, b = the n
+    weights; 1 <= n <= 4)."""
 
     def __init__(self, spec, init_state=None, rec_stride: int = 0, rec_capacity: int = 0,
                  mode: int = MODE_AUTO, block_threads: int = 0, item_chunks: int = 0,
                  device: int | None = None, gate_mode: int = 0, method: int = 0, allocator=None,
-                 min_cluster: int = 0):
+                 min_cluster: int = 0, tableau=None):
         lib = load()
+        rk_stages, rk_a, rk_b = 0, [0.0] * 3, [0.0] * 4
+        if tableau is not None:
+            a, b = (list(np.atleast_1d(np.asarray(x, np.float64))) for x in tableau)
+            if not 1 <= len(b) <= 4 or len(a) != len(b) - 1:
+                raise ValueError("a tableau has 1..4 stages and n_stages - 1 coefficients a")
+            method, rk_stages = METHOD_TABLEAU, len(b)
+            rk_a[:len(a)], rk_b[:len(b)] = a, b
         keep = dict(
             off=_arr(spec.net_neuron_off, np.int32), nt=_arr(spec.neuron_type, np.int32),
             np_=_arr(spec.neuron_params, np.float32), rp=_arr(spec.row_ptr, np.int64),
@@ -215,7 +226,8 @@ class Network:
             noise_amp=float(spec.noise_amp), dt=float(spec.dt), init_state=ptr("init"),
             rec_stride=int(rec_stride), rec_capacity=int(rec_capacity), mode=int(mode),
             block_threads=int(block_threads), item_chunks=int(item_chunks), device=int(device),
-            gate_mode=int(gate_mode), method=int(method), min_cluster=int(min_cluster))
+            gate_mode=int(gate_mode), method=int(method), min_cluster=int(min_cluster), rk_stages=rk_stages,
+            rk_a=(C.c_float * 3)(*rk_a), rk_b=(C.c_float * 4)(*rk_b))
         self._allocator = TorchAllocator(device) if allocator == "torch" else allocator
         if self._allocator is not None and not isinstance(self._allocator, TorchAllocator):
             raise ValueError("allocator must be None or 'torch'")

@@ -82,7 +82,7 @@ def _desc(spec, **kw):
     ("item_chunks", 65, b"item_chunks"),
     ("rec_stride", -1, b"rec_stride"),
     ("gate_mode", 2, b"gate_mode"),
-    ("method", 2, b"method"),
+    ("method", 3, b"method"),
     ("mode", 3, b"mode"),
     ("min_cluster", 3, b"min_cluster"),
 ])
@@ -92,6 +92,20 @@ def test_invalid_descriptor_rejected_on_host(lib, field, value, needle):
     h = C.c_void_p()
     rc = lib.psst_create_network(C.byref(d), None, C.byref(h))
     assert rc == -1 and not h.value
+    assert needle in lib.psst_last_error()
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(method=2, rk_stages=0), b"rk_stages"),
+    (dict(method=2, rk_stages=5), b"rk_stages"),
+    (dict(method=2, rk_stages=2, rk_b=(C.c_float * 4)(0.0, 0.0, 1.0, 1.0)), b"rk_b"),
+    (dict(method=2, rk_stages=2, rk_a=(C.c_float * 3)(float("nan"), 0.0, 0.0),
+          rk_b=(C.c_float * 4)(0.5, 0.5, 0.0, 0.0)), b"rk_a"),
+])
+def test_invalid_tableau_rejected_on_host(lib, kw, needle):
+    d, keep = _desc(ng.plain20(), **kw)
+    h = C.c_void_p()
+    assert lib.psst_create_network(C.byref(d), None, C.byref(h)) == -1 and not h.value
     assert needle in lib.psst_last_error()
 
 
