@@ -171,7 +171,8 @@ typedef struct {
    allocator with a NULL function), OOM, CUDA, UNSUPPORTED. */
 int psst_create_network(const psst_network_desc *d, const psst_allocator *a, psst_net **out);
 
-/* Advance every network by n_steps RK4 steps from the current state
+/* Advance every network by n_steps steps of the handle's method (RK4,
+   Euler or its tableau) from the current state
    (Sec. "Circumventing memory constraints", item 2: successive calls
    continue where the previous one stopped; results are bitwise independent
    of how the steps are split into calls).  Asynchronous on `stream`;
@@ -182,7 +183,7 @@ int psst_create_network(const psst_network_desc *d, const psst_allocator *a, pss
 int psst_integrate(psst_net *h, int64_t n_steps, void *stream);
 
 /* Grid mode only: time limit of one wait at the device-wide barrier between
-   RK4 stages (default 2 s).  On expiry the kernel records PSST_ERR_TIMEOUT,
+   stages (default 2 s).  On expiry the kernel records PSST_ERR_TIMEOUT,
    every CTA returns, and the state keeps its value from before the call's
    first step that failed.  0 makes every wait give up at once (a way to
    exercise the error path without a hang). */

@@ -12,7 +12,8 @@
 // (psst_indep.cu).
 //
 // Per RK4 step (classic tableau, Sec. "Brain simulations as computational
-// graphs", RK4 paragraph) and stage s = 0..3 (Euler: one stage):
+// graphs", RK4 paragraph) and stage s = 0..3 (Euler: one stage; a given
+// tableau: its 1..4 stages):
 //   S-phase   each thread sums its work items (per-pair layout: A = sum w G
 //             with the pair's gate G gathered from the gate table), after
 //             the owned neurons' gates m, h, n (on the highest threads);

@@ -1,6 +1,6 @@
-// Integration (RK4, Euler or a tableau) of networks without synapses: every neuron is an
-// independent ODE system (the uncoupled systems of the paper's Fig. 2b
-// benchmark), so no stage needs a barrier.  One thread owns one neuron for
+// Integration (RK4, Euler or a tableau) of networks without synapses:
+// every neuron is an independent ODE system (the uncoupled systems of the
+// paper's Fig. 2b benchmark), so no stage needs a barrier.  One thread owns one neuron for
 // all steps of a launch, with its state, its RK4 sums and its parameters in
 // registers; the right-hand side and the stage updates are the functions
 // the coupled kernels use (psst_syn.cuh), called with a zero synaptic

@@ -109,6 +109,13 @@ def test_invalid_tableau_rejected_on_host(lib, kw, needle):
     assert needle in lib.psst_last_error()
 
 
+@pytest.mark.parametrize("tableau", [([0.5, 0.5], [0.5, 0.5]), ([], []), ([0.5] * 4, [0.2] * 5)])
+def test_binding_rejects_malformed_tableau(lib, tableau):
+    # a tableau has 1..4 weights b and one coefficient a fewer
+    with pytest.raises(ValueError):
+        psst.Network(ng.plain20(), tableau=tableau)
+
+
 def test_out_of_range_presynaptic_index_rejected(lib):
     spec = ng.plain20()
     spec.pre = spec.pre.copy()
