@@ -43,6 +43,11 @@ MUTANTS = [
     ("out[3] = r[3] * (1.0 - r[3]) / 10.0;", "out[3] = r[3] * (1.0 - r[3]) / 20.0;"),  # constant
     ("gp[P_GK] += -q * n4 * (V[i] - p[P_EK]);", "gp[P_GK] += q * n4 * (V[i] - p[P_EK]);"),  # sign
     ("if (g) g->gw[k] += -q * G * (V[i] - E);", "if (g) g->gw[k] += -q * (V[i] - E);"),  # dropped factor
+    # forward Euler and its adjoint
+    ("for (int64_t i = 0; i < d; ++i) y[i] = y[i] + h * work[i];",
+     "for (int64_t i = 0; i < d; ++i) y[i] = y[i] + 0.5 * h * work[i];"),   # step size
+    ("for (int64_t i = 0; i < d; ++i) kb[i] = hstep * lam[i];",
+     "for (int64_t i = 0; i < d; ++i) kb[i] = lam[i];"),                    # dropped factor
     # tableau map and its adjoint
     ("Y[i] = y[i] + h * tab[st - 1] * k[i];", "Y[i] = y[i] + h * tab[st] * k[i];"),  # coefficient index
     ("sum[i] += tab[3 + st] * k[i];", "sum[i] += k[i];"),                  # dropped weight
