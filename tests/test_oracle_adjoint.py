@@ -96,11 +96,13 @@ def _loss(net, y0, nsteps, g, stride, step0=0, order=4, tableau=None):
     return float(np.sum(rec * g))
 
 
-# Heun's third-order method: a_21 = 1/3, a_32 = 2/3, b = (1/4, 0, 3/4)
+# Heun's third-order method: a_21 = 1/3, a_32 = 2/3, b = (1/4, 0, 3/4);
+# the midpoint method (first weight zero): a_21 = 1/2, b = (0, 1)
 HEUN3 = ([1.0 / 3.0, 2.0 / 3.0], [0.25, 0.0, 0.75])
+MIDPOINT = ([0.5], [0.0, 1.0])
 
 
-@pytest.mark.parametrize("order,tableau", [(4, None), (1, None), (0, HEUN3)])
+@pytest.mark.parametrize("order,tableau", [(4, None), (1, None), (0, HEUN3), (0, MIDPOINT)])
 def test_trajectory_gradient_vs_fd(order, tableau):
     spec = _small_al(seed=4)
     net = oracle.OracleNet(spec)
