@@ -6,11 +6,11 @@ float64, built with gcc) through ctypes and shares no code with the CUDA
 library: it reads the same seeded input arrays (any object with the
 ``NetworkSpec`` attributes) and widens them to float64.
 
-Pinned functions and their pins live in ``tests/test_oracle_pins.py`` and
-``tests/test_oracle_adjoint.py``.  The
-Philox generator is pinned only statistically (no published known-answer
-vector is available here): its parity with the published generator is
-unpinned; its parity with the CUDA side is bit-exact by test.
+Pinned functions and their pins live in ``tests/test_oracle_pins.py``,
+``tests/test_oracle_adjoint.py`` and ``tests/test_oracle_tableau.py``.  The
+Philox generator is pinned to its published known-answer vectors
+(``tests/golden/philox_kat.json``) and to an independent library
+implementation; its parity with the CUDA side is bit-exact by test.
 """
 from __future__ import annotations
 

@@ -2,8 +2,8 @@
 that the pins in test_oracle_pins.py, test_oracle_adjoint.py and
 test_oracle_tableau.py catch every one of them.
 
-The Philox round structure is deliberately absent: it is pinned only
-statistically, so its parity with the published generator is unpinned.
+The Philox mutants are caught by the generator's published known-answer
+vectors (tests/golden/philox_kat.json).
 """
 import os
 import shutil
@@ -56,6 +56,13 @@ MUTANTS = [
     ("kb[i] = hstep * tab[3 + st] * lam[i];", "kb[i] = hstep * lam[i];"),  # dropped weight
     ("Ys[(st - 1) * d + i] = y[i] + hstep * tab[st - 1] * k[i];",
      "Ys[(st - 1) * d + i] = y[i] + hstep * k[i];"),                       # dropped coefficient
+    # Philox4x32-10
+    ("const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;",
+     "const uint32_t M0 = 0xCD9E8D57u, M1 = 0xD2511F53u;"),                # swapped multipliers
+    ("if (round > 0) { k0 += W0; k1 += W1; }", "if (round > 0) { k0 += W0; }"),  # dropped key bump
+    ("uint32_t n2 = hi0 ^ c3 ^ k1;", "uint32_t n2 = hi0 ^ c1 ^ k1;"),      # wrong word
+    ("for (int round = 0; round < 10; ++round) {\n        if (round > 0) { k0",
+     "for (int round = 0; round < 9; ++round) {\n        if (round > 0) { k0"),  # rounds
 ]
 
 

@@ -294,8 +294,67 @@ def test_shot_noise_wiring():
         assert y[i] == pytest.approx(-65.0 + 2.0 * dt * cnt, abs=1e-11)
 
 
+PHILOX_KAT = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "philox_kat.json")))
+
+
+@pytest.mark.parametrize("vec", PHILOX_KAT["vectors"])
+def test_philox_known_answer_vectors(vec):
+    # The generator's published known-answer vectors (Salmon et al., SC'11;
+    # tests/golden/philox_kat.json): all four output words, bit for bit.
+    ctr = tuple(int(x, 16) for x in vec["ctr"])
+    key = tuple(int(x, 16) for x in vec["key"])
+    want = [int(x, 16) for x in vec["out"]]
+    got = [int(x) for x in oracle.philox(ctr, key)]
+    assert got == want, ["%08x" % g for g in got]
+
+
+_TRITON_PHILOX = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def draw(out, c0p, c1p, c2p, c3p, seed, B: tl.constexpr):
+    o = tl.arange(0, B)
+    a, b, c, d = tl.philox(seed, tl.load(c0p + o), tl.load(c1p + o), tl.load(c2p + o), tl.load(c3p + o))
+    tl.store(out + 4 * o, a)
+    tl.store(out + 4 * o + 1, b)
+    tl.store(out + 4 * o + 2, c)
+    tl.store(out + 4 * o + 3, d)
+
+ctr = np.array(json.loads(sys.argv[1]), dtype=np.uint32)
+B = ctr.shape[0]
+out = torch.zeros(4 * B, dtype=torch.int32)
+cols = [torch.from_numpy(np.ascontiguousarray(ctr[:, j]).view(np.int32)) for j in range(4)]
+draw[(1,)](out, *cols, int(sys.argv[2]), B=B)
+print(json.dumps(out.numpy().view(np.uint32).reshape(B, 4).tolist()))
+"""
+
+
+def test_philox_matches_library_generator():
+    # A second, independent implementation of the same generator: Triton's
+    # tl.philox (Philox4x32 with 10 rounds, key = the 64-bit seed split into
+    # low and high words), run by Triton's CPU interpreter in a child
+    # process.  Random counters and a fixed key; all four words must agree.
+    pytest.importorskip("triton")
+    import subprocess
+    import sys
+    rng = np.random.default_rng(123)
+    ctr = rng.integers(0, 1 << 32, size=(16, 4), dtype=np.uint64)
+    seed = 0x0BADF00D1234ABCD
+    r = subprocess.run([sys.executable, "-c", _TRITON_PHILOX, json.dumps(ctr.tolist()), str(seed)],
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        pytest.skip("Triton's CPU interpreter is unavailable: " + r.stderr.strip().splitlines()[-1][:200])
+    lib = np.array(json.loads(r.stdout.strip().splitlines()[-1]), dtype=np.uint64)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for row, want in zip(ctr, lib):
+        got = oracle.philox(tuple(int(x) for x in row), key)
+        assert [int(x) for x in got] == [int(x) for x in want]
+
+
 def test_philox_statistics():
-    # Statistical pin only; no published known-answer vector is available.
+    # Statistical properties, beside the exact pins above.
     words = []
     key = (0x1234ABCD, 0x0BADF00D)
     for c in range(1 << 14):
