@@ -148,6 +148,11 @@ typedef struct {
                                       pair; the others keep one gate per synapse (gate_mode) */
     int32_t n_independent_nets;    /* CTA mode: networks without synapses, integrated one thread per neuron
                                       without barriers (bitwise the same results) */
+    int64_t ck_start;              /* checkpoints recorded for psst_adjoint (psst_record_checkpoints):
+                                      global step at which the recorded integrate call started, or -1
+                                      when no valid recording exists (none made, or the state, step,
+                                      weights or neuron table changed since) */
+    int64_t ck_steps;              /* steps of that recorded call (0 when ck_start is -1) */
 } psst_info;
 
 typedef struct psst_net psst_net;

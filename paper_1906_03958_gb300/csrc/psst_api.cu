@@ -1526,6 +1526,8 @@ int psst_query(const psst_net *h, psst_info *out) {
     } else {
         for (uint8_t f : h->pin.flags) out->n_pair_gate_nets += (f & psst::NET_PAIR) ? 1 : 0;
     }
+    out->ck_start = h->rec_ck_valid ? h->rec_ck_start : -1;
+    out->ck_steps = h->rec_ck_valid ? h->rec_ck_nsteps : 0;
     return PSST_OK;
 }
 

@@ -72,7 +72,7 @@ class Info(C.Structure):
                 ("smem_bytes", C.c_int32), ("n_single_cta_nets", C.c_int32),
                 ("n_cluster_nets", C.c_int32), ("n_launch_classes", C.c_int32),
                 ("kernel_launches", C.c_int32), ("n_pair_gate_nets", C.c_int32),
-                ("n_independent_nets", C.c_int32)]
+                ("n_independent_nets", C.c_int32), ("ck_start", C.c_int64), ("ck_steps", C.c_int64)]
 
 
 _lib = None
@@ -243,6 +243,11 @@ class Network:
         self._cap = int(rec_capacity) if rec_stride > 0 else 0
         self.n_ntypes = keep["np_"].shape[0]
         self.recording_checkpoints = False
+        # what the weight and neuron tables currently hold (the last source
+        # written), and a counter bumped by every write: autograd.PsstTrace
+        # uses both to run a backward against the tables of its own forward
+        self._w_src, self._p_src = spec.weight, spec.neuron_params
+        self.tables_version = 0
 
     def __del__(self):
         self.close()
@@ -311,10 +316,19 @@ class Network:
     def set_weights(self, w, stream=None):
         """Synaptic weights [S] from a float32 CUDA tensor or host array."""
         self._set_table(load().psst_set_weights, w, stream)
+        self._w_src = w
+        self.tables_version += 1
 
     def set_neuron_params(self, p, stream=None):
         """Neuron-type table [n_types, 9] from a float32 CUDA tensor or host array."""
         self._set_table(load().psst_set_neuron_params, p, stream)
+        self._p_src = p
+        self.tables_version += 1
+
+    def tables_source(self):
+        """(weights, neuron table) last written into the network: the
+        objects given to set_weights / set_neuron_params, or the spec's."""
+        return self._w_src, self._p_src
 
     def _set_table(self, fn, x, stream):
         import torch

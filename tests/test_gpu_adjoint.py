@@ -5,6 +5,7 @@ import pytest
 
 import oracle
 from paper_1906_03958_gb300 import netgen as ng
+from tests.helpers import grad_error
 
 pytestmark = pytest.mark.gpu
 
@@ -17,10 +18,6 @@ def _spec(seed=3, sets=1):
         s.pulse_on[:] = 5
         s.pulse_off[:] = 10_000
     return hidden, start
-
-
-def _rel(a, b):
-    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30)
 
 
 def _gpu_adjoint(spec, nsteps, dLdV, stride, ckpt=50, step0=0):
@@ -41,10 +38,10 @@ def test_adjoint_matches_oracle_adjoint():
     y0 = oracle.rest_state(spec)
     gy64, gw64, gp64 = oracle.adjoint(spec, y0, nsteps, g, stride, ckpt=100)
     gw, gp, gy = _gpu_adjoint(spec, nsteps, g, stride)
-    assert _rel(gw, gw64) <= GRAD_TOL
-    assert _rel(gp, gp64) <= GRAD_TOL
+    assert grad_error(gw, gw64) <= GRAD_TOL
+    assert grad_error(gp, gp64) <= GRAD_TOL
     N = spec.n_neurons
-    assert _rel(gy.ravel(), gy64[:4 * N]) <= GRAD_TOL
+    assert grad_error(gy.ravel(), gy64[:4 * N]) <= GRAD_TOL
 
 
 def test_adjoint_vs_fp64_finite_differences():
@@ -95,8 +92,8 @@ def test_adjoint_batch_of_parameter_sets():
     gw, gp, _ = _gpu_adjoint(spec, nsteps, g, stride, ckpt=64)
     for b in range(spec.n_nets):
         s0, s1 = spec.row_ptr[spec.net_neuron_off[b]], spec.row_ptr[spec.net_neuron_off[b + 1]]
-        assert _rel(gw[s0:s1], gw64[s0:s1]) <= GRAD_TOL
-        assert _rel(gp[2 * b:2 * b + 2], gp64[2 * b:2 * b + 2]) <= GRAD_TOL
+        assert grad_error(gw[s0:s1], gw64[s0:s1]) <= GRAD_TOL
+        assert grad_error(gp[2 * b:2 * b + 2], gp64[2 * b:2 * b + 2]) <= GRAD_TOL
 
 
 def test_checkpoint_spacing_and_step_offset():
@@ -108,9 +105,9 @@ def test_checkpoint_spacing_and_step_offset():
     a = _gpu_adjoint(spec, nsteps, g, stride, ckpt=7, step0=step0)
     b = _gpu_adjoint(spec, nsteps, g, stride, ckpt=240, step0=step0)
     for x, y in zip(a, b):
-        assert _rel(x, y) <= 1e-5
+        assert grad_error(x, y) <= 1e-5
     _, gw64, _ = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, step0=step0)
-    assert _rel(a[0], gw64) <= GRAD_TOL
+    assert grad_error(a[0], gw64) <= GRAD_TOL
 
 
 def test_nonuniform_gates_are_rejected():
@@ -150,8 +147,8 @@ def test_autograd_mse_loss():
     diff = (v - target).detach().cpu().numpy()
     dLdV[:, :12] = 2.0 * diff[:, :12] / (nsteps * 12)
     _, gw64, gp64 = oracle.adjoint(start, oracle.rest_state(start), nsteps, dLdV, 1)
-    assert _rel(w.grad.cpu().numpy(), gw64) <= GRAD_TOL
-    assert _rel(p.grad.cpu().numpy(), gp64) <= GRAD_TOL
+    assert grad_error(w.grad.cpu().numpy(), gw64) <= GRAD_TOL
+    assert grad_error(p.grad.cpu().numpy(), gp64) <= GRAD_TOL
     assert float(loss.detach()) > 0
 
 
@@ -169,7 +166,7 @@ def test_recorded_checkpoints_match_own_checkpoints():
         rec = net.adjoint(nsteps, g, 0)
         net.status()
         for a, b in zip(own, rec):
-            assert _rel(b.cpu().numpy(), a.cpu().numpy()) <= 1e-5
+            assert grad_error(b.cpu().numpy(), a.cpu().numpy()) <= 1e-5
         net.set_state(net.get_state())  # invalidates the recorded span
         with pytest.raises(psst.PsstError) as ei:
             net.adjoint(nsteps, g, 0)
@@ -192,8 +189,8 @@ def test_autograd_with_recorded_checkpoints():
             v = trace(net, w, p, nsteps, ckpt_every=50)
             (v ** 2).mean().backward()
             out.append((w.grad.cpu().numpy(), p.grad.cpu().numpy()))
-    assert _rel(out[1][0], out[0][0]) <= 1e-5
-    assert _rel(out[1][1], out[0][1]) <= 1e-5
+    assert grad_error(out[1][0], out[0][0]) <= 1e-5
+    assert grad_error(out[1][1], out[0][1]) <= 1e-5
 
 
 def _with_duplicate_synapses(spec, seed=9):
@@ -241,5 +238,50 @@ def test_duplicate_synapses_forward_and_adjoint():
     g = rng.standard_normal((nsteps // stride, N))
     gy64, gw64, gp64 = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, ckpt=100)
     gw, gp, gy = _gpu_adjoint(spec, nsteps, g, stride)
-    assert _rel(gw, gw64) <= GRAD_TOL
-    assert _rel(gp, gp64) <= GRAD_TOL
+    assert grad_error(gw, gw64) <= GRAD_TOL
+    assert grad_error(gp, gp64) <= GRAD_TOL
+
+
+def test_autograd_two_windows_before_one_backward():
+    # Two trace windows of equal length with different weights, then one
+    # backward of a loss over both: each window's gradient must be the
+    # adjoint of its own span with its own tables (the network meanwhile
+    # holds the second window's checkpoints and weights).  Reference: each
+    # window's adjoint taken separately on a fresh network.
+    import torch
+    from paper_1906_03958_gb300 import psst
+    from paper_1906_03958_gb300.autograd import trace
+    _, spec = _spec(seed=12)
+    nsteps, stride = 200, 2
+    frames = nsteps // stride
+    for record in (False, True):
+        with psst.Network(spec, rec_stride=stride, rec_capacity=2 * frames) as net:
+            if record:
+                net.record_checkpoints(50, nsteps)
+            w1 = torch.from_numpy(spec.weight).cuda().requires_grad_(True)
+            p1 = torch.from_numpy(spec.neuron_params).cuda().requires_grad_(True)
+            v1 = trace(net, w1, p1, nsteps, ckpt_every=50)
+            y_mid = net.get_state().clone()
+            w2 = (1.25 * w1.detach()).requires_grad_(True)
+            p2 = p1.detach().clone().requires_grad_(True)
+            v2 = trace(net, w2, p2, nsteps, ckpt_every=50)
+            y_end = net.get_state().clone()
+            ((v1 ** 2).mean() + (v2 ** 3).mean()).backward()
+            # the network is left where the second window ended, with its tables
+            assert net.info()["steps_done"] == 2 * nsteps
+            assert torch.equal(net.get_state(), y_end)
+        g1 = (2.0 * v1.detach() / v1.numel()).cpu().numpy()
+        g2 = (3.0 * v2.detach() ** 2 / v2.numel()).cpu().numpy()
+        spec2 = ng.NetworkSpec(**{k: getattr(spec, k) for k in spec.__dataclass_fields__})
+        spec2.weight = (1.25 * spec.weight.astype(np.float32)).astype(np.float32)
+        with psst.Network(spec, rec_stride=stride, rec_capacity=frames) as ref:
+            r1 = ref.adjoint(nsteps, torch.from_numpy(g1).cuda(), 50)
+        with psst.Network(spec2, init_state=y_mid.cpu().numpy(), rec_stride=stride,
+                          rec_capacity=frames) as ref:
+            ref.set_step(nsteps)
+            r2 = ref.adjoint(nsteps, torch.from_numpy(g2).cuda(), 50)
+            ref.status()
+        assert grad_error(w1.grad.cpu().numpy(), r1[0].cpu().numpy()) <= 1e-5, record
+        assert grad_error(p1.grad.cpu().numpy(), r1[1].cpu().numpy()) <= 1e-5, record
+        assert grad_error(w2.grad.cpu().numpy(), r2[0].cpu().numpy()) <= 1e-5, record
+        assert grad_error(p2.grad.cpu().numpy(), r2[1].cpu().numpy()) <= 1e-5, record

@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 from paper_1906_03958_gb300 import netgen as ng
+from tests.helpers import grad_error
 from tests.helpers import step_error
 
 pytestmark = pytest.mark.gpu
@@ -91,10 +92,6 @@ def test_euler_trajectory_tracks_oracle_euler():
 GRAD_TOL = 1e-3
 
 
-def _rel(a, b):
-    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30)
-
-
 def _diff_spec(seed, sets=1):
     _, spec = ng.differentiated(n_sets=sets, seed=seed, n_pn=12, n_ln=4)
     spec.pulse_on[:] = 5
@@ -123,13 +120,13 @@ def test_euler_adjoint_matches_oracle_euler_adjoint(sets, ckpt):
     gw, gp, gy = _euler_adjoint(spec, nsteps, g, stride, ckpt=ckpt)
     for b in range(spec.n_nets):
         s0, s1 = spec.row_ptr[spec.net_neuron_off[b]], spec.row_ptr[spec.net_neuron_off[b + 1]]
-        assert _rel(gw[s0:s1], gw64[s0:s1]) <= GRAD_TOL
-        assert _rel(gp[2 * b:2 * b + 2], gp64[2 * b:2 * b + 2]) <= GRAD_TOL
+        assert grad_error(gw[s0:s1], gw64[s0:s1]) <= GRAD_TOL
+        assert grad_error(gp[2 * b:2 * b + 2], gp64[2 * b:2 * b + 2]) <= GRAD_TOL
     N = spec.n_neurons
-    assert _rel(gy.ravel(), gy64[:4 * N]) <= GRAD_TOL
+    assert grad_error(gy.ravel(), gy64[:4 * N]) <= GRAD_TOL
     # not the RK4 adjoint: the two maps' gradients differ by more than the bar
     _, gw_rk4, _ = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, ckpt=ckpt, order=4)
-    assert _rel(gw_rk4, gw64) > 10 * GRAD_TOL
+    assert grad_error(gw_rk4, gw64) > 10 * GRAD_TOL
 
 
 def test_euler_adjoint_vs_fp64_finite_differences():
@@ -184,9 +181,9 @@ def test_euler_adjoint_checkpoint_spacing_step_offset_and_recorded_span():
     a = _euler_adjoint(spec, nsteps, g, stride, ckpt=7, step0=step0)
     b = _euler_adjoint(spec, nsteps, g, stride, ckpt=240, step0=step0)
     for x, y in zip(a, b):
-        assert _rel(x, y) <= 1e-5
+        assert grad_error(x, y) <= 1e-5
     _, gw64, _ = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, step0=step0, order=1)
-    assert _rel(a[0], gw64) <= GRAD_TOL
+    assert grad_error(a[0], gw64) <= GRAD_TOL
     # the span of an Euler integrate call whose checkpoints were recorded
     gt = torch.from_numpy(g.astype(np.float32)).cuda()
     with _net(spec, rec_stride=stride, rec_capacity=frames) as net:
@@ -195,5 +192,5 @@ def test_euler_adjoint_checkpoint_spacing_step_offset_and_recorded_span():
         net.integrate(nsteps)
         rec = net.adjoint(nsteps, gt, 0)
         net.status()
-        assert _rel(rec[0].cpu().numpy(), a[0]) <= 1e-5
-        assert _rel(rec[1].cpu().numpy(), a[1]) <= 1e-5
+        assert grad_error(rec[0].cpu().numpy(), a[0]) <= 1e-5
+        assert grad_error(rec[1].cpu().numpy(), a[1]) <= 1e-5

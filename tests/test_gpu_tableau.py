@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 from paper_1906_03958_gb300 import netgen as ng
+from tests.helpers import grad_error
 from tests.helpers import step_error
 
 pytestmark = pytest.mark.gpu
@@ -90,10 +91,6 @@ def test_tableau_cta_equals_grid_chunked_and_graph_bitwise(gate_mode):
     assert np.ptp(out[0][0][:spec.n_neurons]) > 10.0
 
 
-def _rel(a, b):
-    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30)
-
-
 @pytest.mark.parametrize("tab,sets", [(HEUN3, 1), (MIDPOINT, 3)], ids=["heun3", "midpoint-batch"])
 def test_tableau_adjoint_matches_oracle(tab, sets):
     import torch
@@ -111,8 +108,8 @@ def test_tableau_adjoint_matches_oracle(tab, sets):
     gw, gp, gy = (x.cpu().numpy() for x in res[0])
     for b in range(spec.n_nets):
         s0, s1 = spec.row_ptr[spec.net_neuron_off[b]], spec.row_ptr[spec.net_neuron_off[b + 1]]
-        assert _rel(gw[s0:s1], gw64[s0:s1]) <= GRAD_TOL
-        assert _rel(gp[2 * b:2 * b + 2], gp64[2 * b:2 * b + 2]) <= GRAD_TOL
-    assert _rel(gy.ravel(), gy64[:4 * spec.n_neurons]) <= GRAD_TOL
+        assert grad_error(gw[s0:s1], gw64[s0:s1]) <= GRAD_TOL
+        assert grad_error(gp[2 * b:2 * b + 2], gp64[2 * b:2 * b + 2]) <= GRAD_TOL
+    assert grad_error(gy.ravel(), gy64[:4 * spec.n_neurons]) <= GRAD_TOL
     for x, y in zip(res[1], res[0]):
-        assert _rel(x.cpu().numpy(), y.cpu().numpy()) <= 1e-5
+        assert grad_error(x.cpu().numpy(), y.cpu().numpy()) <= 1e-5

@@ -155,3 +155,22 @@ def test_checkpoint_spacing_does_not_change_gradients():
     for o in out[1:]:
         for a, b in zip(out[0], o):
             np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14)
+
+
+def test_full_size_differentiated_adjoint_matches_finite_differences():
+    # The stored FP64 oracle adjoint of the full differentiated workload
+    # (120 neurons, dense weights + GABA_B, 20,000 RK4 steps, checkpoints
+    # every 1,000; tests/golden/make_adjoint_al120.py) against the stored
+    # FP64 central differences on 10 coordinates, each taken at the step of
+    # the ladder whose neighbour agrees best, within 1e-4 of the difference
+    # plus its own error bound.
+    import os
+    from tests.helpers import fd_reference
+    G = np.load(os.path.join(os.path.dirname(__file__), "golden", "adjoint_al120_20k.npz"))
+    ref, err = fd_reference(G["fd"])
+    got = [G["gw"][k] for k in G["fd_w_index"]] + [G["gp"][tuple(p)] for p in G["fd_p_index"]]
+    for c, (x, want, e) in enumerate(zip(got, ref, err)):
+        assert abs(x - want) <= 1e-4 * abs(want) + e, (c, x, want, e)
+    # the functional the gradients belong to is the seeded one the script describes
+    from tests.golden import make_adjoint_al120 as gold
+    assert int(G["g_seed"]) == gold.G_SEED and int(G["nsteps"]) == gold.NSTEPS
