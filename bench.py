@@ -50,7 +50,36 @@ FLOP_PAIR1_STAGE = 2         # per-pair gates: G = P + Q r0 of a first-order (ne
 FLOP_PAIR2_STAGE = 10        # per-pair gates, second order: + s map, s^4 / (s^4 + Kd)
 # (per-pair gates: gate maps are updated for the pairs that have synapses only)
 FP32_LANES_PER_SM = 128
-N_SMS = 152
+
+# Discrete adjoint (psst_adjoint), FP32 FLOP per RK4 step, counted from the
+# kernel source: the forward recompute of the segment (synapse: A and B
+# sums, 5 per stage; neuron: 80 per stage; every (neuron, type) pair:
+# transmitter, r and s slopes and stage values, G, 23 per stage) plus the
+# reverse sweep (neuron: stage adjoint, rate derivatives, Jacobian-transpose
+# products, nine parameter gradients, ~165 per stage and 8 per step;
+# synapse: column sum 4 per stage, weight gradient 4 per stage and 1 per
+# step; pair: stage adjoint, transmitter derivative, gate products ~35 per
+# stage and 4 per step).
+ADJ_FLOP_SYN_STEP = 4 * 5 + 4 * 4 + 4 * 4 + 1          # 53
+ADJ_FLOP_NEURON_STEP = 4 * 80 + 4 * 165 + 8             # 988
+ADJ_FLOP_PAIR_STEP = 4 * 23 + 4 * 35 + 4                # 236
+
+# Bytes per RK4 step of the large sparse network if its state streamed from
+# HBM every step (synapse: gate r read + written 8 B, weight + index 8 B;
+# neuron: V, m, h, n read + written 32 B).
+STREAM_BYTES_SYN_STEP = 16
+STREAM_BYTES_NEURON_STEP = 32
+
+
+def device_sms() -> int:
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def fp32_peak_tflops(smax_mhz: float) -> float:
+    """FP32 FMA-pipe peak of the current device: SMs x 128 lanes x 2 FLOP x
+    the maximum SM clock."""
+    return device_sms() * FP32_LANES_PER_SM * 2 * smax_mhz * 1e6 / 1e12
 
 
 def workload_flops_per_step(spec, pair_gates: bool = True) -> float:
@@ -104,9 +133,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, workload: str):
+def traffic_for(kernel: str, workload: str, steps: int | None = None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    on the current kernel sources; else None.  An entry captured on a
+    launch of fewer steps than the timed one (``captured_steps``) is scaled
+    to ``steps`` (its traffic grows in proportion with the steps)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         t = json.load(open(p))
@@ -115,7 +146,10 @@ def traffic_for(kernel: str, workload: str):
     e = t.get(f"{kernel}:{workload}")
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("bytes_per_launch")
+    b = e.get("bytes_per_launch")
+    if b is not None and steps and e.get("captured_steps"):
+        b = b * steps / e["captured_steps"]
+    return b
 
 
 # ----------------------------------------------------------------- clocks
@@ -376,7 +410,7 @@ def main():
         from paper_1906_03958_gb300 import netgen as ng
         peaks = measured_peaks()
         smax = peaks.get("sm_max_mhz", 2070.0)
-        peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
+        peak_tflops = fp32_peak_tflops(smax)
 
         def timed(spec, nsteps, reps):
             with psst.Network(spec) as inet:
@@ -426,11 +460,30 @@ def main():
             sn.status()
             sinfo = sn.info()
             sms = e0.elapsed_time(e1)
+        peaks = measured_peaks()
+        smax = peaks.get("sm_max_mhz", 2070.0)
+        sec = sms / 1e3
+        sflop = workload_flops_per_step(sp, sinfo["n_pair_gate_nets"] == 1) * args.sparse_steps
+        sbytes = (STREAM_BYTES_SYN_STEP * sp.n_synapses + STREAM_BYTES_NEURON_STEP * sp.n_neurons) \
+            * args.sparse_steps
+        hbm = peaks.get("hbm_gbs")
+        straffic = traffic_for("grid_kernel", "sparse_large", args.sparse_steps)
         sparse = {"workload": "10,000 HH neurons (8k E, 2k I), p=0.02, ~2M synapses, Philox shot noise, "
                               f"grid mode over {sinfo['grid_ctas']} CTAs",
-                  "value": sp.n_neurons * args.sparse_steps / (sms / 1e3), "unit": UNIT,
+                  "value": sp.n_neurons * args.sparse_steps / sec, "unit": UNIT,
                   "us_per_rk4_step": sms * 1e3 / args.sparse_steps,
-                  "synapse_steps_per_s": sp.n_synapses * args.sparse_steps / (sms / 1e3)}
+                  "synapse_steps_per_s": sp.n_synapses * args.sparse_steps / sec,
+                  "roofline": {"bound": "alu", "achieved": sflop / sec / 1e12, "peak": fp32_peak_tflops(smax),
+                               "unit": "TFLOP/s", "frac": sflop / sec / 1e12 / fp32_peak_tflops(smax),
+                               "traffic": straffic,
+                               "kernel": "grid_kernel (one launch of the timed call)",
+                               "peak_source": "FP32 FMA pipes: SMs x 128 lanes x 2 x sm_max_mhz"},
+                  "roofline_if_streamed": {
+                      "bound": "hbm", "achieved": sbytes / sec / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": sbytes / sec / 1e9 / hbm if hbm else None,
+                      "note": f"{STREAM_BYTES_SYN_STEP} B per synapse and {STREAM_BYTES_NEURON_STEP} B per neuron "
+                              "per step if the state streamed from HBM; the kernel keeps it in shared memory, "
+                              "so this bound does not bind (traffic per launch is the measured DRAM bytes)"}}
 
     # ---- differentiated form: adjoint gradient time / forward time
     adjoint = None
@@ -462,14 +515,28 @@ def main():
             torch.cuda.synchronize()
             dn.status()
             fwd_ms, adj_ms = e0.elapsed_time(e1), e1b.elapsed_time(e2)
+        peaks = measured_peaks()
+        smax = peaks.get("sm_max_mhz", 2070.0)
+        pairs = start.n_neurons * start.syn_params.shape[0]
+        aflop = (ADJ_FLOP_SYN_STEP * start.n_synapses + ADJ_FLOP_NEURON_STEP * start.n_neurons
+                 + ADJ_FLOP_PAIR_STEP * pairs) * T
+        atraffic = traffic_for("adj_kernel", "differentiated", T)
         adjoint = {"workload": f"64 antennal-lobe parameter sets, dense 120x120 W + GABA_B, {T} steps, "
                                f"checkpoint every {args.ckpt_every} (recorded by the forward), segment recompute",
-                   "forward_ms": fwd_ms, "adjoint_ms": adj_ms, "ratio": adj_ms / fwd_ms}
+                   "forward_ms": fwd_ms, "adjoint_ms": adj_ms, "ratio": adj_ms / fwd_ms,
+                   "roofline": {"bound": "alu", "achieved": aflop / (adj_ms / 1e3) / 1e12,
+                                "peak": fp32_peak_tflops(smax), "unit": "TFLOP/s",
+                                "frac": aflop / (adj_ms / 1e3) / 1e12 / fp32_peak_tflops(smax),
+                                "traffic": atraffic,
+                                "kernel": "adj_kernel (one launch: segment recompute and reverse sweep)",
+                                "flop_per_step": {"synapse": ADJ_FLOP_SYN_STEP, "neuron": ADJ_FLOP_NEURON_STEP,
+                                                  "neuron_type_pair": ADJ_FLOP_PAIR_STEP}}}
 
     # ---- roofline of the dominant kernel (the CTA-resident integrator)
     peaks = measured_peaks()
     smax = peaks.get("sm_max_mhz", 2070.0)
-    peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
+    n_sms = device_sms()
+    peak_tflops = fp32_peak_tflops(smax)
     # one integrate call = the size-class launches back to back, together
     # covering every network once: its FLOP over its duration
     pair_gates = info["n_pair_gate_nets"] == spec.n_nets
@@ -480,7 +547,7 @@ def main():
             "traffic": traffic_for("net_kernel", args.workload),
             "kernel": f"net_kernel: the {info['n_launch_classes']} size-class launches of one integrate call",
             "gates": "per (presynaptic neuron, type) pair" if pair_gates else "per synapse",
-            "peak_source": f"FP32 FMA pipes: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+            "peak_source": f"FP32 FMA pipes: {n_sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                            f"{smax:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"}
 
     if rank == 0:

@@ -110,6 +110,7 @@ struct psst_net {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_nsteps = 0;
+    long long graph_step0 = 0;  // first step of the captured call
     int graph_launches = 0;
     float *tune_buf = nullptr;  // state copy for autotuning trials
     uint8_t *d_check = nullptr; // per-network result of the pair-uniformity check
@@ -981,16 +982,20 @@ int launch_chunks(psst_net *h, long long step0, long long n_steps, long long chu
     return PSST_OK;
 }
 
-// Kernel nodes take the global step index as an argument: net_kernel's 4th
-// (v, list, plans, step0, nsteps, lrep_cap), grid_kernel's 3rd (v, g, step0, nsteps).
+// Kernel nodes take the global step index as an argument: net_kernel's and
+// indep_kernel's 4th (v, list, plans | ind_neuron, ind_net, step0, ...),
+// grid_kernel's 3rd (v, g, step0, nsteps).  The captured graph keeps each
+// node's arguments as captured, so a node's step index minus the step at
+// capture is its offset within the call (0, or a multiple of the launch
+// chunk when the call spans several chunks); the replay gives it the same
+// offset from its own first step, whatever order the nodes are listed in.
 int patch_step0(psst_net *h, long long step0) {
     size_t n = 0;
     cudaError_t e = cudaGraphGetNodes(h->graph, nullptr, &n);
     std::vector<cudaGraphNode_t> nodes(n);
     if (e == cudaSuccess && n) e = cudaGraphGetNodes(h->graph, nodes.data(), &n);
-    long long chunk_base = 0;
-    const long long chunk = 1LL << 30;
-    int k = 0;
+    const int idx = h->mode == PSST_MODE_GRID ? 2 : 3;
+    const int nargs = h->mode == PSST_MODE_GRID ? 4 : 6;
     for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
         cudaGraphNodeType t;
         e = cudaGraphNodeGetType(nodes[i], &t);
@@ -998,19 +1003,13 @@ int patch_step0(psst_net *h, long long step0) {
         cudaKernelNodeParams p;
         e = cudaGraphKernelNodeGetParams(nodes[i], &p);
         if (e != cudaSuccess) break;
-        const int idx = h->mode == PSST_MODE_GRID ? 2 : 3;
-        const int nargs = h->mode == PSST_MODE_GRID ? 4 : 6;
-        // launches of one chunk share step0; chunks follow in capture order
-        const int per_chunk =
-            h->mode == PSST_MODE_GRID ? 1 : (int)h->classes.size() + (h->n_ind_neurons > 0 ? 1 : 0);
-        chunk_base = (long long)(k / per_chunk) * chunk;
-        long long s = step0 + chunk_base;
+        const long long captured = *(const long long *)p.kernelParams[idx];
+        long long s = step0 + (captured - h->graph_step0);
         void *args[6];
         for (int q = 0; q < nargs; ++q) args[q] = p.kernelParams[q];
         args[idx] = &s;
         p.kernelParams = args;
         e = cudaGraphExecKernelNodeSetParams(h->graph_exec, nodes[i], &p);
-        ++k;
     }
     return e == cudaSuccess ? PSST_OK : cuda_fail(e, "graph update");
 }
@@ -1041,6 +1040,7 @@ int replay_steps(psst_net *h, long long step0, long long n_steps, cudaStream_t s
         }
         h->graph = g;
         h->graph_nsteps = n_steps;
+        h->graph_step0 = step0;
         h->graph_launches = h->launches;
     } else {
         const int rc = patch_step0(h, step0);

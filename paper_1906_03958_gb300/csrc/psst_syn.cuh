@@ -412,10 +412,13 @@ __device__ inline void load_items_pair(Items &it, const NetView &v, long long ro
 // side (entry e, copy c at e * 2^lrep + c) and lane l reads copy
 // l mod 2^lrep: with 32 copies the 32 lanes of a gather hit 32 different
 // banks whatever the entries.
-__device__ __forceinline__ void sphase_pair(const Items &it, const float *Gt, int lrep) {
-    const int tid = threadIdx.x, nthr = blockDim.x, K = it.K, n = it.n1;
+// sphase_pair_range: the items [t0, t1) by the threads j = 0..nthr-1 of a
+// group (thread j takes items t0 + j, t0 + j + nthr, ...).
+__device__ __forceinline__ void sphase_pair_range(const Items &it, const float *Gt, int lrep, int t0, int t1, int j,
+                                                  int nthr) {
+    const int K = it.K, n = it.n1;
     const float *Gl = Gt + (threadIdx.x & ((1 << lrep) - 1));
-    for (int t = tid; t < n; t += nthr) {
+    for (int t = t0 + j; t < t1; t += nthr) {
         float A = 0.0f;
 #pragma unroll 4
         for (int j = 0; j < K; ++j) {  // unrolled: several chunks' loads in flight, sums in order
@@ -430,6 +433,10 @@ __device__ __forceinline__ void sphase_pair(const Items &it, const float *Gt, in
         }
         it.pa[t] = A;
     }
+}
+
+__device__ __forceinline__ void sphase_pair(const Items &it, const float *Gt, int lrep) {
+    sphase_pair_range(it, Gt, lrep, 0, it.n1, threadIdx.x, blockDim.x);
 }
 
 // Synaptic current of owned row i from its typed items (fixed order).

@@ -44,14 +44,15 @@ def grad_error(got, want, floor_frac=GRAD_FLOOR):
 
 
 def fd_reference(fd):
-    """Per coordinate, the central difference of the step-ladder rung whose
-    neighbour agrees best, and that disagreement as its error bound.
-    fd: [rungs, coordinates], the step growing by a constant factor per
-    rung.  Small steps carry the rounding noise of the FP64 trajectory
-    divided by h, large ones truncation error O(h^2); neighbouring rungs
-    that agree bound both."""
+    """Per coordinate, a central-difference value and its error bound from a
+    step ladder.  fd: [rungs, coordinates], the step growing by a constant
+    factor per rung.  Small steps carry the rounding noise of the FP64
+    trajectory divided by h, large ones truncation error O(h^2), so the
+    differences converge toward the derivative and then drift away; the
+    neighbouring pair of rungs that agree best is taken, its midpoint as the
+    value and its full gap as the bound."""
     fd = np.asarray(fd, np.float64)
     e = np.abs(np.diff(fd, axis=0))
     j = np.argmin(e, axis=0)
     c = np.arange(fd.shape[1])
-    return fd[j, c], e[j, c]
+    return 0.5 * (fd[j, c] + fd[j + 1, c]), e[j, c]

@@ -160,7 +160,8 @@ def test_checkpoint_spacing_does_not_change_gradients():
 def test_full_size_differentiated_adjoint_matches_finite_differences():
     # The stored FP64 oracle adjoint of the full differentiated workload
     # (120 neurons, dense weights + GABA_B, 20,000 RK4 steps, checkpoints
-    # every 1,000; tests/golden/make_adjoint_al120.py) against the stored
+    # every 1,000; mean-square PN trace loss; tests/golden/make_adjoint_al120.py)
+    # against the stored
     # FP64 central differences on 10 coordinates, each taken at the step of
     # the ladder whose neighbour agrees best, within 1e-4 of the difference
     # plus its own error bound.
@@ -171,6 +172,6 @@ def test_full_size_differentiated_adjoint_matches_finite_differences():
     got = [G["gw"][k] for k in G["fd_w_index"]] + [G["gp"][tuple(p)] for p in G["fd_p_index"]]
     for c, (x, want, e) in enumerate(zip(got, ref, err)):
         assert abs(x - want) <= 1e-4 * abs(want) + e, (c, x, want, e)
-    # the functional the gradients belong to is the seeded one the script describes
+    # the loss the gradients belong to is the one the script describes
     from tests.golden import make_adjoint_al120 as gold
-    assert int(G["g_seed"]) == gold.G_SEED and int(G["nsteps"]) == gold.NSTEPS
+    assert int(G["nsteps"]) == gold.NSTEPS and int(G["n_pn"]) == gold.N_PN
