@@ -73,19 +73,18 @@ struct SmemCoef {
     __device__ __forceinline__ float4 s(int i) const { return t2[i]; }
 };
 
-// One stage of kind ST (psst_syn.cuh: 0..3 classic RK4, 4 forward Euler,
-// 8..23 a tableau's stages).  par selects the double-buffered stage
-// potentials and gates read by this stage: the parity of the stage's index
-// counted over the launch.
-template <int ST, int CL, bool HAS2, bool PAIR>
-__device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0, int N, int nt, int M, int r_lo,
-                                      int nown, unsigned rank, long long rec_slot, float dt, float *vst, float *y0,
-                                      float *acc, float *ys, const float *prm, const float *iext, float2 *cur1,
-                                      float2 *acc1, float2 *fin1, float4 *cur2, float4 *acc2, float4 *fin2,
-                                      float *pst, float *Gt, int lrep, const float *stab, int par) {
-    constexpr bool FIRST = stage_first(ST), LAST = stage_last(ST);
+// One stage sg of the handle's method (its flags and coefficients at run
+// time: one copy of this code serves every stage of RK4, Euler and a
+// tableau).  par selects the double-buffered stage potentials and gates read
+// by this stage: the parity of the stage's index counted over the launch.
+template <int CL, bool HAS2, bool PAIR>
+__device__ __forceinline__ void stage(const NetView &v, const StageRT &sg, const Items &it, int n0, int N, int nt,
+                                      int M, int r_lo, int nown, unsigned rank, long long rec_slot, float *vst,
+                                      float *y0, float *acc, float *ys, const float *prm, const float *iext,
+                                      float2 *cur1, float2 *acc1, float2 *fin1, float4 *cur2, float4 *acc2,
+                                      float4 *fin2, float *pst, float *Gt, int lrep, const float *stab, int par) {
+    const bool FIRST = sg.first, LAST = sg.last;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const StageCoef sc = stage_coef<ST>(v, dt);
     const float *vcur = vst + par * N;
     float *vnxt = vst + (par ^ 1) * N;
     const float *ysc = ys + par * 3 * nown;
@@ -97,10 +96,9 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
     // potentials: they are computed before the S-phase (on the highest
     // threads), where their latency overlaps the S-phase's loads, and leave
     // the N-phase fewer units.
-    for (int i = nthr - 1 - tid; i < nown; i += nthr)
-        neuron_gates<ST>(i, nown, vcur[r_lo + i], ysc, ysn, y0, acc, sc);
+    for (int i = nthr - 1 - tid; i < nown; i += nthr) neuron_gates(sg, i, nown, vcur[r_lo + i], ysc, ysn, y0, acc);
     if (PAIR) sphase_pair(it, Gt, lrep);
-    else sphase<ST, HAS2>(it, SmemCoef{FIRST ? fin1 : cur1, FIRST ? fin2 : cur2});
+    else sphase<HAS2>(FIRST, it, SmemCoef{FIRST ? fin1 : cur1, FIRST ? fin2 : cur2});
     __syncthreads();
     // independent work units: potential of each owned neuron and the gate
     // map (and per-pair gate) of each entry; the potentials take whole warps
@@ -111,9 +109,9 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
             if (u >= nown) continue;
             const int i = u;
             const float V = vcur[r_lo + i];
-            const VPre pre = neuron_v_pre<ST>(i, nown, V, ysc, y0, acc, prm, iext[i]);
+            const VPre pre = neuron_v_pre(sg, i, nown, V, ysc, y0, acc, prm, iext[i]);
             const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
-            const float vn = neuron_v_post<ST>(i, pre, isyn, y0, acc, sc);
+            const float vn = neuron_v_post(sg, i, pre, isyn, y0, acc);
             vnxt[r_lo + i] = vn;
             if (CL > 1) {
 #pragma unroll
@@ -128,7 +126,7 @@ __device__ __forceinline__ void stage(const NetView &v, const Items &it, int n0,
             float4 &f2 = HAS2 ? fin2[p] : d4;
             const int ci = PAIR ? (int)pof[p] : p;  // (neuron, type) pair of the entry
             const float *sp = stab + (ci % nt) * 9;
-            coef_update<ST, HAS2>(sp, vcur[ci / nt], sc, cur1[p], acc1[p], fin1[p], c2, a2, f2);
+            coef_update<HAS2>(sp, vcur[ci / nt], sg, cur1[p], acc1[p], fin1[p], c2, a2, f2);
             if (PAIR) {
                 // the pair's gate for the next stage (same operations as the per-synapse path)
                 const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
@@ -231,6 +229,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     if (CL > 1) cluster_sync();
 
     const float dt = v.dt;
+    const int ns = method_stages(v);
     // record: phase of (step + 1) modulo the stride, advanced once per step
     int rec_phase = v.rec_stride > 0 ? (int)((step0 + 1) % v.rec_stride) : -1;
     for (int itn = 0; itn < nsteps; ++itn) {
@@ -244,34 +243,12 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         for (int i = tid; i < nown; i += nthr)
             iext[i] = input_current(v, inp[i], inp[nown + i], in_pulse, (long long)n0 + r_lo + i, step);
         // iext is read in the N-phase, after the S-phase barrier
-        if (v.method == PSST_METHOD_EULER) {
-            stage<4, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm,
-                                     iext, cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, itn & 1);
-            continue;
-        }
-        if (v.method == PSST_METHOD_TABLEAU) {
-            // stage s of step itn reads parity (itn * n + s) & 1
-#define PSST_TAB_STAGE(n, s)                                                                                    \
-    stage<tableau_stage(n, s), CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, \
-                                               ys, prm, iext, cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep,   \
-                                               stab, (itn * (n) + (s)) & 1)
-            switch (v.rk_ns) {
-            case 1: PSST_TAB_STAGE(1, 0); break;
-            case 2: PSST_TAB_STAGE(2, 0); PSST_TAB_STAGE(2, 1); break;
-            case 3: PSST_TAB_STAGE(3, 0); PSST_TAB_STAGE(3, 1); PSST_TAB_STAGE(3, 2); break;
-            default: PSST_TAB_STAGE(4, 0); PSST_TAB_STAGE(4, 1); PSST_TAB_STAGE(4, 2); PSST_TAB_STAGE(4, 3); break;
-            }
-#undef PSST_TAB_STAGE
-            continue;
-        }
-        stage<0, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, 0);
-        stage<1, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, 1);
-        stage<2, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, 0);
-        stage<3, CL, HAS2, PAIR>(v, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, dt, vst, y0, acc, ys, prm, iext,
-                                 cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, 1);
+        // stage s of step itn reads parity (itn * ns + s) & 1
+#pragma unroll 1
+        for (int s = 0; s < ns; ++s)
+            stage<CL, HAS2, PAIR>(v, stage_rt(v, s, dt), it, n0, N, nt, M, r_lo, nown, rank, rec_slot, vst, y0, acc,
+                                  ys, prm, iext, cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab,
+                                  (itn * ns + s) & 1);
     }
 
     // write back: owned synapses with the last step's gate map, owned neurons

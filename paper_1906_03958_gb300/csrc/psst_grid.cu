@@ -102,22 +102,22 @@ struct GlobalCoef {
     __device__ __forceinline__ float4 s(int i) const { return __ldcg(t2 + i); }
 };
 
-// One stage of kind ST (psst_syn.cuh: 0..3 classic RK4, 4 forward Euler,
-// 8..23 a tableau's stages); par selects the double-buffered potentials,
-// gates and global tables this stage reads (the parity of the stage's index
-// counted over the launch).  On entry the
-// owned neurons' gates m, h, n of this stage are done and tgt is the barrier
-// count to wait for; on return the CTA has arrived at the stage's closing
-// barrier (tgt updated) and, when `more`, computed the next stage's gates.
-template <int ST, bool HAS2, bool PAIR>
-__device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, const Items &it, int lo, int N,
-                                           int nt, int M, long long rec_slot, float dt, float *vst, float *y0,
-                                           float *acc, float *ys, const float *prm, const float *iext,
-                                           float2 *cur1, float2 *acc1, float4 *cur2, float4 *acc2, float *pst,
-                                           float *gtab, const float *stab, int par, unsigned long long &tgt,
-                                           bool more) {
-    constexpr bool LAST = stage_last(ST);
-    const StageCoef sc = stage_coef<ST>(v, dt);
+// One stage sg of the handle's method (flags and coefficients at run time:
+// one copy of this code serves every stage of RK4, Euler and a tableau);
+// par selects the double-buffered potentials, gates and global tables this
+// stage reads (the parity of the stage's index counted over the launch).  On
+// entry the owned neurons' gates m, h, n of this stage are done and tgt is
+// the barrier count to wait for; on return the CTA has arrived at the
+// stage's closing barrier (tgt updated) and, when `more`, computed the next
+// stage's (sx's) gates.
+template <bool HAS2, bool PAIR>
+__device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, const StageRT &sg,
+                                           const StageRT &sx, const Items &it, int lo, int N, int nt, int M,
+                                           long long rec_slot, float *vst, float *y0, float *acc, float *ys,
+                                           const float *prm, const float *iext, float2 *cur1, float2 *acc1,
+                                           float4 *cur2, float4 *acc2, float *pst, float *gtab, const float *stab,
+                                           int par, unsigned long long &tgt, bool more) {
+    const bool LAST = sg.last;
     const int tid = threadIdx.x, nthr = blockDim.x, Mloc = N * nt;
     const float *vcur = vst + par * N;
     float *vnxt = vst + (par ^ 1) * N;
@@ -135,7 +135,7 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
         __syncthreads();
         sphase_pair(it, gtab, 0);
     } else {
-        sphase<ST, HAS2>(it, GlobalCoef{g.c1 + (size_t)par * M, HAS2 ? g.c2 + (size_t)par * M : nullptr});
+        sphase<HAS2>(sg.first, it, GlobalCoef{g.c1 + (size_t)par * M, HAS2 ? g.c2 + (size_t)par * M : nullptr});
     }
     __syncthreads();
     // independent work units: potential of each owned neuron and the gate map
@@ -151,9 +151,9 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
             if (u >= N) continue;
             const int i = u;
             const float V = vcur[i];
-            const VPre pre = neuron_v_pre<ST>(i, N, V, ysc, y0, acc, prm, iext[i]);
+            const VPre pre = neuron_v_pre(sg, i, N, V, ysc, y0, acc, prm, iext[i]);
             const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
-            const float vn = neuron_v_post<ST>(i, pre, isyn, y0, acc, sc);
+            const float vn = neuron_v_post(sg, i, pre, isyn, y0, acc);
             vnxt[i] = vn;
             if (LAST && rec_slot >= 0) v.rec[rec_slot * v.N + lo + i] = vn;
         } else {
@@ -168,7 +168,7 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
                 float4 &c2 = HAS2 ? cur2[p] : d4;
                 float4 &a2 = HAS2 ? acc2[p] : d4;
                 const float *sp = stab + (p % nt) * 9;
-                coef_update<ST, HAS2>(sp, vcur[p / nt], sc, cur1[p], acc1[p], f1, c2, a2, f2);
+                coef_update<HAS2>(sp, vcur[p / nt], sg, cur1[p], acc1[p], f1, c2, a2, f2);
                 const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
                 float G;
                 if (!LAST) {
@@ -187,7 +187,7 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
                 float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = f2;
                 float4 &c2 = HAS2 ? cur2[p] : d4;
                 float4 &a2 = HAS2 ? acc2[p] : d4;
-                coef_update<ST, HAS2>(stab + (p % nt) * 9, vcur[p / nt], sc, cur1[p], acc1[p], f1, c2, a2, f2);
+                coef_update<HAS2>(stab + (p % nt) * 9, vcur[p / nt], sg, cur1[p], acc1[p], f1, c2, a2, f2);
                 o1[p] = LAST ? f1 : cur1[p];
                 if (HAS2) o2[p] = LAST ? f2 : cur2[p];
             }
@@ -197,11 +197,9 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
     if (more) {
         // the next stage's gates of the owned neurons (own data only) while
         // the other CTAs arrive; that stage reads this one's ysn and vnxt
-        // after a step's last stage comes the first stage of the next step
-        constexpr int NX = !LAST ? ST + 1 : ST >= 8 ? ST - (ST & 3) : ST == 4 ? 4 : 0;
-        const StageCoef sx = stage_coef<NX>(v, dt);
+        // (after a step's last stage comes the first stage of the next step)
         float *ysx = ys + par * 3 * N;
-        for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates<NX>(i, N, vnxt[i], ysn, ysx, y0, acc, sx);
+        for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates(sx, i, N, vnxt[i], ysn, ysx, y0, acc);
     }
     return true;
 }
@@ -281,28 +279,15 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         load_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.weight, v.syn_code, stab, tmp);
     }
     const float dt = v.dt;
+    const int ns = method_stages(v);
     unsigned long long tgt = grid_arrive(g.bar);
     // the first stage's gates (own data) while the other CTAs finish setting up
     {
         const float *ysc = ys, *vcur = vst;
         float *ysn = ys + 3 * N;
         if (nsteps > 0) {
-#define PSST_FIRST_GATES(K)                                                                                     \
-    for (int i = nthr - 1 - tid; i < N; i += nthr)                                                              \
-        neuron_gates<K>(i, N, vcur[i], ysc, ysn, y0, acc, stage_coef<K>(v, dt))
-            if (v.method == PSST_METHOD_EULER) {
-                PSST_FIRST_GATES(4);
-            } else if (v.method == PSST_METHOD_TABLEAU) {
-                switch (v.rk_ns) {
-                case 1: PSST_FIRST_GATES(tableau_stage(1, 0)); break;
-                case 2: PSST_FIRST_GATES(tableau_stage(2, 0)); break;
-                case 3: PSST_FIRST_GATES(tableau_stage(3, 0)); break;
-                default: PSST_FIRST_GATES(tableau_stage(4, 0)); break;
-                }
-            } else {
-                PSST_FIRST_GATES(0);
-            }
-#undef PSST_FIRST_GATES
+            const StageRT s0 = stage_rt(v, 0, dt);
+            for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates(s0, i, N, vcur[i], ysc, ysn, y0, acc);
         }
     }
     bool ok = true;
@@ -319,38 +304,14 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         for (int i = tid; i < N; i += nthr)
             iext[i] = input_current(v, inp[i], inp[N + i], in_pulse, (long long)lo + i, step);
         const bool more = itn + 1 < nsteps;
-        if (v.method == PSST_METHOD_EULER) {
-            ok = grid_stage<4, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab, itn & 1, tgt, more);
-            continue;
+        // stage s of step itn reads parity (itn * ns + s) & 1
+#pragma unroll 1
+        for (int s = 0; ok && s < ns; ++s) {
+            const StageRT sg = stage_rt(v, s, dt), sx = stage_rt(v, s + 1 < ns ? s + 1 : 0, dt);
+            ok = grid_stage<HAS2, PAIR>(v, g, sg, sx, it, lo, N, nt, M, rec_slot, vst, y0, acc, ys, prm, iext, cur1,
+                                        acc1, cur2, acc2, pst, gtab, stab, (itn * ns + s) & 1, tgt,
+                                        s + 1 < ns || more);
         }
-        if (v.method == PSST_METHOD_TABLEAU) {
-            // stage s of step itn reads parity (itn * n + s) & 1
-#define PSST_TAB_STAGE(n, s)                                                                                    \
-    if (ok)                                                                                                     \
-        ok = grid_stage<tableau_stage(n, s), HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys,  \
-                                                         prm, iext, cur1, acc1, cur2, acc2, pst, gtab, stab,      \
-                                                         (itn * (n) + (s)) & 1, tgt, (s) + 1 < (n) || more)
-            switch (v.rk_ns) {
-            case 1: PSST_TAB_STAGE(1, 0); break;
-            case 2: PSST_TAB_STAGE(2, 0); PSST_TAB_STAGE(2, 1); break;
-            case 3: PSST_TAB_STAGE(3, 0); PSST_TAB_STAGE(3, 1); PSST_TAB_STAGE(3, 2); break;
-            default: PSST_TAB_STAGE(4, 0); PSST_TAB_STAGE(4, 1); PSST_TAB_STAGE(4, 2); PSST_TAB_STAGE(4, 3); break;
-            }
-#undef PSST_TAB_STAGE
-            continue;
-        }
-        ok = grid_stage<0, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                       acc1, cur2, acc2, pst, gtab, stab, 0, tgt, true);
-        if (ok)
-            ok = grid_stage<1, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab, 1, tgt, true);
-        if (ok)
-            ok = grid_stage<2, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab, 0, tgt, true);
-        if (ok)
-            ok = grid_stage<3, HAS2, PAIR>(v, g, it, lo, N, nt, M, rec_slot, dt, vst, y0, acc, ys, prm, iext, cur1,
-                                           acc1, cur2, acc2, pst, gtab, stab, 1, tgt, more);
         // the next step's input currents (own data) run before stage 0's wait
     }
     // the last stage's (or the setup's) barrier
@@ -378,8 +339,7 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
     } else {
         // the last stage wrote the step's final maps into the table of the
         // launch's stage count's parity (RK4: four stages per step, table 0)
-        const long long nst = v.method == PSST_METHOD_EULER ? 1 : v.method == PSST_METHOD_TABLEAU ? v.rk_ns : 4;
-        const size_t fin = (size_t)((nsteps * nst) & 1);
+        const size_t fin = (size_t)(((long long)nsteps * ns) & 1);
         store_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.syn_code, stab,
                           GlobalCoef{g.c1 + fin * M, HAS2 ? g.c2 + fin * M : nullptr});
     }

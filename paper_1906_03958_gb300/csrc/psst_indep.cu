@@ -23,9 +23,9 @@ constexpr int INDEP_THREADS = 256;
 template <int ST>
 __device__ __forceinline__ float indep_stage(const NetView &v, float V, const float *ysc, float *ysn, float *y0,
                                              float *acc, const float *prm, float iext, float dt) {
-    const StageCoef sc = stage_coef<ST>(v, dt);
-    neuron_gates<ST>(0, 1, V, ysc, ysn, y0, acc, sc);
-    return neuron_v<ST>(0, 1, V, ysc, y0, acc, prm, iext, 0.0f, sc);
+    const StageCT<ST> sg{stage_coef<ST>(v, dt)};
+    neuron_gates(sg, 0, 1, V, ysc, ysn, y0, acc);
+    return neuron_v(sg, 0, 1, V, ysc, y0, acc, prm, iext, 0.0f);
 }
 
 // Thread t integrates neuron ind_neuron[t] of network ind_net[t] for nsteps

@@ -189,20 +189,18 @@ __device__ void store_items(const Items &it, const NetView &v, long long row_g0,
 // One synapse of the current stage: gate value from the affine map, then
 // accumulate A += w G, B += wE G.  At the step's first stage the previous
 // step's final map is applied and the new step-start gate stored.
-template <bool FIRST_STAGE>
-__device__ __forceinline__ void syn1(float &r, float w, float we, float2 F, float &A, float &B) {
+__device__ __forceinline__ void syn1(bool first, float &r, float w, float we, float2 F, float &A, float &B) {
     const float g = fmaf(F.y, r, F.x);
-    if (FIRST_STAGE) r = g;
+    if (first) r = g;
     A = fmaf(w, g, A);
     B = fmaf(we, g, B);
 }
 
-template <bool FIRST_STAGE>
-__device__ __forceinline__ void syn2(float &r, float &s, float w, float we, float2 F, float4 F2, float &A,
-                                     float &B) {
+__device__ __forceinline__ void syn2(bool first, float &r, float &s, float w, float we, float2 F, float4 F2,
+                                     float &A, float &B) {
     const float rr = fmaf(F.y, r, F.x);
     const float ss = fmaf(F2.z, s, fmaf(F2.y, r, F2.x));
-    if (FIRST_STAGE) {
+    if (first) {
         r = rr;
         s = ss;
     }
@@ -244,17 +242,55 @@ __device__ __forceinline__ StageCoef stage_coef(const NetView &v, float dt) {
     return c;
 }
 
-// The first stage's term of the step's sum (RK4 and Euler: weight 1).
+// Stage descriptors: whether the stage is its step's first and last, its
+// coefficients, and the first stage's term of the step's sum.  StageCT<ST>
+// fixes the kind at compile time (kernels unrolled per stage kind);
+// StageRT carries it at run time, so that one copy of the stage code serves
+// every stage of every method (the classic RK4 and Euler stages as the
+// tableau stages with the same coefficients: their first weight is 1, and
+// 1 * d is d, so both descriptors give the same bits).
 template <int ST>
-__device__ __forceinline__ float first_term(const StageCoef &c, float d) {
-    return ST >= 8 ? __fmul_rn(c.w, d) : d;
+struct StageCT {
+    static constexpr bool first = stage_first(ST), last = stage_last(ST);
+    StageCoef c;
+    __device__ __forceinline__ float first_term(float d) const { return ST >= 8 ? __fmul_rn(c.w, d) : d; }
+};
+
+struct StageRT {
+    bool first, last;
+    StageCoef c;
+    __device__ __forceinline__ float first_term(float d) const { return __fmul_rn(c.w, d); }
+};
+
+// Stages per step of the handle's method.
+__host__ __device__ inline int method_stages(const NetView &v) {
+    return v.method == PSST_METHOD_EULER ? 1 : v.method == PSST_METHOD_TABLEAU ? v.rk_ns : 4;
+}
+
+// Stage s of the handle's method at run time, with the coefficients
+// stage_coef gives the corresponding compile-time kind.
+__device__ __forceinline__ StageRT stage_rt(const NetView &v, int s, float dt) {
+    StageRT r;
+    const int ns = method_stages(v);
+    r.first = s == 0;
+    r.last = s == ns - 1;
+    if (v.method == PSST_METHOD_TABLEAU) {
+        r.c.w = v.rk_w[s];
+        r.c.cn = s < 3 ? v.rk_c[s < 3 ? s : 0] * dt : 0.0f;
+        r.c.fin = v.rk_beta * dt;
+    } else {
+        const bool euler = v.method == PSST_METHOD_EULER;
+        r.c.w = (!euler && (s == 1 || s == 2)) ? 2.0f : 1.0f;
+        r.c.cn = (!euler && s == 2) ? dt : 0.5f * dt;
+        r.c.fin = euler ? dt : dt * (1.0f / 6.0f);
+    }
+    return r;
 }
 
 // S-phase: every item's partial sums (A, B) at stage ST.  Coef supplies
 // r(ci) (float2 r-map) and s(ci) (float4 s-map, w = Kd).
-template <int ST, bool HAS2, class Coef>
-__device__ __forceinline__ void sphase(const Items &it, const Coef &cf) {
-    constexpr bool FIRST = stage_first(ST);
+template <bool HAS2, class Coef>
+__device__ __forceinline__ void sphase(bool FIRST, const Items &it, const Coef &cf) {
     const int tid = threadIdx.x, nthr = blockDim.x, K = it.K, n1 = it.n1;
     for (int t = tid; t < n1; t += nthr) {
         float A = 0.0f, B = 0.0f;
@@ -263,10 +299,10 @@ __device__ __forceinline__ void sphase(const Items &it, const Coef &cf) {
             float4 r = it.r[c];
             const float4 w = it.w[c], we = it.we[c];
             const ushort4 id = it.id[c];
-            syn1<FIRST>(r.x, w.x, we.x, cf.r(id.x), A, B);
-            syn1<FIRST>(r.y, w.y, we.y, cf.r(id.y), A, B);
-            syn1<FIRST>(r.z, w.z, we.z, cf.r(id.z), A, B);
-            syn1<FIRST>(r.w, w.w, we.w, cf.r(id.w), A, B);
+            syn1(FIRST, r.x, w.x, we.x, cf.r(id.x), A, B);
+            syn1(FIRST, r.y, w.y, we.y, cf.r(id.y), A, B);
+            syn1(FIRST, r.z, w.z, we.z, cf.r(id.z), A, B);
+            syn1(FIRST, r.w, w.w, we.w, cf.r(id.w), A, B);
             if (FIRST) it.r[c] = r;
         }
         it.pa[t] = A;
@@ -281,10 +317,10 @@ __device__ __forceinline__ void sphase(const Items &it, const Coef &cf) {
                 float4 r = it.r[c], s = it.s[c];
                 const float4 w = it.w[c], we = it.we[c];
                 const ushort4 id = it.id[c];
-                syn2<FIRST>(r.x, s.x, w.x, we.x, cf.r(id.x), cf.s(id.x), A, B);
-                syn2<FIRST>(r.y, s.y, w.y, we.y, cf.r(id.y), cf.s(id.y), A, B);
-                syn2<FIRST>(r.z, s.z, w.z, we.z, cf.r(id.z), cf.s(id.z), A, B);
-                syn2<FIRST>(r.w, s.w, w.w, we.w, cf.r(id.w), cf.s(id.w), A, B);
+                syn2(FIRST, r.x, s.x, w.x, we.x, cf.r(id.x), cf.s(id.x), A, B);
+                syn2(FIRST, r.y, s.y, w.y, we.y, cf.r(id.y), cf.s(id.y), A, B);
+                syn2(FIRST, r.z, s.z, w.z, we.z, cf.r(id.z), cf.s(id.z), A, B);
+                syn2(FIRST, r.w, s.w, w.w, we.w, cf.r(id.w), cf.s(id.w), A, B);
                 if (FIRST) {
                     it.r[c] = r;
                     it.s[c] = s;
@@ -495,11 +531,11 @@ __device__ __forceinline__ float pair_gate(bool second, float2 F, float4 F2, flo
 // map and the running RK4 sum; writes the next stage's map into cur, or at
 // the step's last stage the step's final map into fin.  The s-map's fourth
 // component carries Kd (1 for first-order types, whose s-map is never used).
-template <int ST, bool HAS2>
-__device__ __forceinline__ void coef_update(const float *sp, float V, const StageCoef &sc, float2 &cur,
-                                            float2 &acc, float2 &fin, float4 &cur2, float4 &acc2, float4 &fin2) {
-    constexpr bool FIRST = stage_first(ST), LAST = stage_last(ST);
-    const float WGT = sc.w, cnext = sc.cn, dt6 = sc.fin;
+template <bool HAS2, class SG>
+__device__ __forceinline__ void coef_update(const float *sp, float V, const SG &sg, float2 &cur, float2 &acc,
+                                            float2 &fin, float4 &cur2, float4 &acc2, float4 &fin2) {
+    const bool FIRST = sg.first, LAST = sg.last;
+    const float WGT = sg.c.w, cnext = sg.c.cn, dt6 = sg.c.fin;
     const float T = transmitter(V, sp[SP_VP], sp[SP_KP]);  // table holds 1/Kp
     // explicit roundings: no product is contracted into an FMA or folded
     // with a constant stage weight, so every kernel and stage kind (constant
@@ -516,7 +552,7 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, const Stag
         }
     }
     const float kP = fmaf(-bb, P, a_), kQ = __fmul_rn(-bb, Q);
-    float2 A1 = make_float2(first_term<ST>(sc, kP), first_term<ST>(sc, kQ));
+    float2 A1 = make_float2(sg.first_term(kP), sg.first_term(kQ));
     if (!FIRST) A1 = make_float2(fmaf(WGT, kP, acc.x), fmaf(WGT, kQ, acc.y));
     if (!LAST) {
         acc = A1;
@@ -529,7 +565,7 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, const Stag
         const float Kd = sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f;
         const float kU = fmaf(K3, P, __fmul_rn(-K4, U)), kX = fmaf(K3, Q, __fmul_rn(-K4, X));
         const float kZ = __fmul_rn(-K4, Z);
-        float4 A2 = make_float4(first_term<ST>(sc, kU), first_term<ST>(sc, kX), first_term<ST>(sc, kZ), 0.0f);
+        float4 A2 = make_float4(sg.first_term(kU), sg.first_term(kX), sg.first_term(kZ), 0.0f);
         if (!FIRST) A2 = make_float4(fmaf(WGT, kU, acc2.x), fmaf(WGT, kX, acc2.y), fmaf(WGT, kZ, acc2.z), 0.0f);
         if (!LAST) {
             acc2 = A2;
@@ -558,10 +594,10 @@ struct VPre {
     float acc;   // RK4 sum of V's stage slopes so far
 };
 
-template <int ST>
-__device__ __forceinline__ VPre neuron_v_pre(int i, int n, float V, const float *ysc, const float *y0,
-                                             const float *acc, const float *prm, float iext) {
-    constexpr bool FIRST = stage_first(ST);
+template <class SG>
+__device__ __forceinline__ VPre neuron_v_pre(const SG &sg, int i, int n, float V, const float *ysc,
+                                             const float *y0, const float *acc, const float *prm, float iext) {
+    const bool FIRST = sg.first;
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
     // explicit roundings (no contraction left to the compiler), so that every
     // kernel evaluates the same operations in whatever context it is inlined
@@ -579,13 +615,13 @@ __device__ __forceinline__ VPre neuron_v_pre(int i, int n, float V, const float 
     return r;
 }
 
-template <int ST>
-__device__ __forceinline__ float neuron_v_post(int i, const VPre &p, float isyn, float *y0, float *acc,
-                                              const StageCoef &sc) {
-    constexpr bool FIRST = stage_first(ST), LAST = stage_last(ST);
-    const float WGT = sc.w, cnext = sc.cn, dt6 = sc.fin;
+template <class SG>
+__device__ __forceinline__ float neuron_v_post(const SG &sg, int i, const VPre &p, float isyn, float *y0,
+                                              float *acc) {
+    const bool FIRST = sg.first, LAST = sg.last;
+    const float WGT = sg.c.w, cnext = sg.c.cn, dt6 = sg.c.fin;
     const float d = __fmul_rn(__fsub_rn(p.ie, isyn), p.invC);
-    const float ac = FIRST ? first_term<ST>(sc, d) : fmaf(WGT, d, p.acc);
+    const float ac = FIRST ? sg.first_term(d) : fmaf(WGT, d, p.acc);
     if (!LAST) {
         acc[i] = ac;
         return fmaf(cnext, d, p.y0);
@@ -595,19 +631,19 @@ __device__ __forceinline__ float neuron_v_post(int i, const VPre &p, float isyn,
     return yn;
 }
 
-template <int ST>
-__device__ __forceinline__ float neuron_v(int i, int n, float V, const float *ysc, float *y0, float *acc,
-                                          const float *prm, float iext, float isyn, const StageCoef &sc) {
-    return neuron_v_post<ST>(i, neuron_v_pre<ST>(i, n, V, ysc, y0, acc, prm, iext), isyn, y0, acc, sc);
+template <class SG>
+__device__ __forceinline__ float neuron_v(const SG &sg, int i, int n, float V, const float *ysc, float *y0,
+                                          float *acc, const float *prm, float iext, float isyn) {
+    return neuron_v_post(sg, i, neuron_v_pre(sg, i, n, V, ysc, y0, acc, prm, iext), isyn, y0, acc);
 }
 
 // Gates: writes the next stage's m, h, n, or after the last stage the new
 // step-start ones.
-template <int ST>
-__device__ __forceinline__ void neuron_gates(int i, int n, float V, const float *ysc, float *ysn, float *y0,
-                                             float *acc, const StageCoef &sc) {
-    constexpr bool FIRST = stage_first(ST), LAST = stage_last(ST);
-    const float WGT = sc.w, cnext = sc.cn, dt6 = sc.fin;
+template <class SG>
+__device__ __forceinline__ void neuron_gates(const SG &sg, int i, int n, float V, const float *ysc, float *ysn,
+                                             float *y0, float *acc) {
+    const bool FIRST = sg.first, LAST = sg.last;
+    const float WGT = sg.c.w, cnext = sg.c.cn, dt6 = sg.c.fin;
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
     const Rates q = hh_rates(V);
     float d[3];
@@ -617,7 +653,7 @@ __device__ __forceinline__ void neuron_gates(int i, int n, float V, const float 
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
         const int ix = (x + 1) * n + i;
-        const float ac = FIRST ? first_term<ST>(sc, d[x]) : fmaf(WGT, d[x], acc[ix]);
+        const float ac = FIRST ? sg.first_term(d[x]) : fmaf(WGT, d[x], acc[ix]);
         float yn;
         if (!LAST) {
             acc[ix] = ac;
