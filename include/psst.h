@@ -180,7 +180,11 @@ int psst_create_network(const psst_network_desc *d, const psst_allocator *a, pss
    Euler or its tableau) from the current state
    (Sec. "Circumventing memory constraints", item 2: successive calls
    continue where the previous one stopped; results are bitwise independent
-   of how the steps are split into calls).  Asynchronous on `stream`;
+   of how the steps are split into calls).  Each step-start state variable
+   is carried with the rounding remainder of its compensated step sums
+   (Knuth's TwoSum; the handle keeps the remainders between calls), so the
+   FP32 trajectory tracks the exact RK4 map far more closely than plain
+   FP32 accumulation.  Asynchronous on `stream`;
    device-side failures (NONFINITE, TIMEOUT) are reported by psst_status.
    With the environment variable PSST_SYNC set (to anything but "0") the
    call synchronises `stream` and returns what psst_status would.
@@ -220,12 +224,17 @@ int psst_autotune(psst_net *h, int64_t trial_steps, void *stream);
    clear it. */
 int psst_status(psst_net *h, void *stream);
 
-/* Copy the state [V, m, h, n, r, s] (4N+2S floats) to dst (host or device
-   memory as dst_on_device says), stream-ordered; synchronises the stream
-   when dst is on the host.  Errors: INVALID_ARG if n < 4N+2S. */
+/* Copy the state [V, m, h, n, r, s] (4N+2S floats, the FP32 values without
+   their remainders) to dst (host or device memory as dst_on_device says),
+   stream-ordered; synchronises the stream when dst is on the host.
+   Errors: INVALID_ARG if n < 4N+2S. */
 int psst_get_state(const psst_net *h, float *dst, size_t n, int dst_on_device, void *stream);
 
-/* Overwrite the state from src (4N+2S floats, host or device). */
+/* Overwrite the state from src (4N+2S floats, host or device).  The
+   remainders of the compensated sums restart at zero (an FP32 state given
+   by the caller is exact): a run continued from a state copied out with
+   psst_get_state agrees with the uninterrupted run to rounding, not bit for
+   bit. */
 int psst_set_state(psst_net *h, const float *src, size_t n, int src_on_device, void *stream);
 
 /* Set the global step index (time = step * dt) used for inputs and
@@ -247,12 +256,13 @@ int psst_set_weights(psst_net *h, const float *w, size_t n, int on_device, void 
 int psst_set_neuron_params(psst_net *h, const float *p, size_t n, int on_device, void *stream);
 
 /* Record checkpoints for the adjoint: while every > 0, each psst_integrate
-   call (of at most max_steps steps) stores the full state at its start and
-   after every `every` steps, so that psst_adjoint(..., ckpt_every = 0) can
-   differentiate that call's span without its own checkpointing pass.  The
-   recorded span is invalidated by set_state, set_step, set_weights and
-   set_neuron_params.  every = 0 stops recording.  CTA mode only.  The buffer
-   (ceil(max_steps / every) full states) is allocated here. */
+   call (of at most max_steps steps) stores the full state and its
+   remainders at its start and after every `every` steps, so that
+   psst_adjoint(..., ckpt_every = 0) can differentiate that call's span
+   without integrating it again.  The recorded span is invalidated by
+   set_state, set_step, set_weights and set_neuron_params.  every = 0 stops
+   recording.  CTA mode only.  The buffers (2 x ceil(max_steps / every) full
+   states) are allocated here, or reused when large enough. */
 int psst_record_checkpoints(psst_net *h, int32_t every, int64_t max_steps);
 
 /* Discrete adjoint of the integration map -- RK4, forward Euler (Eq. euler)
@@ -267,9 +277,14 @@ int psst_record_checkpoints(psst_net *h, int32_t every, int64_t max_steps);
      grad_w              [S]   dL/dw for every synapse, CSR order;
      grad_neuron_params  [n_neuron_types * 9]  dL/d(neuron-type table);
      grad_state0         [4][N] dL/d(V, m, h, n at the start), or NULL.
-   The state and step index are left unchanged.  Memory: reduced states are
-   checkpointed every ckpt_every steps and each segment is recomputed;
-   the handle allocates the storage on first use and grows it as needed.
+   The state and step index are left unchanged.  Memory: the forward
+   kernel integrates the span once, recording the full state and its
+   remainders every ckpt_every steps (the record ring is not written), and
+   each segment is recomputed from its checkpoint; the handle allocates the
+   storage on first use and grows it as needed.  The recomputation uses the
+   adjoint's own arithmetic, so its trajectory drifts slowly from the forward
+   kernel's: spacings of up to about 1000 steps keep FP32 gradients within
+   1e-3 of the exact map's on 20,000-step spiking spans.
    ckpt_every = 0 differentiates instead the span of the last psst_integrate
    call, whose checkpoints were recorded (psst_record_checkpoints); n_steps
    must equal that call's; PSST_ERR_STATE if no such checkpoints exist.
@@ -311,8 +326,10 @@ const char *psst_last_error(void);
  * RK4 steps starting at global step index step0, exactly like
  * psst_integrate in PSST_MODE_GRID with one gate per synapse (same kernel;
  * with gate_mode = 1 and the same item_chunks the results are bitwise
- * identical; the per-pair gate table of psst_integrate groups the synaptic
- * sums by type and agrees to rounding).  It runs on the current device and
+ * identical to a psst_integrate call made right after psst_set_state: the
+ * call keeps no remainders of its compensated step sums, so each call
+ * starts them at zero; the per-pair gate table of psst_integrate groups the
+ * synaptic sums by type and agrees to rounding).  It runs on the current device and
  * `stream`.  Its first call on a device looks up that device's address of
  * the fixed array (cudaGetSymbolAddress); make that first call before any
  * stream capture.  Each call synchronises `stream` once, after planning and

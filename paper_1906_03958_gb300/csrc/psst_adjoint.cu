@@ -24,9 +24,12 @@
 // Forward Euler (Eq. euler) is the one-stage case: kb1 = h lam,
 // lam_n = lam + J(y_n)^T kb1.  A tableau (stage s starts at
 // y + h a_s k_{s-1}, weights b_s) has kb_s = h b_s lam + h a_{s+1} Yb_{s+1}.
-// States are checkpointed every `ckpt` steps in a first forward pass; each
-// segment is recomputed forward, keeping every step's stages in global
-// memory, then swept backward from those stages.
+// The forward kernel records the full state and its compensated-sum
+// remainders every `ckpt` steps (psst_integrate with recording, run by
+// psst_adjoint itself when the caller recorded nothing); each segment is
+// recomputed forward from its checkpoint, keeping every step's stages in
+// global memory, then swept backward from those stages.  The recomputation
+// carries the remainders too (compensated state, psst_device.cuh).
 //
 // Jacobian-transpose product at a stage (q_i = kbV_i / C_i,
 // A_i = sum_k w_k G_p(k), G_p the pair's gate, I_syn = V A - B):
@@ -72,8 +75,8 @@ __device__ __forceinline__ float ratio_u_deriv(float u) {
         const float u2 = u * u;
         return fmaf(u, fmaf(u2, -1.0f / 180.0f, 1.0f / 6.0f), 0.5f);
     }
-    const float e = __expf(-u), den = 1.0f - e;
-    return __fdividef(den - u * e, den * den);
+    const float e = expf(-u), den = -expm1f(-u);
+    return __fdiv_rn(den - u * e, den * den);
 }
 
 struct AdjSmem {
@@ -89,6 +92,7 @@ struct AdjSmem {
     float *sA, *sfv;           // [4][N]
     // reduced state y (step start) and running RK4 sums
     float *y;                  // [4N + 2M]: V, m, h, n, r, s
+    float *ylo;                // [4N + 2M]: remainders of y (compensated step sums)
     float *acc;                // [4N + 2M]
     // adjoint
     float *lam, *yprev, *ysum; // [4N + 2M]
@@ -109,7 +113,7 @@ __host__ __device__ inline long long adj_smem_bytes(int N, int M, int n_items, i
     b += 8LL * n_items + 2LL * n_items + 16;  // pa, pb, irow
     b += 4LL * (N + 1);
     b += 4LL * 4 * (6LL * N + 3LL * M);  // stage storage
-    b += 4LL * 5 * (4LL * N + 2LL * M);  // y, acc, lam, yprev, ysum
+    b += 4LL * 6 * (4LL * N + 2LL * M);  // y, ylo, acc, lam, yprev, ysum
     b += 32LL * N + 4LL * M + 4LL * N;    // ab, csum, uV
     b += 8LL * 9 * N;                    // gp (double)
     b += 4LL * 9 * N + 4LL * 3 * N;      // prm, iext, inp
@@ -154,7 +158,7 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
             S.sr[p] = r[p];
             S.ss[p] = s[p];
             const float s2 = s[p] * s[p], s4 = s2 * s2;
-            S.sG[p] = sp[SP_KIND] != 0.0f ? __fdividef(s4, s4 + sp[SP_KD]) : r[p];
+            S.sG[p] = sp[SP_KIND] != 0.0f ? __fdiv_rn(s4, s4 + sp[SP_KD]) : r[p];
         }
     }
     __syncthreads();
@@ -215,9 +219,9 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
                 const float ac = (st == 0) ? W0 * d[x] : fmaf(WGT, d[x], S.acc[ix]);
                 if (st < NST - 1) {
                     S.acc[ix] = ac;
-                    stg[x][(st + 1) * N + i] = fmaf(cnext, d[x], S.y[ix]);
+                    stg[x][(st + 1) * N + i] = ext_stage(S.y[ix], S.ylo[ix], cnext, d[x]);
                 } else {
-                    S.y[ix] = fmaf(dt6, ac, S.y[ix]);
+                    ext_step(S.y[ix], S.ylo[ix], dt6, ac);
                 }
             }
             // own gate pairs
@@ -235,15 +239,15 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
                 if (st < NST - 1) {
                     S.acc[ir] = ar;
                     S.acc[is] = as;
-                    rn = fmaf(cnext, dr, S.y[ir]);
-                    sn = fmaf(cnext, ds, S.y[is]);
+                    rn = ext_stage(S.y[ir], S.ylo[ir], cnext, dr);
+                    sn = ext_stage(S.y[is], S.ylo[is], cnext, ds);
                     S.sr[(st + 1) * M + p] = rn;
                     S.ss[(st + 1) * M + p] = sn;
                     const float s2 = sn * sn, s4 = s2 * s2;
-                    S.sG[(st + 1) * M + p] = sp[SP_KIND] != 0.0f ? __fdividef(s4, s4 + sp[SP_KD]) : rn;
+                    S.sG[(st + 1) * M + p] = sp[SP_KIND] != 0.0f ? __fdiv_rn(s4, s4 + sp[SP_KD]) : rn;
                 } else {
-                    S.y[ir] = fmaf(dt6, ar, S.y[ir]);
-                    S.y[is] = fmaf(dt6, as, S.y[is]);
+                    ext_step(S.y[ir], S.ylo[ir], dt6, ar);
+                    ext_step(S.y[is], S.ylo[is], dt6, as);
                 }
             }
         }
@@ -367,7 +371,7 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
                 float ur = -(sp[SP_A] * T + sp[SP_B]) * kbr, us = 0.0f;
                 if (sp[SP_KIND] != 0.0f) {
                     const float s2 = ss * ss, s4 = s2 * s2, den = s4 + sp[SP_KD];
-                    const float dG = __fdividef(4.0f * s2 * ss * sp[SP_KD], den * den);
+                    const float dG = __fdiv_rn(4.0f * s2 * ss * sp[SP_KD], den * den);
                     ur = fmaf(sp[SP_K3], kbs, ur);
                     us = -C * dG - sp[SP_K4] * kbs;
                 } else {
@@ -430,17 +434,25 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
 }
 
 // Reduced state of the network from a full state [V, m, h, n, r, s] of the
-// whole batch: neurons as they are, each pair's gates from its synapses
-// (all equal by the precondition; *bad, if given, is set when they differ).
+// whole batch and its remainders full_lo (null: zero): neurons as they are,
+// each pair's gates from its synapses (all equal by the precondition; *bad,
+// if given, is set when they differ).
 __device__ void load_reduced(const NetView &v, const AdjNet &a, const AdjSmem &S, const float *full,
-                             const long long *rp, const uint32_t *gcode, int *bad) {
+                             const float *full_lo, const long long *rp, const uint32_t *gcode, int *bad) {
     const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, M = a.M;
     const float *gr = full + 4 * v.N + a.sbase, *gs = full + 4 * v.N + v.S + a.sbase;
+    const float *grl = full_lo ? full_lo + 4 * v.N + a.sbase : nullptr;
+    const float *gsl = full_lo ? full_lo + 4 * v.N + v.S + a.sbase : nullptr;
     for (int i = tid; i < N; i += nthr)
-        for (int x = 0; x < 4; ++x) S.y[x * N + i] = full[(long long)x * v.N + a.n0 + i];
+        for (int x = 0; x < 4; ++x) {
+            S.y[x * N + i] = full[(long long)x * v.N + a.n0 + i];
+            S.ylo[x * N + i] = full_lo ? full_lo[(long long)x * v.N + a.n0 + i] : 0.0f;
+        }
     for (int q = tid; q < M; q += nthr) {
         S.y[4 * N + q] = 0.0f;
         S.y[4 * N + M + q] = 0.0f;
+        S.ylo[4 * N + q] = 0.0f;
+        S.ylo[4 * N + M + q] = 0.0f;
     }
     __syncthreads();
     for (int i = tid; i < N; i += nthr)
@@ -448,6 +460,10 @@ __device__ void load_reduced(const NetView &v, const AdjNet &a, const AdjSmem &S
             const int ci = (int)(gcode[k] & 0xFFFFFFu);
             S.y[4 * N + ci] = gr[k];
             S.y[4 * N + M + ci] = gs[k];
+            if (grl) {
+                S.ylo[4 * N + ci] = grl[k];
+                S.ylo[4 * N + M + ci] = gsl[k];
+            }
         }
     __syncthreads();
     if (bad) {
@@ -533,6 +549,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     S.sA = (float *)take(p, 16LL * N);
     S.sfv = (float *)take(p, 16LL * N);
     S.y = (float *)take(p, 4LL * a.R);
+    S.ylo = (float *)take(p, 4LL * a.R);
     S.acc = (float *)take(p, 4LL * a.R);
     S.lam = (float *)take(p, 4LL * a.R);
     S.yprev = (float *)take(p, 4LL * a.R);
@@ -606,9 +623,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         }
     }
     __syncthreads();
-    // starting state (reduced), checked for equal gates within each pair
-    const float *full0 = av.ck_full ? av.ck_full : v.state;
-    load_reduced(v, a, S, full0, rp, gcode, &s_bad);
+    // starting state (reduced; the span's first checkpoint), checked for
+    // equal gates within each pair
+    load_reduced(v, a, S, av.ck_full, av.ck_full_lo, rp, gcode, &s_bad);
     if (s_bad) {
         if (tid == 0) set_error(v.err, PSST_ERR_UNSUPPORTED);
         return;
@@ -632,7 +649,6 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     // the two CTAs of the network's cluster: rank 0 recomputes segments
     // forward, rank 1 sweeps them backward and owns the gradients
     const bool fwd_cta = cluster_rank() == 0;
-    float *ck = av.ckpt + av.ck_off[a.b];
     float *seg0 = av.seg + av.seg_off[a.b];
     const long long seg_buf = (long long)min(ckpt, nsteps) * step_floats;  // floats of one segment buffer
     float4 *gpart = av.gpart + av.slot_off[a.b] / 4;
@@ -640,14 +656,6 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     if (!fwd_cta) {
         for (long long c = tid; c < slots; c += nthr) gpart[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         for (long long c = tid; c < slots * 4; c += nthr) gtot[c] = 0.0;
-    }
-    // pass 1 (rank 0): checkpoints every ckpt steps, unless recorded by the forward
-    if (fwd_cta && !av.ck_full) {
-        for (int n = 0; n < nsteps; ++n) {
-            if (n % ckpt == 0)
-                for (int q = tid; q < a.R; q += nthr) ck[(long long)(n / ckpt) * a.R + q] = S.y[q];
-            fwd_step<false, NST, TAB>(v, a, S, stab, step0 + n, dt);
-        }
     }
     // frames: global steps k in (step0, step0 + nsteps] with k % stride == 0
     const int stride = v.rec_stride;
@@ -662,12 +670,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     // every step's four stages kept
     auto recompute = [&](int c) {
         const int k0 = c * ckpt, k1 = min(k0 + ckpt, nsteps);
-        if (av.ck_full) {
-            load_reduced(v, a, S, av.ck_full + (long long)c * av.dim, rp, gcode, nullptr);
-        } else {
-            for (int q = tid; q < a.R; q += nthr) S.y[q] = ck[(long long)c * a.R + q];
-            __syncthreads();
-        }
+        load_reduced(v, a, S, av.ck_full + (long long)c * av.dim,
+                     av.ck_full_lo ? av.ck_full_lo + (long long)c * av.dim : nullptr, rp, gcode, nullptr);
         float *seg = seg0 + (long long)(c & 1) * seg_buf;
         for (int n = k0; n < k1; ++n) {
             fwd_step<true, NST, TAB>(v, a, S, stab, step0 + n, dt);

@@ -92,19 +92,22 @@ struct psst_net {
     std::vector<int> adj_K, adj_items;
     int adj_smem = 0;
     int *d_adjK = nullptr, *d_adjI = nullptr;
-    long long *d_ckoff = nullptr, *d_segoff = nullptr, *d_slotoff = nullptr;
+    long long *d_segoff = nullptr, *d_slotoff = nullptr;
     uint8_t *d_colwarp = nullptr;  // [n_nets] adjoint column sums through per-warp rows
-    float *adj_ckpt = nullptr, *adj_seg = nullptr, *adj_gy0 = nullptr;
+    float *adj_seg = nullptr, *adj_gy0 = nullptr;
     float4 *adj_gpart = nullptr;
     double *adj_gtot = nullptr;
     double *adj_gpn = nullptr;
-    long long adj_ck_cap = 0, adj_seg_cap = 0;
+    long long adj_seg_cap = 0;
     int adj_ckpt_every = 0;
     // checkpoints recorded by psst_integrate for a later psst_adjoint
     int rec_ck_every = 0;
+    int rec_ck_spacing = 0;  // checkpoint spacing of the valid recording
+    long long rec_ck_cap = 0;  // floats of each checkpoint buffer
     long long rec_ck_cap_steps = 0, rec_ck_start = 0, rec_ck_nsteps = 0;
     bool rec_ck_valid = false;
     float *rec_ck = nullptr;
+    float *rec_ck_lo = nullptr;  // the recorded states' remainders
     // CUDA-graph replay of one integrate chunk
     bool graph_mode = false;
     cudaGraph_t graph = nullptr;
@@ -525,6 +528,8 @@ int grid_pair_tables(psst_net *h, const psst_network_desc *d, cudaError_t *err) 
     if (e == cudaSuccess) e = cudaMemset(g.gt, 0, (size_t)2 * std::max(g.mt, 1) * sizeof(float));
     if (e == cudaSuccess) e = h->alloc(&g.r0g, (size_t)used);
     if (e == cudaSuccess) e = h->alloc(&g.s0g, (size_t)used);
+    if (e == cudaSuccess) e = h->alloc(&g.r0lg, (size_t)used);
+    if (e == cudaSuccess) e = h->alloc(&g.s0lg, (size_t)used);
     g.tix = h->v.pair_tix;
     g.rep = r;
     if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid pair tables");
@@ -884,6 +889,8 @@ int psst_create_network(const psst_network_desc *d, const psst_allocator *a, pss
 #undef UP
     const long long dim = 4 * N + 2 * S;
     if (e == cudaSuccess) e = h->alloc(&v.state, (size_t)dim);
+    if (e == cudaSuccess) e = h->alloc(&v.state_lo, (size_t)dim);
+    if (e == cudaSuccess) e = cudaMemset(v.state_lo, 0, (size_t)dim * sizeof(float));
     if (e == cudaSuccess && v.rec_cap > 0) e = h->alloc(&v.rec, (size_t)(v.rec_cap * N));
     if (e == cudaSuccess) e = h->alloc(&v.err, 1);
     if (e == cudaSuccess) e = cudaMemset(v.err, 0, sizeof(int));
@@ -1101,8 +1108,11 @@ int psst_autotune(psst_net *h, int64_t trial_steps, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     const size_t dim = (size_t)(4 * h->v.N + 2 * h->v.S);
     cudaError_t e = cudaSuccess;
-    if (!h->tune_buf) e = h->alloc(&h->tune_buf, dim);
+    // the state and its remainders, restored after the trials
+    if (!h->tune_buf) e = h->alloc(&h->tune_buf, 2 * dim);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->tune_buf, h->v.state, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->tune_buf + dim, h->v.state_lo, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&ev1);
@@ -1181,6 +1191,8 @@ int psst_autotune(psst_net *h, int64_t trial_steps, void *stream) {
     }
     h->v.rec_stride = stride;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->v.state, h->tune_buf, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->v.state_lo, h->tune_buf + dim, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -1227,6 +1239,9 @@ static int integrate_async(psst_net *h, int64_t n_steps, cudaStream_t stream) {
     for (long long done = 0, c = 0; done < n_steps; ++c) {
         cudaError_t e = cudaMemcpyAsync(h->rec_ck + c * dim, h->v.state, dim * sizeof(float),
                                         cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->rec_ck_lo + c * dim, h->v.state_lo, dim * sizeof(float), cudaMemcpyDeviceToDevice,
+                                st);
         if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
         const long long n = std::min<long long>(h->rec_ck_every, n_steps - done);
         const int rc = launch_steps(h, s0 + done, n, st);
@@ -1236,6 +1251,7 @@ static int integrate_async(psst_net *h, int64_t n_steps, cudaStream_t stream) {
     h->step += n_steps;
     h->rec_ck_start = s0;
     h->rec_ck_nsteps = n_steps;
+    h->rec_ck_spacing = h->rec_ck_every;
     h->rec_ck_valid = true;
     return PSST_OK;
 }
@@ -1247,16 +1263,25 @@ int psst_record_checkpoints(psst_net *h, int32_t every, int64_t max_steps) {
     h->rec_ck_valid = false;
     h->rec_ck_every = every;
     if (every == 0) return PSST_OK;
-    const long long need = ((max_steps + every - 1) / every) * (4 * h->v.N + 2 * h->v.S);
-    if (max_steps > h->rec_ck_cap_steps || !h->rec_ck) {
+    // the buffers hold whole checkpoints: a call of max_steps steps records
+    // ceil(max_steps / every) of them
+    const long long dim = 4 * h->v.N + 2 * h->v.S;
+    const long long need = ((max_steps + every - 1) / every) * dim;
+    if (need > h->rec_ck_cap || !h->rec_ck) {
         DeviceGuard guard(h->device);
         cudaError_t e = h->alloc(&h->rec_ck, (size_t)need);
+        if (e == cudaSuccess) e = h->alloc(&h->rec_ck_lo, (size_t)need);
         if (e != cudaSuccess) {
+            h->rec_ck = h->rec_ck_lo = nullptr;
+            h->rec_ck_cap = 0;
+            h->rec_ck_cap_steps = 0;
             h->rec_ck_every = 0;
             return cuda_fail(e, "checkpoint buffer");
         }
+        h->rec_ck_cap = need;
     }
-    h->rec_ck_cap_steps = std::max<long long>(h->rec_ck_cap_steps, max_steps);
+    // the steps one integrate call may record at this spacing
+    h->rec_ck_cap_steps = (h->rec_ck_cap / dim) * every;
     return PSST_OK;
 }
 
@@ -1301,6 +1326,8 @@ int psst_set_state(psst_net *h, const float *src, size_t n, int src_on_device, v
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(h->v.state, src, dim * sizeof(float),
                                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    // an FP32 state given by the caller is exact: its remainders are zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->v.state_lo, 0, dim * sizeof(float), st);
     if (e == cudaSuccess && !src_on_device) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "psst_set_state");
     return recheck_pairs(h, st);
@@ -1378,14 +1405,13 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
     if (!h || !grad_w || !grad_neuron_params) return fail(PSST_ERR_INVALID_ARG, "NULL argument");
     if (h->mode != PSST_MODE_CTA) return fail(PSST_ERR_UNSUPPORTED, "the adjoint runs in CTA mode only");
     if (n_steps < 1 || n_steps > (1LL << 30)) return fail(PSST_ERR_INVALID_ARG, "n_steps must be in 1..2^30");
-    const bool recorded = ckpt_every == 0;
-    if (recorded) {
+    if (ckpt_every == 0) {
         if (!h->rec_ck_valid || h->rec_ck_nsteps != n_steps)
             return fail(PSST_ERR_STATE, "no checkpoints of a %lld-step integrate call are recorded", (long long)n_steps);
-        ckpt_every = h->rec_ck_every;
+    } else if (ckpt_every < 1) {
+        return fail(PSST_ERR_INVALID_ARG, "ckpt_every must be >= 1 (0 = recorded)");
     }
-    if (ckpt_every < 1) return fail(PSST_ERR_INVALID_ARG, "ckpt_every must be >= 1 (0 = recorded)");
-    const long long stride = h->v.rec_stride, s0 = recorded ? h->rec_ck_start : h->step;
+    const long long stride = h->v.rec_stride, s0 = ckpt_every == 0 ? h->rec_ck_start : h->step;
     long long want = 0;
     if (stride > 0) want = (s0 + n_steps) / stride - s0 / stride;
     if (n_frames != want)
@@ -1394,6 +1420,35 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
     DeviceGuard guard(h->device);
     const int n_nets = h->v.n_nets, nt = h->v.n_stypes;
     cudaError_t e = cudaSuccess;
+    if (ckpt_every > 0) {
+        // The span's checkpoints: the forward kernel integrates it once from
+        // the current state, recording the state and its remainders every
+        // ckpt_every steps, so that each segment the adjoint recomputes
+        // starts on the forward kernel's trajectory; the network's state,
+        // step, record ring and recording setting are then put back.
+        const size_t dim = (size_t)(4 * h->v.N + 2 * h->v.S);
+        cudaStream_t st = (cudaStream_t)stream;
+        if (!h->tune_buf) e = h->alloc(&h->tune_buf, 2 * dim);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->tune_buf, h->v.state, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->tune_buf + dim, h->v.state_lo, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint state copy");
+        const int keep_every = h->rec_ck_every, keep_stride = h->v.rec_stride;
+        const long long keep_step = h->step;
+        h->v.rec_stride = 0;
+        int rc = psst_record_checkpoints(h, ckpt_every, n_steps);
+        if (rc == PSST_OK) rc = integrate_async(h, n_steps, st);
+        h->v.rec_stride = keep_stride;
+        h->rec_ck_every = keep_every;
+        h->rec_ck_cap_steps = keep_every > 0 ? (h->rec_ck_cap / (long long)dim) * keep_every : 0;
+        h->step = keep_step;
+        e = cudaMemcpyAsync(h->v.state, h->tune_buf, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->v.state_lo, h->tune_buf + dim, dim * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        if (rc != PSST_OK) return rc;
+        if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint state copy");
+    }
+    ckpt_every = h->rec_ck_spacing;
     // per-network plan (host copy of the CSR offsets is not kept: read them back once)
     if (h->adj_K.empty()) {
         std::vector<int> off((size_t)n_nets + 1);
@@ -1445,7 +1500,6 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         if (e == cudaSuccess) e = h->alloc(&h->adj_gtot, (size_t)slots);
         if (e == cudaSuccess) e = h->alloc(&h->adj_gpn, (size_t)h->v.N * 9);
         if (e == cudaSuccess) e = h->alloc(&h->adj_gy0, (size_t)h->v.N * 4);
-        if (e == cudaSuccess) e = h->alloc(&h->d_ckoff, (size_t)n_nets);
         if (e == cudaSuccess) e = h->alloc(&h->d_segoff, (size_t)n_nets);
         if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint buffers");
     }
@@ -1454,26 +1508,18 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         std::vector<int> off((size_t)n_nets + 1);
         e = cudaMemcpy(off.data(), h->v.net_off, off.size() * sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint offsets");
-        const long long nck = (n_steps + ckpt_every - 1) / ckpt_every;
-        std::vector<long long> ck((size_t)n_nets), sg((size_t)n_nets);
-        long long ck_total = 0, seg_total = 0;
+        std::vector<long long> sg((size_t)n_nets);
+        long long seg_total = 0;
         for (int b = 0; b < n_nets; ++b) {
-            const long long N = off[b + 1] - off[b], R = 4 * N + 2 * N * nt;
+            const long long N = off[b + 1] - off[b];
             const long long step_floats = psst::adj_segment_floats(h->v.method, h->v.rk_ns, (int)N, nt);  // one step's stages
-            ck[b] = ck_total;
             sg[b] = seg_total;
-            ck_total += nck * R;
             seg_total += 2LL * std::min<long long>(ckpt_every, n_steps) * step_floats;  // two buffers
         }
-        if (ck_total > h->adj_ck_cap) {
-            e = h->alloc(&h->adj_ckpt, (size_t)ck_total);
-            h->adj_ck_cap = ck_total;
-        }
-        if (e == cudaSuccess && seg_total > h->adj_seg_cap) {
+        if (seg_total > h->adj_seg_cap) {
             e = h->alloc(&h->adj_seg, (size_t)seg_total);
             h->adj_seg_cap = seg_total;
         }
-        if (e == cudaSuccess) e = cudaMemcpy(h->d_ckoff, ck.data(), ck.size() * sizeof(long long), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(h->d_segoff, sg.data(), sg.size() * sizeof(long long), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint storage");
     }
@@ -1481,10 +1527,9 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
     av.K = h->d_adjK;
     av.n_items = h->d_adjI;
     av.ckpt_every = ckpt_every;
-    av.ck_full = recorded ? h->rec_ck : nullptr;
+    av.ck_full = h->rec_ck;
+    av.ck_full_lo = h->rec_ck_lo;
     av.dim = 4 * h->v.N + 2 * h->v.S;
-    av.ckpt = h->adj_ckpt;
-    av.ck_off = h->d_ckoff;
     av.seg = h->adj_seg;
     av.seg_off = h->d_segoff;
     av.gpart = h->adj_gpart;

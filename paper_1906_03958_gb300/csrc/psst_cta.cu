@@ -80,7 +80,8 @@ struct SmemCoef {
 template <int CL, bool HAS2, bool PAIR>
 __device__ __forceinline__ void stage(const NetView &v, const StageRT &sg, const Items &it, int n0, int N, int nt,
                                       int M, int r_lo, int nown, unsigned rank, long long rec_slot, float *vst,
-                                      float *y0, float *acc, float *ys, const float *prm, const float *iext,
+                                      float *y0, float *ylo, float *acc, float *ys, const float *prm,
+                                      const float *iext,
                                       float2 *cur1, float2 *acc1, float2 *fin1, float4 *cur2, float4 *acc2,
                                       float4 *fin2, float *pst, float *Gt, int lrep, const float *stab, int par) {
     const bool FIRST = sg.first, LAST = sg.last;
@@ -90,13 +91,14 @@ __device__ __forceinline__ void stage(const NetView &v, const StageRT &sg, const
     const float *ysc = ys + par * 3 * nown;
     float *ysn = ys + (par ^ 1) * 3 * nown;
     // gate-map entries: every (neuron, type) pair, or the used pairs (PAIR)
-    float *r0p = pst, *s0p = pst + M;
-    const unsigned short *pof = (const unsigned short *)(pst + 2 * M);
+    float *r0p = pst, *s0p = pst + M, *r0lo = pst + 2 * M, *s0lo = pst + 3 * M;
+    const unsigned short *pof = (const unsigned short *)(pst + 4 * M);
     // The gates m, h, n of the owned neurons need only this stage's
     // potentials: they are computed before the S-phase (on the highest
     // threads), where their latency overlaps the S-phase's loads, and leave
     // the N-phase fewer units.
-    for (int i = nthr - 1 - tid; i < nown; i += nthr) neuron_gates(sg, i, nown, vcur[r_lo + i], ysc, ysn, y0, acc);
+    for (int i = nthr - 1 - tid; i < nown; i += nthr)
+        neuron_gates(sg, i, nown, vcur[r_lo + i], ysc, ysn, y0, ylo, acc);
     if (PAIR) sphase_pair(it, Gt, lrep);
     else sphase<HAS2>(FIRST, it, SmemCoef{FIRST ? fin1 : cur1, FIRST ? fin2 : cur2});
     __syncthreads();
@@ -109,9 +111,9 @@ __device__ __forceinline__ void stage(const NetView &v, const StageRT &sg, const
             if (u >= nown) continue;
             const int i = u;
             const float V = vcur[r_lo + i];
-            const VPre pre = neuron_v_pre(sg, i, nown, V, ysc, y0, acc, prm, iext[i]);
+            const VPre pre = neuron_v_pre(sg, i, nown, V, ysc, y0, ylo, acc, prm, iext[i]);
             const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
-            const float vn = neuron_v_post(sg, i, pre, isyn, y0, acc);
+            const float vn = neuron_v_post(sg, i, pre, isyn, y0, ylo, acc);
             vnxt[r_lo + i] = vn;
             if (CL > 1) {
 #pragma unroll
@@ -131,12 +133,17 @@ __device__ __forceinline__ void stage(const NetView &v, const StageRT &sg, const
                 // the pair's gate for the next stage (same operations as the per-synapse path)
                 const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
                 if (!LAST) {
-                    put_gate(Gt, p, lrep, pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]));
+                    put_gate(Gt, p, lrep, pair_gate(sec, cur1[p], c2, r0p[p], s0p[p], r0lo[p], s0lo[p]));
                 } else {
-                    const float r0 = r0p[p], s0 = s0p[p];
-                    put_gate(Gt, p, lrep, pair_gate(sec, fin1[p], f2, r0, s0));
-                    r0p[p] = fmaf(fin1[p].y, r0, fin1[p].x);
-                    if (sec) s0p[p] = fmaf(f2.z, s0, fmaf(f2.y, r0, f2.x));
+                    // the step's end gates: the next step's first-stage gates and step-start state
+                    float r0 = r0p[p], s0 = s0p[p], rl = r0lo[p], sl = s0lo[p];
+                    pair_step(sec, fin1[p], f2, r0, s0, rl, sl);
+                    put_gate(Gt, p, lrep, pair_gate(sec, make_float2(0.0f, 0.0f), make_float4(0.0f, 0.0f, 0.0f, f2.w),
+                                                    r0, s0, rl, sl));
+                    r0p[p] = r0;
+                    s0p[p] = s0;
+                    r0lo[p] = rl;
+                    s0lo[p] = sl;
                 }
             }
         }
@@ -159,7 +166,8 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     const int r_lo = pl.split[rank], nown = pl.split[rank + 1] - r_lo;
     const int lrep = PAIR ? min(pl.lrep, lrep_cap) : 0;  // copies of the gate table (at most the plan's)
     const NeuronLayout L = make_nlayout(nown, N, M, HAS2, PAIR, 1 << lrep);
-    float *y0 = (float *)(smem + L.y0), *ys = (float *)(smem + L.ys), *acc = (float *)(smem + L.acc);
+    float *y0 = (float *)(smem + L.y0), *ylo = (float *)(smem + L.ylo), *ys = (float *)(smem + L.ys);
+    float *acc = (float *)(smem + L.acc);
     float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext), *inp = (float *)(smem + L.inp);
     float *vst = (float *)(smem + L.vst);
     float2 *cur1 = (float2 *)(smem + L.cur1), *acc1 = (float2 *)(smem + L.acc1), *fin1 = (float2 *)(smem + L.fin1);
@@ -175,6 +183,10 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
     float *gV = v.state + n0;
     float *gr = v.state + 4 * v.N + sbase;
     float *gs = v.state + 4 * v.N + v.S + sbase;
+    // the state's remainders (compensated sums), if the handle keeps them
+    float *gVl = v.state_lo ? v.state_lo + n0 : nullptr;
+    float *grl = v.state_lo ? v.state_lo + 4 * v.N + sbase : nullptr;
+    float *gsl = v.state_lo ? v.state_lo + 4 * v.N + v.S + sbase : nullptr;
     const float *gw = v.weight + sbase;
     const uint32_t *gcode = v.syn_code + sbase;
 
@@ -185,6 +197,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         for (int x = 0; x < 4; ++x) {
             const float y = gV[(long long)x * v.N + gi];
             y0[x * nown + i] = y;
+            ylo[x * nown + i] = gVl ? gVl[(long long)x * v.N + gi] : 0.0f;
             if (x > 0) ys[(x - 1) * nown + i] = y;  // stage-0 gates, parity 0
         }
         const float *p = v.nparams + (long long)v.neuron_type[n0 + gi] * PSST_NEURON_NPARAM;
@@ -195,32 +208,38 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         inp[nown + i] = v.pulse_amp ? v.pulse_amp[n0 + gi] : 0.0f;
     }
     const long long pon = v.pulse_on[b], poff = v.pulse_off[b];
-    unsigned short *pof = PAIR ? (unsigned short *)(pst + 2 * M) : nullptr;
+    unsigned short *pof = PAIR ? (unsigned short *)(pst + 4 * M) : nullptr;
     if (PAIR)
         for (int k = tid; k < M; k += nthr) pof[k] = (unsigned short)v.pair_of[v.pair_off[b] + k];
     for (int k = tid; k < M; k += nthr) {
-        fin1[k] = make_float2(0.0f, 1.0f);
+        fin1[k] = make_float2(0.0f, 0.0f);  // identity maps (increment form)
         if (HAS2) {
             const int ci = PAIR ? v.pair_of[v.pair_off[b] + k] : k;
             const float *sp = stab + (ci % nt) * 9;
-            fin2[k] = make_float4(0.0f, 0.0f, 1.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
+            fin2[k] = make_float4(0.0f, 0.0f, 0.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
         }
     }
     if (PAIR) {
         // pair state from the network's synapses (all gates of a pair are equal)
-        for (int p = tid; p < 2 * M; p += nthr) pst[p] = 0.0f;
+        for (int p = tid; p < 4 * M; p += nthr) pst[p] = 0.0f;
         __syncthreads();
         const int S = (int)(v.row_ptr[n0 + N] - sbase);
         for (int k = tid; k < S; k += nthr) {
             const int t = ptix[gcode[k] & 0xFFFFFFu];
+            const bool sec = HAS2 && second_order(stab, gcode[k]);
             pst[t] = gr[k];
-            if (HAS2 && second_order(stab, gcode[k])) pst[M + t] = gs[k];
+            if (sec) pst[M + t] = gs[k];
+            if (grl) {
+                pst[2 * M + t] = grl[k];
+                if (sec) pst[3 * M + t] = gsl[k];
+            }
         }
         __syncthreads();
         for (int p = tid; p < M; p += nthr) {
             const bool sec = HAS2 && stab[(pof[p] % nt) * 9 + SP_KIND] != 0.0f;
             put_gate(Gt, p, lrep,
-                     pair_gate(sec, fin1[p], HAS2 ? fin2[p] : make_float4(0.f, 0.f, 1.f, 1.f), pst[p], pst[M + p]));
+                     pair_gate(sec, fin1[p], HAS2 ? fin2[p] : make_float4(0.f, 0.f, 0.f, 1.f), pst[p], pst[M + p],
+                               pst[2 * M + p], pst[3 * M + p]));
         }
         load_items_pair(it, v, n0, sbase, r_lo, gw, gcode, stab, tmp, ptix);  // ends with __syncthreads
     } else {
@@ -246,8 +265,8 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         // stage s of step itn reads parity (itn * ns + s) & 1
 #pragma unroll 1
         for (int s = 0; s < ns; ++s)
-            stage<CL, HAS2, PAIR>(v, stage_rt(v, s, dt), it, n0, N, nt, M, r_lo, nown, rank, rec_slot, vst, y0, acc,
-                                  ys, prm, iext, cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab,
+            stage<CL, HAS2, PAIR>(v, stage_rt(v, s, dt), it, n0, N, nt, M, r_lo, nown, rank, rec_slot, vst, y0, ylo,
+                                  acc, ys, prm, iext, cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab,
                                   (itn * ns + s) & 1);
     }
 
@@ -256,8 +275,13 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         const long long k0 = v.row_ptr[n0 + r_lo] - sbase, k1 = v.row_ptr[n0 + r_lo + nown] - sbase;
         for (long long k = k0 + tid; k < k1; k += nthr) {
             const int t = ptix[gcode[k] & 0xFFFFFFu];
+            const bool sec = HAS2 && second_order(stab, gcode[k]);
             gr[k] = pst[t];
-            if (HAS2 && second_order(stab, gcode[k])) gs[k] = pst[M + t];
+            if (sec) gs[k] = pst[M + t];
+            if (grl) {
+                grl[k] = pst[2 * M + t];
+                if (sec) gsl[k] = pst[3 * M + t];
+            }
         }
     } else {
         store_items<HAS2>(it, v, n0, sbase, r_lo, gr, gs, gcode, stab, SmemCoef{fin1, fin2});
@@ -269,6 +293,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
             const float y = y0[x * nown + i];
             bad |= !isfinite(y);
             gV[(long long)x * v.N + r_lo + i] = y;
+            if (gVl) gVl[(long long)x * v.N + r_lo + i] = ylo[x * nown + i];
         }
     }
     if (bad) set_error(v.err, PSST_ERR_NONFINITE);

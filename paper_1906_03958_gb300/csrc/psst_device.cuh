@@ -38,6 +38,8 @@ struct NetView {
     float noise_amp;
     float dt;
     float *state;                // [4N + 2S]: V, m, h, n, r, s
+    float *state_lo;             // [4N + 2S] remainders of the compensated step sums (same layout), or
+                                 // null: a launch starts them at zero and does not keep them
     float *rec;                  // [rec_cap][N] ring of V frames, or null
     int rec_stride;
     long long rec_cap;
@@ -74,6 +76,7 @@ struct GridView {
     const long long *rep;        // [used pairs] one synapse of each pair (holds the pair's gates)
     float *gt;                   // [2][mt] each pair's gate for the next stage, double-buffered by stage parity
     float *r0g, *s0g;            // [used pairs] step-start gates handed to the synapses' owners at the end
+    float *r0lg, *s0lg;          // [used pairs] their remainders (null with a null state_lo)
 };
 
 // Column indices of the parameter tables.
@@ -86,10 +89,9 @@ struct AdjView {
     const int *K;               // [n_nets] chunks per work item
     const int *n_items;         // [n_nets]
     int ckpt_every;
-    const float *ck_full;       // full states [4N+2S] every ckpt_every steps recorded by psst_integrate, or null
+    const float *ck_full;       // full states [4N+2S] every ckpt_every steps, recorded by the forward kernel
+    const float *ck_full_lo;    // their remainders (same layout)
     long long dim;              // 4N + 2S
-    float *ckpt;                // reduced states every ckpt_every steps (when ck_full is null)
-    const long long *ck_off;    // [n_nets] float offset of each network's checkpoints
     float *seg;                 // step states of the segment being swept
     const long long *seg_off;   // [n_nets]
     float4 *gpart;              // per-segment FP32 partial weight gradients, item-slot order (4 per chunk)
@@ -124,12 +126,14 @@ struct NeuronLayout {
     int cur2, acc2, fin2;  // float4 [m]: s-maps (second order only)
     int cur1, acc1, fin1;  // float2 [m]: r-maps
     int y0, ys, acc;       // float [4][n_own] step-start state, [2][3][n_own] stage m/h/n, [4][n_own] RK4 k-sum
+    int ylo;               // float [4][n_own] remainders of the step-start state (compensated sums)
     int prm;               // float [9][n_own]: 1/C, gNa, gK, gL, ENa, EK, EL, gKL, EKL
     int iext;              // float [n_own]
     int inp;               // float [2][n_own]: constant current, pulse amplitude
     int vst;               // float [2][n_all]: stage potential, by stage parity
     int tmp;               // int [2][n_own + 1]: scan scratch
-    int pair;              // per-pair variant: float [2][m] step-start r, s, ushort [m] local pair
+    int pair;              // per-pair variant: float [4][m] step-start r, s and their remainders,
+                           // ushort [m] local pair
     int gt;                // per-pair variant: float [m][rep] stage gate of each entry, rep copies
     int syn;               // start of the synapse items
 };
@@ -154,13 +158,14 @@ __host__ __device__ inline NeuronLayout make_nlayout(int n_own, int n_all, int m
     // (peers write into them through distributed shared memory)
     L.vst = lay_take(o, 8LL * n_all);
     L.y0 = lay_take(o, 16LL * n_own);
+    L.ylo = lay_take(o, 16LL * n_own);
     L.ys = lay_take(o, 24LL * n_own);  // stage m, h, n: [2][3][n] by stage parity
     L.acc = lay_take(o, 16LL * n_own);
     L.prm = lay_take(o, 36LL * n_own);
     L.iext = lay_take(o, 4LL * n_own);
     L.inp = lay_take(o, 8LL * n_own);
     L.tmp = lay_take(o, 8LL * (n_own + 1));
-    L.pair = pair ? lay_take(o, 10LL * m) : -1;  // r0, s0 (float) and the local pair (ushort) per entry
+    L.pair = pair ? lay_take(o, 18LL * m) : -1;  // r0, s0, their remainders (float), the local pair (ushort)
     L.gt = pair ? lay_take(o, 4LL * rep * m) : -1;
     L.syn = o;
     return L;
@@ -176,7 +181,7 @@ __device__ __forceinline__ float ratio_u(float u) {
         const float u2 = u * u;
         return fmaf(u2, fmaf(u2, -1.0f / 720.0f, 1.0f / 12.0f), fmaf(0.5f, u, 1.0f));
     }
-    return __fdividef(u, 1.0f - __expf(-u));
+    return __fdiv_rn(u, -expm1f(-u));
 }
 
 struct Rates {
@@ -187,17 +192,17 @@ struct Rates {
 __device__ __forceinline__ Rates hh_rates(float V) {
     Rates r;
     r.am = ratio_u((V + 40.0f) * 0.1f);
-    r.bm = 4.0f * __expf((V + 65.0f) * (-1.0f / 18.0f));
-    r.ah = 0.07f * __expf((V + 65.0f) * (-1.0f / 20.0f));
-    r.bh = __frcp_rn(1.0f + __expf((V + 35.0f) * (-0.1f)));
+    r.bm = 4.0f * expf((V + 65.0f) * (-1.0f / 18.0f));
+    r.ah = 0.07f * expf((V + 65.0f) * (-1.0f / 20.0f));
+    r.bh = __frcp_rn(1.0f + expf((V + 35.0f) * (-0.1f)));
     r.an = 0.1f * ratio_u((V + 55.0f) * 0.1f);
-    r.bn = 0.125f * __expf((V + 65.0f) * (-1.0f / 80.0f));
+    r.bn = 0.125f * expf((V + 65.0f) * (-1.0f / 80.0f));
     return r;
 }
 
 // Transmitter release T(V_pre) = 1 / (1 + exp(-(V - Vp) / Kp)).
 __device__ __forceinline__ float transmitter(float V, float Vp, float inv_Kp) {
-    return __frcp_rn(1.0f + __expf((Vp - V) * inv_Kp));
+    return __frcp_rn(1.0f + expf((Vp - V) * inv_Kp));
 }
 
 // Philox4x32-10 (Salmon et al., SC'11), word 0 of the output block.
@@ -234,6 +239,45 @@ __device__ __forceinline__ float input_current(const NetView &v, float i_const, 
         if ((x >> 8) < v.noise_thresh) I += v.noise_amp;
     }
     return I;
+}
+
+// Compensated state.  Within a launch, each step-start state variable is
+// held as a pair (hi, lo): hi the FP32 value, lo the rounding remainder the
+// step updates have accumulated, so that hi + lo carries about twice
+// FP32's precision.  Rounding the small RK4 increment into an FP32 state
+// every step otherwise dominates the drift of the FP32 trajectory from the
+// exact map (it shifts spike times by microseconds over 10^4 steps).  A
+// stage value is hi + (c d + lo); the step's update adds the increment with
+// Knuth's TwoSum, which returns the rounded sum and its exact error.  All
+// with explicit roundings, so every kernel computes the same bits.  A call
+// starts with lo = 0 and returns hi: the FP32 state alone determines the
+// continuation.
+__device__ __forceinline__ float ext_stage(float hi, float lo, float c, float d) {
+    return __fadd_rn(hi, fmaf(c, d, lo));
+}
+
+// (hi, lo) += c a: t = c a + lo, then TwoSum(hi, t).
+__device__ __forceinline__ void ext_step(float &hi, float &lo, float c, float a) {
+    const float t = fmaf(c, a, lo);
+    const float s = __fadd_rn(hi, t);
+    const float bp = __fsub_rn(s, hi);
+    lo = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(t, bp));
+    hi = s;
+}
+
+// (hi, lo) += inc (TwoSum of hi and inc + lo).
+__device__ __forceinline__ void ext_add(float &hi, float &lo, float inc) { ext_step(hi, lo, 1.0f, inc); }
+
+// Gate maps in increment form.  A stage's gate of a (presynaptic neuron,
+// type) pair is an affine function of its step-start gates r0 (and s0):
+//   r = r0 + (P + Qm r0),          (r-map F = (P, Qm))
+//   s = s0 + (U + X r0 + Zm s0),   (s-map F2 = (U, X, Zm, Kd))
+// i.e. Q = 1 + Qm and Z = 1 + Zm are kept as their differences from 1
+// (rounding Q itself would cost bits of Qm, which is of order dt (a T + b)).
+// The identity map is all zeros.
+__device__ __forceinline__ float map_r(float2 F, float r0) { return __fadd_rn(r0, fmaf(F.y, r0, F.x)); }
+__device__ __forceinline__ float map_s(float4 F2, float r0, float s0) {
+    return __fadd_rn(s0, fmaf(F2.z, s0, fmaf(F2.y, r0, F2.x)));
 }
 
 __device__ __forceinline__ void set_error(int *err, int code) { atomicCAS(err, 0, code); }

@@ -113,7 +113,8 @@ struct GlobalCoef {
 template <bool HAS2, bool PAIR>
 __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, const StageRT &sg,
                                            const StageRT &sx, const Items &it, int lo, int N, int nt, int M,
-                                           long long rec_slot, float *vst, float *y0, float *acc, float *ys,
+                                           long long rec_slot, float *vst, float *y0, float *ylo, float *acc,
+                                           float *ys,
                                            const float *prm, const float *iext, float2 *cur1, float2 *acc1,
                                            float4 *cur2, float4 *acc2, float *pst, float *gtab, const float *stab,
                                            int par, unsigned long long &tgt, bool more) {
@@ -140,7 +141,7 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
     __syncthreads();
     // independent work units: potential of each owned neuron and the gate map
     // of each own (neuron, type) pair; the potentials take whole warps
-    float *r0p = pst, *s0p = pst + Mloc;
+    float *r0p = pst, *s0p = pst + Mloc, *r0lo = pst + 2 * Mloc, *s0lo = pst + 3 * Mloc;
     float *gout = PAIR ? g.gt + (size_t)(par ^ 1) * g.mt : nullptr;
     float2 *o1 = g.c1 + (size_t)(par ^ 1) * M + (size_t)lo * nt;
     float4 *o2 = HAS2 ? g.c2 + (size_t)(par ^ 1) * M + (size_t)lo * nt : nullptr;
@@ -151,9 +152,9 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
             if (u >= N) continue;
             const int i = u;
             const float V = vcur[i];
-            const VPre pre = neuron_v_pre(sg, i, N, V, ysc, y0, acc, prm, iext[i]);
+            const VPre pre = neuron_v_pre(sg, i, N, V, ysc, y0, ylo, acc, prm, iext[i]);
             const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
-            const float vn = neuron_v_post(sg, i, pre, isyn, y0, acc);
+            const float vn = neuron_v_post(sg, i, pre, isyn, y0, ylo, acc);
             vnxt[i] = vn;
             if (LAST && rec_slot >= 0) v.rec[rec_slot * v.N + lo + i] = vn;
         } else {
@@ -172,12 +173,16 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
                 const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
                 float G;
                 if (!LAST) {
-                    G = pair_gate(sec, cur1[p], c2, r0p[p], s0p[p]);
+                    G = pair_gate(sec, cur1[p], c2, r0p[p], s0p[p], r0lo[p], s0lo[p]);
                 } else {
-                    const float r0 = r0p[p], s0 = s0p[p];
-                    G = pair_gate(sec, f1, f2, r0, s0);
-                    r0p[p] = fmaf(f1.y, r0, f1.x);
-                    if (sec) s0p[p] = fmaf(f2.z, s0, fmaf(f2.y, r0, f2.x));
+                    // the step's end gates: the next step's first-stage gates and step-start state
+                    float r0 = r0p[p], s0 = s0p[p], rl = r0lo[p], sl = s0lo[p];
+                    pair_step(sec, f1, f2, r0, s0, rl, sl);
+                    G = pair_gate(sec, make_float2(0.0f, 0.0f), make_float4(0.0f, 0.0f, 0.0f, f2.w), r0, s0, rl, sl);
+                    r0p[p] = r0;
+                    s0p[p] = s0;
+                    r0lo[p] = rl;
+                    s0lo[p] = sl;
                 }
                 gout[t] = G;
             } else {
@@ -199,7 +204,7 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
         // the other CTAs arrive; that stage reads this one's ysn and vnxt
         // (after a step's last stage comes the first stage of the next step)
         float *ysx = ys + par * 3 * N;
-        for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates(sx, i, N, vnxt[i], ysn, ysx, y0, acc);
+        for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates(sx, i, N, vnxt[i], ysn, ysx, y0, ylo, acc);
     }
     return true;
 }
@@ -212,7 +217,8 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
     const int nt = v.n_stypes, Mloc = N * nt;
     const int M = (int)(v.N * nt);
     const NeuronLayout L = make_nlayout(N, N, Mloc, HAS2, PAIR, 0);  // the gate table sits after the layout
-    float *y0 = (float *)(smem + L.y0), *ys = (float *)(smem + L.ys), *acc = (float *)(smem + L.acc);
+    float *y0 = (float *)(smem + L.y0), *ylo = (float *)(smem + L.ylo), *ys = (float *)(smem + L.ys);
+    float *acc = (float *)(smem + L.acc);
     float *prm = (float *)(smem + L.prm), *iext = (float *)(smem + L.iext), *inp = (float *)(smem + L.inp);
     float *vst = (float *)(smem + L.vst);
     float2 *cur1 = (float2 *)(smem + L.cur1), *acc1 = (float2 *)(smem + L.acc1);
@@ -228,6 +234,11 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
     float *gV = v.state + lo;
     float *gr = v.state + 4 * v.N;
     float *gs = v.state + 4 * v.N + v.S;
+    // the state's remainders (compensated sums), if the handle keeps them
+    float *gVl = v.state_lo ? v.state_lo + lo : nullptr;
+    float *grl = v.state_lo ? v.state_lo + 4 * v.N : nullptr;
+    float *gsl = v.state_lo ? v.state_lo + 4 * v.N + v.S : nullptr;
+    const bool keep_lo = gVl && g.r0lg;
 
     for (int i = tid; i < N; i += nthr) {
         const float V = gV[i];
@@ -236,6 +247,7 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         for (int x = 0; x < 4; ++x) {
             const float y = gV[(long long)x * v.N + i];
             y0[x * N + i] = y;
+            ylo[x * N + i] = gVl ? gVl[(long long)x * v.N + i] : 0.0f;
             if (x > 0) ys[(x - 1) * N + i] = y;  // stage-0 gates, parity 0
         }
         const float *p = v.nparams + (long long)v.neuron_type[lo + i] * PSST_NEURON_NPARAM;
@@ -249,31 +261,37 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
     if (PAIR) {
         // own pairs' step-start gates from one synapse of each, and their
         // stage-0 gates (identity step-end map) in table 0
-        float *r0p = pst, *s0p = pst + Mloc;
+        float *r0p = pst, *s0p = pst + Mloc, *r0lo = pst + 2 * Mloc, *s0lo = pst + 3 * Mloc;
         for (int p = tid; p < Mloc; p += nthr) {
             const int t = g.tix[(size_t)lo * nt + p];
-            float r0 = 0.0f, s0 = 0.0f;
+            float r0 = 0.0f, s0 = 0.0f, rl = 0.0f, sl = 0.0f;
             if (t >= 0) {
                 const float *sp = stab + (p % nt) * 9;
                 const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
                 const long long k = g.rep[t];
                 r0 = gr[k];
                 if (sec) s0 = gs[k];
-                g.gt[t] = pair_gate(sec, make_float2(0.0f, 1.0f),
-                                    make_float4(0.0f, 0.0f, 1.0f, sec ? sp[SP_KD] : 1.0f), r0, s0);
+                if (keep_lo) {
+                    rl = grl[k];
+                    if (sec) sl = gsl[k];
+                }
+                g.gt[t] = pair_gate(sec, make_float2(0.0f, 0.0f),
+                                    make_float4(0.0f, 0.0f, 0.0f, sec ? sp[SP_KD] : 1.0f), r0, s0, rl, sl);
             }
             r0p[p] = r0;
             s0p[p] = s0;
+            r0lo[p] = rl;
+            s0lo[p] = sl;
         }
         load_items_pair(it, v, 0, 0, lo, v.weight, v.syn_code, stab, tmp, g.tix);
     } else {
         // identity step-end maps of the own pairs in table 0 (read by stage 0)
         for (int p = tid; p < Mloc; p += nthr) {
             const int gi = lo * nt + p;
-            g.c1[gi] = make_float2(0.0f, 1.0f);
+            g.c1[gi] = make_float2(0.0f, 0.0f);  // identity maps (increment form)
             if (HAS2) {
                 const float *sp = stab + (p % nt) * 9;
-                g.c2[gi] = make_float4(0.0f, 0.0f, 1.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
+                g.c2[gi] = make_float4(0.0f, 0.0f, 0.0f, sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f);
             }
         }
         load_items<HAS2>(it, v, 0, 0, lo, gr, gs, v.weight, v.syn_code, stab, tmp);
@@ -287,7 +305,7 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         float *ysn = ys + 3 * N;
         if (nsteps > 0) {
             const StageRT s0 = stage_rt(v, 0, dt);
-            for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates(s0, i, N, vcur[i], ysc, ysn, y0, acc);
+            for (int i = nthr - 1 - tid; i < N; i += nthr) neuron_gates(s0, i, N, vcur[i], ysc, ysn, y0, ylo, acc);
         }
     }
     bool ok = true;
@@ -308,8 +326,8 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
 #pragma unroll 1
         for (int s = 0; ok && s < ns; ++s) {
             const StageRT sg = stage_rt(v, s, dt), sx = stage_rt(v, s + 1 < ns ? s + 1 : 0, dt);
-            ok = grid_stage<HAS2, PAIR>(v, g, sg, sx, it, lo, N, nt, M, rec_slot, vst, y0, acc, ys, prm, iext, cur1,
-                                        acc1, cur2, acc2, pst, gtab, stab, (itn * ns + s) & 1, tgt,
+            ok = grid_stage<HAS2, PAIR>(v, g, sg, sx, it, lo, N, nt, M, rec_slot, vst, y0, ylo, acc, ys, prm, iext,
+                                        cur1, acc1, cur2, acc2, pst, gtab, stab, (itn * ns + s) & 1, tgt,
                                         s + 1 < ns || more);
         }
         // the next step's input currents (own data) run before stage 0's wait
@@ -320,12 +338,16 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
 
     if (PAIR) {
         // the owners hand their pairs' gates to the CTAs owning the synapses
-        const float *r0p = pst, *s0p = pst + Mloc;
+        const float *r0p = pst, *s0p = pst + Mloc, *r0lo = pst + 2 * Mloc, *s0lo = pst + 3 * Mloc;
         for (int p = tid; p < Mloc; p += nthr) {
             const int t = g.tix[(size_t)lo * nt + p];
             if (t >= 0) {
                 g.r0g[t] = r0p[p];
                 g.s0g[t] = s0p[p];
+                if (keep_lo) {
+                    g.r0lg[t] = r0lo[p];
+                    g.s0lg[t] = s0lo[p];
+                }
             }
         }
         if (!grid_barrier(g.bar, g.timeout_ns, v.err)) return;
@@ -333,8 +355,13 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
         for (long long k = k0 + tid; k < k1; k += nthr) {
             const uint32_t code = v.syn_code[k];
             const int t = g.tix[code & 0xFFFFFFu];
+            const bool sec = HAS2 && second_order(stab, code);
             gr[k] = __ldcg(g.r0g + t);
-            if (HAS2 && second_order(stab, code)) gs[k] = __ldcg(g.s0g + t);
+            if (sec) gs[k] = __ldcg(g.s0g + t);
+            if (keep_lo) {
+                grl[k] = __ldcg(g.r0lg + t);
+                if (sec) gsl[k] = __ldcg(g.s0lg + t);
+            }
         }
     } else {
         // the last stage wrote the step's final maps into the table of the
@@ -350,6 +377,7 @@ __device__ void grid_run(const NetView &v, const GridView &g, long long step0, i
             const float y = y0[x * N + i];
             bad |= !isfinite(y);
             gV[(long long)x * v.N + i] = y;
+            if (gVl) gVl[(long long)x * v.N + i] = ylo[x * N + i];
         }
     }
     if (bad) set_error(v.err, PSST_ERR_NONFINITE);

@@ -22,10 +22,10 @@ constexpr int INDEP_THREADS = 256;
 // the next stage's gates.
 template <int ST>
 __device__ __forceinline__ float indep_stage(const NetView &v, float V, const float *ysc, float *ysn, float *y0,
-                                             float *acc, const float *prm, float iext, float dt) {
+                                             float *ylo, float *acc, const float *prm, float iext, float dt) {
     const StageCT<ST> sg{stage_coef<ST>(v, dt)};
-    neuron_gates(sg, 0, 1, V, ysc, ysn, y0, acc);
-    return neuron_v(sg, 0, 1, V, ysc, y0, acc, prm, iext, 0.0f);
+    neuron_gates(sg, 0, 1, V, ysc, ysn, y0, ylo, acc);
+    return neuron_v(sg, 0, 1, V, ysc, y0, ylo, acc, prm, iext, 0.0f);
 }
 
 // Thread t integrates neuron ind_neuron[t] of network ind_net[t] for nsteps
@@ -37,10 +37,11 @@ __global__ void __launch_bounds__(INDEP_THREADS) indep_kernel(NetView v, const i
     if (t >= count) return;
     const long long gi = ind_neuron[t];
     const int b = ind_net[t];
-    float y0[4], acc[4], ysa[3], ysb[3], prm[PSST_NEURON_NPARAM];
+    float y0[4], ylo[4], acc[4], ysa[3], ysb[3], prm[PSST_NEURON_NPARAM];
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
         y0[x] = v.state[(long long)x * v.N + gi];
+        ylo[x] = v.state_lo ? v.state_lo[(long long)x * v.N + gi] : 0.0f;
         acc[x] = 0.0f;
         if (x > 0) ysa[x - 1] = y0[x];
     }
@@ -58,13 +59,13 @@ __global__ void __launch_bounds__(INDEP_THREADS) indep_kernel(NetView v, const i
         const float iext = input_current(v, i_const, pulse, step >= pon && step < poff, gi, step);
         if (v.method == PSST_METHOD_EULER) {
             // one stage per step; the gates alternate between ysa and ysb by step
-            if (itn & 1) V = indep_stage<4>(v, V, ysb, ysa, y0, acc, prm, iext, dt);
-            else V = indep_stage<4>(v, V, ysa, ysb, y0, acc, prm, iext, dt);
+            if (itn & 1) V = indep_stage<4>(v, V, ysb, ysa, y0, ylo, acc, prm, iext, dt);
+            else V = indep_stage<4>(v, V, ysa, ysb, y0, ylo, acc, prm, iext, dt);
         } else if (v.method == PSST_METHOD_TABLEAU) {
             // stage s of step itn reads the gates of parity (itn * n + s) & 1
 #define PSST_TAB_STAGE(n, s)                                                                                    \
-    V = (((itn * (n) + (s)) & 1) ? indep_stage<tableau_stage(n, s)>(v, V, ysb, ysa, y0, acc, prm, iext, dt)         \
-                                 : indep_stage<tableau_stage(n, s)>(v, V, ysa, ysb, y0, acc, prm, iext, dt))
+    V = (((itn * (n) + (s)) & 1) ? indep_stage<tableau_stage(n, s)>(v, V, ysb, ysa, y0, ylo, acc, prm, iext, dt)         \
+                                 : indep_stage<tableau_stage(n, s)>(v, V, ysa, ysb, y0, ylo, acc, prm, iext, dt))
             switch (v.rk_ns) {
             case 1: PSST_TAB_STAGE(1, 0); break;
             case 2: PSST_TAB_STAGE(2, 0); PSST_TAB_STAGE(2, 1); break;
@@ -74,10 +75,10 @@ __global__ void __launch_bounds__(INDEP_THREADS) indep_kernel(NetView v, const i
 #undef PSST_TAB_STAGE
         } else {
             // stage gates alternate between ysa (even stages read) and ysb
-            V = indep_stage<0>(v, V, ysa, ysb, y0, acc, prm, iext, dt);
-            V = indep_stage<1>(v, V, ysb, ysa, y0, acc, prm, iext, dt);
-            V = indep_stage<2>(v, V, ysa, ysb, y0, acc, prm, iext, dt);
-            V = indep_stage<3>(v, V, ysb, ysa, y0, acc, prm, iext, dt);
+            V = indep_stage<0>(v, V, ysa, ysb, y0, ylo, acc, prm, iext, dt);
+            V = indep_stage<1>(v, V, ysb, ysa, y0, ylo, acc, prm, iext, dt);
+            V = indep_stage<2>(v, V, ysa, ysb, y0, ylo, acc, prm, iext, dt);
+            V = indep_stage<3>(v, V, ysb, ysa, y0, ylo, acc, prm, iext, dt);
         }
         if (rec_phase >= 0) {
             if (rec_phase == 0) v.rec[(((step + 1) / v.rec_stride - 1) % v.rec_cap) * v.N + gi] = V;
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(INDEP_THREADS) indep_kernel(NetView v, const i
     for (int x = 0; x < 4; ++x) {
         bad |= !isfinite(y0[x]);
         v.state[(long long)x * v.N + gi] = y0[x];
+        if (v.state_lo) v.state_lo[(long long)x * v.N + gi] = ylo[x];
     }
     if (bad) set_error(v.err, PSST_ERR_NONFINITE);
 }

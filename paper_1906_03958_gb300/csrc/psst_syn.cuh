@@ -176,12 +176,8 @@ __device__ void store_items(const Items &it, const NetView &v, long long row_g0,
             const long long p = sec ? item_slot(it.ib2[i], m2++, K, it.n2, K * it.n1)
                                     : item_slot(it.ib1[i], m1++, K, it.n1, 0);
             const float r0 = R[p];
-            const float2 F = fin.r(ci);
-            gr[k] = fmaf(F.y, r0, F.x);
-            if (HAS2 && sec) {
-                const float4 F2 = fin.s(ci);
-                gs[k] = fmaf(F2.z, Sg[p], fmaf(F2.y, r0, F2.x));
-            }
+            gr[k] = map_r(fin.r(ci), r0);
+            if (HAS2 && sec) gs[k] = map_s(fin.s(ci), r0, Sg[p]);
         }
     }
 }
@@ -190,7 +186,7 @@ __device__ void store_items(const Items &it, const NetView &v, long long row_g0,
 // accumulate A += w G, B += wE G.  At the step's first stage the previous
 // step's final map is applied and the new step-start gate stored.
 __device__ __forceinline__ void syn1(bool first, float &r, float w, float we, float2 F, float &A, float &B) {
-    const float g = fmaf(F.y, r, F.x);
+    const float g = map_r(F, r);
     if (first) r = g;
     A = fmaf(w, g, A);
     B = fmaf(we, g, B);
@@ -198,14 +194,14 @@ __device__ __forceinline__ void syn1(bool first, float &r, float w, float we, fl
 
 __device__ __forceinline__ void syn2(bool first, float &r, float &s, float w, float we, float2 F, float4 F2,
                                      float &A, float &B) {
-    const float rr = fmaf(F.y, r, F.x);
-    const float ss = fmaf(F2.z, s, fmaf(F2.y, r, F2.x));
+    const float rr = map_r(F, r);
+    const float ss = map_s(F2, r, s);
     if (first) {
         r = rr;
         s = ss;
     }
     const float s2 = ss * ss, s4 = s2 * s2;
-    const float g = __fdividef(s4, __fadd_rn(s4, F2.w));  // no contraction into an FMA: same bits everywhere
+    const float g = __fdiv_rn(s4, __fadd_rn(s4, F2.w));  // no contraction into an FMA: same bits everywhere
     A = fmaf(w, g, A);
     B = fmaf(we, g, B);
 }
@@ -518,12 +514,22 @@ __device__ __forceinline__ void put_gate(float *Gt, int e, int lrep, float G) {
 // Gate value G of a pair from its stage maps and step-start gates, with
 // exactly the operations of syn1/syn2 (first order: r; second order:
 // s^4 / (s^4 + Kd), Kd in F2.w).
-__device__ __forceinline__ float pair_gate(bool second, float2 F, float4 F2, float r0, float s0) {
-    const float rr = fmaf(F.y, r0, F.x);
+__device__ __forceinline__ float pair_gate(bool second, float2 F, float4 F2, float r0, float s0, float r0lo,
+                                           float s0lo) {
+    const float rr = __fadd_rn(r0, __fadd_rn(fmaf(F.y, r0, F.x), r0lo));
     if (!second) return rr;
-    const float ss = fmaf(F2.z, s0, fmaf(F2.y, r0, F2.x));
+    const float ss = __fadd_rn(s0, __fadd_rn(fmaf(F2.z, s0, fmaf(F2.y, r0, F2.x)), s0lo));
     const float s2 = ss * ss, s4 = s2 * s2;
-    return __fdividef(s4, __fadd_rn(s4, F2.w));
+    return __fdiv_rn(s4, __fadd_rn(s4, F2.w));
+}
+
+// A pair's step-start gates (r0, s0) with their remainders advanced by the
+// step's final maps (F, F2).
+__device__ __forceinline__ void pair_step(bool second, float2 F, float4 F2, float &r0, float &s0, float &r0lo,
+                                          float &s0lo) {
+    const float r_old = r0;
+    ext_add(r0, r0lo, fmaf(F.y, r_old, F.x));
+    if (second) ext_add(s0, s0lo, fmaf(F2.z, s0, fmaf(F2.y, r_old, F2.x)));
 }
 
 // Gate-map update of one (presynaptic neuron j, synapse type tau) pair at
@@ -541,37 +547,41 @@ __device__ __forceinline__ void coef_update(const float *sp, float V, const SG &
     // with a constant stage weight, so every kernel and stage kind (constant
     // or run-time coefficients) gets the same bits
     const float a_ = __fmul_rn(sp[SP_A], T), bb = __fadd_rn(a_, sp[SP_B]);
-    float P = 0.0f, Q = 1.0f, U = 0.0f, X = 0.0f, Z = 1.0f;
+    // stage map (P, Qm) and (U, X, Zm) in increment form (Q = 1 + Qm, Z = 1 + Zm);
+    // the first stage's is the identity
+    float P = 0.0f, Qm = 0.0f, U = 0.0f, X = 0.0f, Zm = 0.0f;
     if (!FIRST) {
         P = cur.x;
-        Q = cur.y;
+        Qm = cur.y;
         if (HAS2) {
             U = cur2.x;
             X = cur2.y;
-            Z = cur2.z;
+            Zm = cur2.z;
         }
     }
-    const float kP = fmaf(-bb, P, a_), kQ = __fmul_rn(-bb, Q);
+    // slope a T (1 - r) - b r = kP + kQ r0, with kQ = -bb Q = -bb - bb Qm
+    const float kP = fmaf(-bb, P, a_), kQ = fmaf(-bb, Qm, -bb);
     float2 A1 = make_float2(sg.first_term(kP), sg.first_term(kQ));
     if (!FIRST) A1 = make_float2(fmaf(WGT, kP, acc.x), fmaf(WGT, kQ, acc.y));
     if (!LAST) {
         acc = A1;
-        cur = make_float2(cnext * kP, fmaf(cnext, kQ, 1.0f));
+        cur = make_float2(cnext * kP, cnext * kQ);
     } else {
-        fin = make_float2(dt6 * A1.x, fmaf(dt6, A1.y, 1.0f));
+        fin = make_float2(dt6 * A1.x, dt6 * A1.y);
     }
     if (HAS2) {
         const float K3 = sp[SP_K3], K4 = sp[SP_K4];
         const float Kd = sp[SP_KIND] != 0.0f ? sp[SP_KD] : 1.0f;
-        const float kU = fmaf(K3, P, __fmul_rn(-K4, U)), kX = fmaf(K3, Q, __fmul_rn(-K4, X));
-        const float kZ = __fmul_rn(-K4, Z);
+        // slope K3 r - K4 s = kU + kX r0 + kZ s0 with kX = K3 Q - K4 X, kZ = -K4 Z
+        const float kU = fmaf(K3, P, __fmul_rn(-K4, U)), kX = fmaf(K3, Qm, fmaf(-K4, X, K3));
+        const float kZ = fmaf(-K4, Zm, -K4);
         float4 A2 = make_float4(sg.first_term(kU), sg.first_term(kX), sg.first_term(kZ), 0.0f);
         if (!FIRST) A2 = make_float4(fmaf(WGT, kU, acc2.x), fmaf(WGT, kX, acc2.y), fmaf(WGT, kZ, acc2.z), 0.0f);
         if (!LAST) {
             acc2 = A2;
-            cur2 = make_float4(cnext * kU, cnext * kX, fmaf(cnext, kZ, 1.0f), Kd);
+            cur2 = make_float4(cnext * kU, cnext * kX, cnext * kZ, Kd);
         } else {
-            fin2 = make_float4(dt6 * A2.x, dt6 * A2.y, fmaf(dt6, A2.z, 1.0f), Kd);
+            fin2 = make_float4(dt6 * A2.x, dt6 * A2.y, dt6 * A2.z, Kd);
         }
     }
 }
@@ -591,12 +601,14 @@ struct VPre {
     float ie;    // I_ext - I_ion
     float invC;  // 1 / C
     float y0;    // step-start V
+    float lo;    // its remainder (compensated state)
     float acc;   // RK4 sum of V's stage slopes so far
 };
 
 template <class SG>
 __device__ __forceinline__ VPre neuron_v_pre(const SG &sg, int i, int n, float V, const float *ysc,
-                                             const float *y0, const float *acc, const float *prm, float iext) {
+                                             const float *y0, const float *ylo, const float *acc, const float *prm,
+                                             float iext) {
     const bool FIRST = sg.first;
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
     // explicit roundings (no contraction left to the compiler), so that every
@@ -611,37 +623,40 @@ __device__ __forceinline__ VPre neuron_v_pre(const SG &sg, int i, int n, float V
     r.ie = __fsub_rn(iext, iion);
     r.invC = prm[NP_C * n + i];  // prm row 0 holds 1/C
     r.y0 = y0[i];
+    r.lo = ylo[i];
     r.acc = FIRST ? 0.0f : acc[i];
     return r;
 }
 
 template <class SG>
 __device__ __forceinline__ float neuron_v_post(const SG &sg, int i, const VPre &p, float isyn, float *y0,
-                                              float *acc) {
+                                              float *ylo, float *acc) {
     const bool FIRST = sg.first, LAST = sg.last;
     const float WGT = sg.c.w, cnext = sg.c.cn, dt6 = sg.c.fin;
     const float d = __fmul_rn(__fsub_rn(p.ie, isyn), p.invC);
     const float ac = FIRST ? sg.first_term(d) : fmaf(WGT, d, p.acc);
     if (!LAST) {
         acc[i] = ac;
-        return fmaf(cnext, d, p.y0);
+        return ext_stage(p.y0, p.lo, cnext, d);
     }
-    const float yn = fmaf(dt6, ac, p.y0);
-    y0[i] = yn;
-    return yn;
+    float hi = p.y0, lo = p.lo;
+    ext_step(hi, lo, dt6, ac);
+    y0[i] = hi;
+    ylo[i] = lo;
+    return hi;
 }
 
 template <class SG>
 __device__ __forceinline__ float neuron_v(const SG &sg, int i, int n, float V, const float *ysc, float *y0,
-                                          float *acc, const float *prm, float iext, float isyn) {
-    return neuron_v_post(sg, i, neuron_v_pre(sg, i, n, V, ysc, y0, acc, prm, iext), isyn, y0, acc);
+                                          float *ylo, float *acc, const float *prm, float iext, float isyn) {
+    return neuron_v_post(sg, i, neuron_v_pre(sg, i, n, V, ysc, y0, ylo, acc, prm, iext), isyn, y0, ylo, acc);
 }
 
 // Gates: writes the next stage's m, h, n, or after the last stage the new
 // step-start ones.
 template <class SG>
 __device__ __forceinline__ void neuron_gates(const SG &sg, int i, int n, float V, const float *ysc, float *ysn,
-                                             float *y0, float *acc) {
+                                             float *y0, float *ylo, float *acc) {
     const bool FIRST = sg.first, LAST = sg.last;
     const float WGT = sg.c.w, cnext = sg.c.cn, dt6 = sg.c.fin;
     const float m = ysc[i], h = ysc[n + i], nn = ysc[2 * n + i];
@@ -657,10 +672,13 @@ __device__ __forceinline__ void neuron_gates(const SG &sg, int i, int n, float V
         float yn;
         if (!LAST) {
             acc[ix] = ac;
-            yn = fmaf(cnext, d[x], y0[ix]);
+            yn = ext_stage(y0[ix], ylo[ix], cnext, d[x]);
         } else {
-            yn = fmaf(dt6, ac, y0[ix]);
-            y0[ix] = yn;
+            float hi = y0[ix], lo = ylo[ix];
+            ext_step(hi, lo, dt6, ac);
+            y0[ix] = hi;
+            ylo[ix] = lo;
+            yn = hi;
         }
         ysn[x * n + i] = yn;
     }

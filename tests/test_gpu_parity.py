@@ -122,6 +122,34 @@ def test_chunked_equals_whole_bitwise():
         np.testing.assert_array_equal(a.read_record(), b.read_record())
 
 
+def test_set_state_restarts_the_compensated_sums():
+    # The step sums carry each state variable's rounding remainder across
+    # steps and calls; get_state returns the FP32 values and set_state starts
+    # the remainders at zero, so a handle continuing from a copied state
+    # agrees with the uninterrupted run far below the single-step bar, and two
+    # handles given the same state continue bit for bit
+    spec = ng.antennal_lobe()
+    N, S = spec.n_neurons, spec.n_synapses
+    y0 = oracle.rest_state(spec).astype(np.float32)
+    with _net(spec, init_state=y0) as a:
+        a.set_step(9900)
+        a.integrate(700)
+        y = a.get_state_numpy()
+        with _net(spec, init_state=y) as b:
+            b.set_step(10600)
+            a.integrate(300)
+            b.integrate(300)
+            a.status(), b.status()
+            assert step_error(b.get_state_numpy(), a.get_state_numpy(), N, S) <= 1e-5
+            yb = b.get_state().clone()
+            a.set_state(yb)
+            b.set_state(yb)
+            a.integrate(200)
+            b.integrate(200)
+            a.status(), b.status()
+            np.testing.assert_array_equal(a.get_state_numpy(), b.get_state_numpy())
+
+
 def test_batched_equals_alone_bitwise():
     specs = [ng.antennal_lobe(seed=21, n_pn=30, n_ln=10), ng.antennal_lobe(seed=22),
              ng.antennal_lobe(seed=23, n_pn=12, n_ln=4, p=0.3)]

@@ -62,6 +62,9 @@ def test_noalloc_matches_grid_mode_on_two_calls():
         err = torch.zeros(1, dtype=torch.int32, device=state.device)
         dn, keep = _device_network(spec, state, rec, err, K)
         for call in range(2):
+            # the no-alloc call starts the remainders of its compensated step
+            # sums at zero, as psst_integrate does after set_state
+            ref.set_state(ref.get_state().clone())
             ref.integrate(150)
             ref.status()
             psst.integrate_grid_noalloc(dn, 150 * call, 150)
