@@ -73,12 +73,13 @@ struct SmemCoef {
     __device__ __forceinline__ float4 s(int i) const { return t2[i]; }
 };
 
-// One stage sg of the handle's method (its flags and coefficients at run
-// time: one copy of this code serves every stage of RK4, Euler and a
-// tableau).  par selects the double-buffered stage potentials and gates read
-// by this stage: the parity of the stage's index counted over the launch.
-template <int CL, bool HAS2, bool PAIR>
-__device__ __forceinline__ void stage(const NetView &v, const StageRT &sg, const Items &it, int n0, int N, int nt,
+// One stage sg of the handle's method: a compile-time descriptor (the four
+// classic RK4 stages, StageCT) or a run-time one (StageRT: one copy of this
+// code serves every stage of Euler and of a tableau); both give the same
+// bits.  par selects the double-buffered stage potentials and gates read by
+// this stage: the parity of the stage's index counted over the launch.
+template <int CL, bool HAS2, bool PAIR, class SG>
+__device__ __forceinline__ void stage(const NetView &v, const SG &sg, const Items &it, int n0, int N, int nt,
                                       int M, int r_lo, int nown, unsigned rank, long long rec_slot, float *vst,
                                       float *y0, float *ylo, float *acc, float *ys, const float *prm,
                                       const float *iext,
@@ -92,7 +93,7 @@ __device__ __forceinline__ void stage(const NetView &v, const StageRT &sg, const
     float *ysn = ys + (par ^ 1) * 3 * nown;
     // gate-map entries: every (neuron, type) pair, or the used pairs (PAIR)
     float *r0p = pst, *s0p = pst + M, *r0lo = pst + 2 * M, *s0lo = pst + 3 * M;
-    const unsigned short *pof = (const unsigned short *)(pst + 4 * M);
+    const unsigned *pof = (const unsigned *)(pst + 4 * M);  // per-pair entries: neuron << 8 | type
     // The gates m, h, n of the owned neurons need only this stage's
     // potentials: they are computed before the S-phase (on the highest
     // threads), where their latency overlaps the S-phase's loads, and leave
@@ -108,11 +109,15 @@ __device__ __forceinline__ void stage(const NetView &v, const StageRT &sg, const
     const int U = nw + M;
     for (int u = tid; u < U; u += nthr) {
         if (u < nw) {
-            if (u >= nown) continue;
-            const int i = u;
+            // the whole warp takes this branch (nw and nthr are multiples of 32)
+            const bool own = u < nown;
+            const int i = own ? u : 0;
+            float isyn = 0.0f;
+            if (PAIR) isyn = row_current_pair(it, i, vcur[r_lo + i], own);
+            if (!own) continue;
             const float V = vcur[r_lo + i];
             const VPre pre = neuron_v_pre(sg, i, nown, V, ysc, y0, ylo, acc, prm, iext[i]);
-            const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
+            if (!PAIR) isyn = row_current<HAS2>(it, i, V);
             const float vn = neuron_v_post(sg, i, pre, isyn, y0, ylo, acc);
             vnxt[r_lo + i] = vn;
             if (CL > 1) {
@@ -126,9 +131,10 @@ __device__ __forceinline__ void stage(const NetView &v, const StageRT &sg, const
             float4 &c2 = HAS2 ? cur2[p] : d4;
             float4 &a2 = HAS2 ? acc2[p] : d4;
             float4 &f2 = HAS2 ? fin2[p] : d4;
-            const int ci = PAIR ? (int)pof[p] : p;  // (neuron, type) pair of the entry
-            const float *sp = stab + (ci % nt) * 9;
-            coef_update<HAS2>(sp, vcur[ci / nt], sg, cur1[p], acc1[p], fin1[p], c2, a2, f2);
+            // presynaptic neuron and synapse type of the entry
+            const int pre = PAIR ? (int)(pof[p] >> 8) : p / nt, tp = PAIR ? (int)(pof[p] & 255u) : p % nt;
+            const float *sp = stab + tp * 9;
+            coef_update<HAS2>(sp, vcur[pre], sg, cur1[p], acc1[p], fin1[p], c2, a2, f2);
             if (PAIR) {
                 // the pair's gate for the next stage (same operations as the per-synapse path)
                 const bool sec = HAS2 && sp[SP_KIND] != 0.0f;
@@ -208,9 +214,12 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         inp[nown + i] = v.pulse_amp ? v.pulse_amp[n0 + gi] : 0.0f;
     }
     const long long pon = v.pulse_on[b], poff = v.pulse_off[b];
-    unsigned short *pof = PAIR ? (unsigned short *)(pst + 4 * M) : nullptr;
+    unsigned *pof = PAIR ? (unsigned *)(pst + 4 * M) : nullptr;
     if (PAIR)
-        for (int k = tid; k < M; k += nthr) pof[k] = (unsigned short)v.pair_of[v.pair_off[b] + k];
+        for (int k = tid; k < M; k += nthr) {
+            const int ci = v.pair_of[v.pair_off[b] + k];  // local pair: neuron * nt + type
+            pof[k] = ((unsigned)(ci / nt) << 8) | (unsigned)(ci % nt);
+        }
     for (int k = tid; k < M; k += nthr) {
         fin1[k] = make_float2(0.0f, 0.0f);  // identity maps (increment form)
         if (HAS2) {
@@ -236,7 +245,7 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
         }
         __syncthreads();
         for (int p = tid; p < M; p += nthr) {
-            const bool sec = HAS2 && stab[(pof[p] % nt) * 9 + SP_KIND] != 0.0f;
+            const bool sec = HAS2 && stab[(pof[p] & 255u) * 9 + SP_KIND] != 0.0f;
             put_gate(Gt, p, lrep,
                      pair_gate(sec, fin1[p], HAS2 ? fin2[p] : make_float4(0.f, 0.f, 0.f, 1.f), pst[p], pst[M + p],
                                pst[2 * M + p], pst[3 * M + p]));
@@ -263,11 +272,20 @@ __device__ void run_net(const NetView &v, int b, const NetPlan &pl, long long st
             iext[i] = input_current(v, inp[i], inp[nown + i], in_pulse, (long long)n0 + r_lo + i, step);
         // iext is read in the N-phase, after the S-phase barrier
         // stage s of step itn reads parity (itn * ns + s) & 1
+#define PSST_STAGE(SG, par)                                                                                    \
+    stage<CL, HAS2, PAIR>(v, SG, it, n0, N, nt, M, r_lo, nown, rank, rec_slot, vst, y0, ylo, acc, ys, prm, iext, \
+                          cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab, par)
+        if (v.method == PSST_METHOD_RK4) {
+            // the classic tableau's stages at compile time (no stage-kind branches on the hot path)
+            PSST_STAGE(StageCT<0>{stage_coef<0>(v, dt)}, 0);
+            PSST_STAGE(StageCT<1>{stage_coef<1>(v, dt)}, 1);
+            PSST_STAGE(StageCT<2>{stage_coef<2>(v, dt)}, 0);
+            PSST_STAGE(StageCT<3>{stage_coef<3>(v, dt)}, 1);
+        } else {
 #pragma unroll 1
-        for (int s = 0; s < ns; ++s)
-            stage<CL, HAS2, PAIR>(v, stage_rt(v, s, dt), it, n0, N, nt, M, r_lo, nown, rank, rec_slot, vst, y0, ylo,
-                                  acc, ys, prm, iext, cur1, acc1, fin1, cur2, acc2, fin2, pst, Gt, lrep, stab,
-                                  (itn * ns + s) & 1);
+            for (int s = 0; s < ns; ++s) PSST_STAGE(stage_rt(v, s, dt), (itn * ns + s) & 1);
+        }
+#undef PSST_STAGE
     }
 
     // write back: owned synapses with the last step's gate map, owned neurons

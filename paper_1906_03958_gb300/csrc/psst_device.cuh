@@ -133,7 +133,7 @@ struct NeuronLayout {
     int vst;               // float [2][n_all]: stage potential, by stage parity
     int tmp;               // int [2][n_own + 1]: scan scratch
     int pair;              // per-pair variant: float [4][m] step-start r, s and their remainders,
-                           // ushort [m] local pair
+                           // uint [m] presynaptic neuron << 8 | synapse type of each entry
     int gt;                // per-pair variant: float [m][rep] stage gate of each entry, rep copies
     int syn;               // start of the synapse items
 };
@@ -165,7 +165,7 @@ __host__ __device__ inline NeuronLayout make_nlayout(int n_own, int n_all, int m
     L.iext = lay_take(o, 4LL * n_own);
     L.inp = lay_take(o, 8LL * n_own);
     L.tmp = lay_take(o, 8LL * (n_own + 1));
-    L.pair = pair ? lay_take(o, 18LL * m) : -1;  // r0, s0, their remainders (float), the local pair (ushort)
+    L.pair = pair ? lay_take(o, 20LL * m) : -1;  // r0, s0, their remainders (float), neuron and type (uint)
     L.gt = pair ? lay_take(o, 4LL * rep * m) : -1;
     L.syn = o;
     return L;

@@ -149,11 +149,15 @@ __device__ __forceinline__ bool grid_stage(const NetView &v, const GridView &g, 
     const int U = nw + Mloc;
     for (int u = tid; u < U; u += nthr) {
         if (u < nw) {
-            if (u >= N) continue;
-            const int i = u;
+            // the whole warp takes this branch (nw and nthr are multiples of 32)
+            const bool own = u < N;
+            const int i = own ? u : 0;
+            float isyn = 0.0f;
+            if (PAIR) isyn = row_current_pair(it, i, vcur[i], own);
+            if (!own) continue;
             const float V = vcur[i];
             const VPre pre = neuron_v_pre(sg, i, N, V, ysc, y0, ylo, acc, prm, iext[i]);
-            const float isyn = PAIR ? row_current_pair(it, i, V) : row_current<HAS2>(it, i, V);
+            if (!PAIR) isyn = row_current<HAS2>(it, i, V);
             const float vn = neuron_v_post(sg, i, pre, isyn, y0, ylo, acc);
             vnxt[i] = vn;
             if (LAST && rec_slot >= 0) v.rec[rec_slot * v.N + lo + i] = vn;

@@ -472,26 +472,32 @@ __device__ __forceinline__ void sphase_pair(const Items &it, const float *Gt, in
 }
 
 // Synaptic current of owned row i from its typed items (fixed order).
-__device__ __forceinline__ float row_current_pair(const Items &it, int i, float V) {
+// Called by all 32 lanes of a warp (valid = false: a lane without a row,
+// which sums nothing): the item partials are loaded in blocks of 8 with
+// predication, over the warp's largest item count, so the loop is uniform
+// across the warp (a divergent, data-dependent loop costs several times its
+// loads and adds here).  The sums run in item order as
+// A += a_t, B = fma(E_t, a_t, B); the padding adds exact zeros (A and B are
+// never -0: A sums w G >= 0 terms, B starts at +0), so every path gets the
+// same bits as the plain item-order loop.
+__device__ __forceinline__ float row_current_pair(const Items &it, int i, float V, bool valid = true) {
+    const int t0 = valid ? it.ib1[i] : 0;
+    const int n = valid ? it.ib1[i + 1] - t0 : 0;
+    const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
     float A = 0.0f, B = 0.0f;
-    int t = it.ib1[i];
-    const int t1 = it.ib1[i + 1];
-    for (; t + 4 <= t1; t += 4) {  // loads issued together, sums in item order
-        const float a0 = it.pa[t], a1 = it.pa[t + 1], a2 = it.pa[t + 2], a3 = it.pa[t + 3];
-        const float e0 = it.pb[t], e1 = it.pb[t + 1], e2 = it.pb[t + 2], e3 = it.pb[t + 3];
-        A += a0;
-        B = fmaf(e0, a0, B);
-        A += a1;
-        B = fmaf(e1, a1, B);
-        A += a2;
-        B = fmaf(e2, a2, B);
-        A += a3;
-        B = fmaf(e3, a3, B);
-    }
-    for (; t < t1; ++t) {
-        const float a = it.pa[t];
-        A += a;
-        B = fmaf(it.pb[t], a, B);
+    for (int base = 0; base < nmax; base += 8) {
+        float a[8], e[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const bool in = base + q < n;
+            a[q] = in ? it.pa[t0 + base + q] : 0.0f;
+            e[q] = in ? it.pb[t0 + base + q] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            A += a[q];
+            B = fmaf(e[q], a[q], B);
+        }
     }
     return fmaf(V, A, -B);
 }
@@ -503,11 +509,15 @@ __device__ __forceinline__ void put_gate(float *Gt, int e, int lrep, float G) {
     const int R = 1 << lrep, l = (int)threadIdx.x;
     float *row = Gt + ((long long)e << lrep);
     if (R >= 4) {
+        // up to 8 predicated 16-byte stores, no loop (R <= 32)
         const float4 g4 = make_float4(G, G, G, G);
         const int n4 = R >> 2;
-        for (int c = 0; c < n4; ++c) ((float4 *)row)[(c + l) & (n4 - 1)] = g4;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c < n4) ((float4 *)row)[(c + l) & (n4 - 1)] = g4;
     } else {
-        for (int c = 0; c < R; ++c) row[c] = G;
+        row[0] = G;
+        if (R > 1) row[1] = G;
     }
 }
 
