@@ -77,7 +77,8 @@ extern "C" {
                              2 or 4 CTAs for all steps; many networks per launch
                              (batched, ragged), one launch per size class */
 #define PSST_MODE_GRID 2  /* one network spread over the whole GPU with a
-                             device-wide barrier per RK4 stage (single network) */
+                             device-wide synchronisation (per-CTA phase flags)
+                             per stage (single network) */
 
 /*
  * A batch of independent networks.  Neurons are numbered globally
@@ -317,7 +318,7 @@ const char *psst_last_error(void);
  * framework's memory pool, a memory-capped or sandboxed process), or code
  * that only receives buffers from its caller.  They pass their own device
  * arrays in the layout below, and the call allocates nothing: the grid-wide
- * kernel's extra memory (gate-map tables, barrier words, per-CTA plan) is
+ * kernel's extra memory (gate-map tables, per-CTA phase flags, plan) is
  * one fixed array of PSST_NOALLOC_SCRATCH_BYTES in device global memory,
  * compiled into the library.  Every GPU that loads the library holds that
  * array until the process exits.
@@ -339,13 +340,28 @@ const char *psst_last_error(void);
  * (different streams without ordering, or different threads) race on the
  * array and give wrong results.
  *
+ * The plan (rows per CTA, item_chunks when it is 0) is the one
+ * psst_integrate makes in grid mode with gate_mode = 1, so item_chunks = 0
+ * gives the same chunk size and bitwise the same results as psst_integrate
+ * with its item_chunks left at 0.
+ *
+ * The array contents are checked on the device before anything else reads
+ * them: row_ptr must rise from 0 to n_synapses; every syn_code must hold a
+ * type below n_syn_types and a pair index pre * n_syn_types + type with the
+ * same type and pre < n_neurons; every neuron_type must lie in
+ * 0..n_neuron_types-1.  A failed check returns PSST_ERR_INVALID_ARG with no
+ * integration launched and *state untouched.  Float contents are not
+ * checked: a NaN or infinity in the state shows up as PSST_ERR_NONFINITE in
+ * *err after the launch.
+ *
  * Limits: n_neurons * n_syn_types < 65536 (the gate-map tables then always
  * fit the array); larger networks return PSST_ERR_UNSUPPORTED, as does a
  * network whose per-CTA share does not fit shared memory.  Errors are
  * reported by return code only (psst_last_error is not updated):
- * INVALID_ARG for a NULL pointer or a bad size/field, UNSUPPORTED for the
- * limits above, CUDA for a failing runtime call.  Device-side failures
- * (TIMEOUT, NONFINITE) are written to *err (the caller zeroes it).
+ * INVALID_ARG for a NULL pointer, a bad size/field or array contents that
+ * fail the checks above, UNSUPPORTED for the limits above, CUDA for a
+ * failing runtime call.  Device-side failures (TIMEOUT, NONFINITE) are
+ * written to *err (the caller zeroes it).
  */
 #define PSST_NOALLOC_SCRATCH_BYTES (4u << 20)
 
@@ -353,6 +369,7 @@ typedef struct {
     int64_t n_neurons, n_synapses;
     int32_t n_syn_types;            /* 1..PSST_MAX_SYN_TYPES */
     int32_t item_chunks;            /* 4-synapse chunks per work item, 0 = chosen by the call */
+    int32_t n_neuron_types;         /* rows of neuron_params, >= 1 */
     const int64_t *row_ptr;         /* device [N+1], CSR by postsynaptic neuron */
     const uint32_t *syn_code;       /* device [S]: (syn_type << 24) | (pre * n_syn_types + syn_type) */
     const float *weight;            /* device [S] */

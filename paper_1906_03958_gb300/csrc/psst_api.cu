@@ -524,8 +524,7 @@ int grid_pair_tables(psst_net *h, const psst_network_desc *d, cudaError_t *err) 
     g.mt = (int)((used + 3) & ~3LL);
     long long *r = nullptr;
     cudaError_t e = upload(h, &r, rep.data(), rep.size());
-    if (e == cudaSuccess) e = h->alloc(&g.gt, (size_t)2 * g.mt);
-    if (e == cudaSuccess) e = cudaMemset(g.gt, 0, (size_t)2 * std::max(g.mt, 1) * sizeof(float));
+    g.used = (int)used;
     if (e == cudaSuccess) e = h->alloc(&g.r0g, (size_t)used);
     if (e == cudaSuccess) e = h->alloc(&g.s0g, (size_t)used);
     if (e == cudaSuccess) e = h->alloc(&g.r0lg, (size_t)used);
@@ -599,7 +598,11 @@ int setup_grid(psst_net *h, const SmemCaps &caps, cudaError_t *err) {
         if (e == cudaSuccess) e = h->alloc(&itd, items.size());
         if (e == cudaSuccess) e = h->alloc(&g.c1, (size_t)(2 * N * nt));
         if (e == cudaSuccess && has2) e = h->alloc(&g.c2, (size_t)(2 * N * nt));
-        if (e == cudaSuccess) e = h->alloc(&g.bar, 2);
+        if (e == cudaSuccess) e = h->alloc(&g.flag, (size_t)parts * psst::GRID_FLAG_STRIDE);
+        if (e == cudaSuccess && g.tix) {
+            g.gts = g.used + parts;
+            e = h->alloc(&g.gt, (size_t)2 * g.gts);
+        }
         g.row_split = rs;
         g.items = itd;
         if (e != cudaSuccess) return *err = e, cuda_fail(e, "grid buffers");

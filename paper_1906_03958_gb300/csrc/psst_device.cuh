@@ -61,10 +61,12 @@ struct NetView {
 enum : uint8_t { NET_HAS2 = 1, NET_PAIR = 2 };  // NET_PAIR: all gates of each (pre, type) pair equal
 
 // Extra device state of the grid-wide mode (one network over all SMs).
+constexpr int GRID_FLAG_STRIDE = 16;  // 64-bit words between two CTAs' phase flags (one 128-byte line each)
+
 struct GridView {
     float2 *c1;                  // [2][N * n_stypes] gate maps (r), double-buffered by stage parity
     float4 *c2;                  // [2][N * n_stypes] gate maps (s), second-order networks only
-    unsigned *bar;               // [2]: the barrier's 64-bit arrival count (8-byte aligned)
+    unsigned long long *flag;    // [gridDim.x][GRID_FLAG_STRIDE] last phase each CTA has published (zeroed before each launch)
     const int *row_split;        // [gridDim.x + 1] first row owned by each CTA
     const int *items;            // [2][gridDim.x] first- and second-order work items of each CTA
     int K;                       // 4-synapse chunks per work item
@@ -74,7 +76,10 @@ struct GridView {
     int mt;                      // entries of one gate table (used pairs, padded to a multiple of 4)
     const int *tix;              // [N * n_stypes] table index of each pair, -1 when no synapse uses it
     const long long *rep;        // [used pairs] one synapse of each pair (holds the pair's gates)
-    float *gt;                   // [2][mt] each pair's gate for the next stage, double-buffered by stage parity
+    int used;                    // used pairs (entries of the gate table)
+    int gts;                     // words of one gate table: used + one heartbeat per CTA
+    unsigned long long *gt;      // [2][gts] tagged words: each used pair's gate for the next stage, then the
+                                 // CTAs' heartbeats; double-buffered by stage parity
     float *r0g, *s0g;            // [used pairs] step-start gates handed to the synapses' owners at the end
     float *r0lg, *s0lg;          // [used pairs] their remainders (null with a null state_lo)
 };

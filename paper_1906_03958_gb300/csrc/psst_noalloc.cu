@@ -6,7 +6,7 @@
 // psst_integrate_grid_noalloc lets them run the grid-wide integration of
 // one network on buffers they already own.  The inputs and outputs are the
 // caller's device arrays; the only extra memory the kernels need -- the
-// double-buffered gate-map tables, the barrier words and the per-CTA plan --
+// double-buffered gate-map tables, the per-CTA phase flags and the plan --
 // lives in one fixed-size array in device global memory that is part of this
 // library (PSST_NOALLOC_SCRATCH_BYTES), so the call itself allocates nothing.
 //
@@ -35,13 +35,20 @@ constexpr int kMaxGrid = 512;  // CTAs of one launch (one per SM)
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Scratch layout (byte offsets).
-constexpr size_t kOffBar = 0;         // unsigned[2]: the grid barrier's 64-bit arrival count
 constexpr size_t kOffFlag = 8;        // unsigned: network holds second-order synapses
+constexpr size_t kOffBad = 12;        // unsigned: bits of the array checks that failed (1 row_ptr, 2 syn_code, 4 neuron_type)
 constexpr size_t kOffPulse = 16;      // long long[2]: pulse window
+constexpr size_t kOffK = 32;          // int: chunks per work item of the launch
 constexpr size_t kOffSplit = 256;     // int[kMaxGrid + 1]: first row of each CTA
 constexpr size_t kOffItems = kOffSplit + 4 * (kMaxGrid + 1 + 63);  // int[2 * kMaxGrid]
-constexpr size_t kOffTables = 8192;   // float2 [2][M], then float4 [2][M]
-static_assert(kOffItems + 8 * kMaxGrid <= kOffTables, "scratch header overlaps the tables");
+constexpr size_t kOffPhase = 8192;    // unsigned long long[kMaxGrid][GRID_FLAG_STRIDE]: each CTA's published phase
+constexpr size_t kOffTables = kOffPhase + 8 * kMaxGrid * psst::GRID_FLAG_STRIDE;  // float2 [2][M], then float4 [2][M]
+// Planning only (dead before the integration launch, which reuses the
+// space for its tables): per row n1, n2 (int[N] each), then the prefix of
+// the row costs (long long[N + 1]).
+constexpr size_t kOffRows = kOffTables;
+static_assert(kOffItems + 8 * kMaxGrid <= kOffPhase, "scratch header overlaps the phase flags");
+static_assert(kOffRows + 16 * 65536 + 8 <= kScratchBytes, "planning arrays exceed the scratch array");
 
 struct DeviceScratch {
     bool ready = false;
@@ -71,66 +78,131 @@ int scratch_base(int dev, unsigned char **out) {
     return PSST_OK;
 }
 
-// Plan of the grid launch, computed on the device from the caller's arrays:
-// CTA c owns rows [split[c], split[c+1]) with about equal synapses + 8 per
-// row, and counts its first- and second-order work items of K chunks.
-__global__ void noalloc_plan_kernel(const long long *row_ptr, const uint32_t *syn_code, const float *sparams,
-                                    long long N, int K, long long pulse_on, long long pulse_off,
+// Array checks and per-row counts, one thread per row: row_ptr must rise
+// from 0 to n_synapses; each syn_code must carry a type below n_syn_types,
+// a pair index pre * n_syn_types + type with that same type and pre < N;
+// each neuron_type must index the neuron table.  A failed check sets its
+// bit in the scratch word kOffBad (and the rest of the call is skipped);
+// nothing outside the arrays' stated extents is read, whatever they hold.
+// Row i's first- and second-order synapse counts go to n1[i], n2[i].
+__global__ void noalloc_rows_kernel(const long long *row_ptr, const uint32_t *syn_code, const int *neuron_type,
+                                    const float *sparams, long long N, long long S, int nt, int n_ntypes,
                                     unsigned char *scratch) {
-    int *split = (int *)(scratch + kOffSplit);
-    int *items = (int *)(scratch + kOffItems);
-    unsigned *flag = (unsigned *)(scratch + kOffFlag);
-    __shared__ long long s_lo, s_hi;
-    __shared__ int s_i1, s_i2;
-    __shared__ unsigned s_has2;
-    const int c = blockIdx.x, G = gridDim.x;
-    if (threadIdx.x == 0) {
-        const double total = (double)row_ptr[N] + 8.0 * (double)N;
-        long long bound[2];
-        for (int q = 0; q < 2; ++q) {
-            const double target = total * (double)(c + q) / (double)G;
-            long long lo = 0, hi = N;
-            while (lo < hi) {  // first row whose prefix cost reaches the target
-                const long long mid = (lo + hi) / 2;
-                if ((double)row_ptr[mid] + 8.0 * (double)mid < target) lo = mid + 1;
-                else hi = mid;
-            }
-            bound[q] = lo;
+    int *n1a = (int *)(scratch + kOffRows), *n2a = n1a + N;
+    unsigned bad = 0, h2 = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        long long a = row_ptr[i], b = row_ptr[i + 1];
+        if ((i == 0 && a != 0) || (i == N - 1 && b != S)) bad |= 1u;
+        if (a < 0 || b < a || b > S) {
+            bad |= 1u;
+            a = b = 0;
         }
-        s_lo = bound[0];
-        s_hi = (c == G - 1) ? N : bound[1];
-        s_i1 = s_i2 = 0;
-        s_has2 = 0;
-        split[c] = (int)s_lo;
-        if (c == G - 1) split[G] = (int)N;
-        if (c == 0) {
-            unsigned *bar = (unsigned *)(scratch + kOffBar);
-            bar[0] = bar[1] = 0u;
-            long long *pw = (long long *)(scratch + kOffPulse);
-            pw[0] = pulse_on;
-            pw[1] = pulse_off;
-        }
-    }
-    __syncthreads();
-    int i1 = 0, i2 = 0;
-    unsigned h2 = 0;
-    for (long long i = s_lo + threadIdx.x; i < s_hi; i += blockDim.x) {
         int n2 = 0;
-        for (long long k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
-            n2 += sparams[(syn_code[k] >> 24) * PSST_SYN_NPARAM] != 0.0f;
-        const int n1 = (int)(row_ptr[i + 1] - row_ptr[i]) - n2;
-        i1 += psst::part_items(n1, K);
-        i2 += psst::part_items(n2, K);
+        for (long long k = a; k < b; ++k) {
+            const uint32_t code = syn_code[k];
+            const unsigned t = code >> 24, idx = code & 0xFFFFFFu;
+            if (t >= (unsigned)nt || idx % (unsigned)nt != t || (long long)(idx / (unsigned)nt) >= N) {
+                bad |= 2u;
+                continue;
+            }
+            n2 += sparams[t * PSST_SYN_NPARAM + psst::SP_KIND] != 0.0f;
+        }
+        const int ty = neuron_type[i];
+        if (ty < 0 || ty >= n_ntypes) bad |= 4u;
+        n1a[i] = (int)(b - a) - n2;
+        n2a[i] = n2;
         h2 |= n2 != 0;
     }
-    atomicAdd(&s_i1, i1);
-    atomicAdd(&s_i2, i2);
-    atomicOr(&s_has2, h2);
+    if (bad) atomicOr((unsigned *)(scratch + kOffBad), bad);
+    if (h2) atomicOr((unsigned *)(scratch + kOffFlag), 1u);
+}
+
+// Plan of the grid launch (one CTA of PLAN_THREADS threads), the same as
+// psst_integrate's grid mode with one gate per synapse: row i costs its
+// 4-synapse chunks of each order plus 2; CTA c owns the rows up to the
+// first whose cost prefix reaches c/G of the total; without a caller's K,
+// K = ceil(largest CTA's chunks / 768), clamped to 1..8; then each CTA's
+// first- and second-order work items of K chunks.
+constexpr int PLAN_THREADS = 1024;
+
+__global__ void __launch_bounds__(PLAN_THREADS) noalloc_plan_kernel(long long N, int G, int user_K, long long pulse_on,
+                                                                   long long pulse_off, unsigned char *scratch) {
+    if (*(volatile unsigned *)(scratch + kOffBad) != 0) return;  // arrays rejected: plan nothing
+    const int *n1a = (const int *)(scratch + kOffRows), *n2a = n1a + N;
+    long long *pref = (long long *)(scratch + kOffRows + 8 * N);
+    int *split = (int *)(scratch + kOffSplit);
+    int *items = (int *)(scratch + kOffItems);
+    __shared__ long long s_part[PLAN_THREADS];
+    __shared__ long long s_worst;
+    const int tid = threadIdx.x;
+    auto row_chunks = [&](long long i) -> long long { return (n1a[i] + 3) / 4 + (n2a[i] + 3) / 4; };
+    // cost prefix: thread t sums a contiguous block of rows, then a block scan
+    const long long R = (N + PLAN_THREADS - 1) / PLAN_THREADS;
+    const long long r0 = tid * R < N ? tid * R : N, r1 = r0 + R < N ? r0 + R : N;
+    long long sum = 0;
+    for (long long i = r0; i < r1; ++i) sum += row_chunks(i) + 2;
+    s_part[tid] = sum;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        items[c] = s_i1;
-        items[G + c] = s_i2;
-        if (s_has2) atomicOr(flag, 1u);
+    for (int off = 1; off < PLAN_THREADS; off <<= 1) {  // inclusive Hillis-Steele scan
+        const long long x = tid >= off ? s_part[tid - off] : 0;
+        __syncthreads();
+        s_part[tid] += x;
+        __syncthreads();
+    }
+    long long run = s_part[tid] - sum;
+    for (long long i = r0; i < r1; ++i) {
+        pref[i] = run;
+        run += row_chunks(i) + 2;
+    }
+    if (tid == PLAN_THREADS - 1) pref[N] = s_part[tid];
+    if (tid == 0) s_worst = 0;
+    __syncthreads();
+    const double total = (double)pref[N];
+    for (int c = tid; c <= G; c += PLAN_THREADS) {
+        long long lo = 0;
+        if (c == G) {
+            lo = N;
+        } else if (c > 0) {
+            const double target = total * c / G;
+            long long hi = N;
+            while (lo < hi) {  // first row whose cost prefix reaches the target
+                const long long mid = (lo + hi) / 2;
+                if ((double)pref[mid] < target) lo = mid + 1;
+                else hi = mid;
+            }
+        }
+        split[c] = (int)lo;
+    }
+    __syncthreads();
+    for (int c = tid; c < G; c += PLAN_THREADS) {
+        const long long a = split[c], b = split[c + 1];
+        atomicMax((unsigned long long *)&s_worst, (unsigned long long)(pref[b] - pref[a] - 2 * (b - a)));
+    }
+    __syncthreads();
+    const long long kw = (s_worst + 767) / 768;
+    const int K = user_K > 0 ? user_K : (int)(kw < 1 ? 1 : kw > 8 ? 8 : kw);
+    // work items per CTA: warp w takes CTAs w, w + 32, ...
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int c = warp; c < G; c += PLAN_THREADS / 32) {
+        int i1 = 0, i2 = 0;
+        for (int i = split[c] + lane; i < split[c + 1]; i += 32) {
+            i1 += psst::part_items(n1a[i], K);
+            i2 += psst::part_items(n2a[i], K);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            i1 += __shfl_xor_sync(0xffffffffu, i1, o);
+            i2 += __shfl_xor_sync(0xffffffffu, i2, o);
+        }
+        if (lane == 0) {
+            items[c] = i1;
+            items[G + c] = i2;
+        }
+    }
+    if (tid == 0) {
+        *(int *)(scratch + kOffK) = K;
+        long long *pw = (long long *)(scratch + kOffPulse);
+        pw[0] = pulse_on;
+        pw[1] = pulse_off;
     }
 }
 
@@ -145,6 +217,7 @@ extern "C" int psst_integrate_grid_noalloc(const psst_device_network *d, int64_t
     if (d->n_neurons < 1 || d->n_synapses < 0) return err_msg(PSST_ERR_INVALID_ARG, "bad sizes");
     if (d->n_syn_types < 1 || d->n_syn_types > PSST_MAX_SYN_TYPES)
         return err_msg(PSST_ERR_INVALID_ARG, "n_syn_types must be in 1..8");
+    if (d->n_neuron_types < 1) return err_msg(PSST_ERR_INVALID_ARG, "n_neuron_types must be >= 1");
     if (!(d->dt > 0.0f)) return err_msg(PSST_ERR_INVALID_ARG, "dt must be > 0");
     if (d->rec_stride < 0 || (d->rec_stride > 0 && (!d->rec || d->rec_capacity < 1)))
         return err_msg(PSST_ERR_INVALID_ARG, "recording needs rec and rec_capacity >= 1");
@@ -170,27 +243,33 @@ extern "C" int psst_integrate_grid_noalloc(const psst_device_network *d, int64_t
         return err_msg(PSST_ERR_CUDA, "device attributes");
     const int max_dyn = optin - psst::cta_static_smem() - 64;
     const int G = (int)std::max(1LL, std::min<long long>(std::min(sms, kMaxGrid), (N + 7) / 8));
-    int K = d->item_chunks;
-    if (K == 0) {
-        const long long chunks = (d->n_synapses / 4 + N) / G + 1;
-        K = (int)std::max(1LL, std::min(8LL, (chunks + 767) / 768));
-    }
     cudaStream_t st = (cudaStream_t)stream;
 
-    // plan on the device, then check every CTA's shared memory on the host
-    e = cudaMemsetAsync(scratch + kOffFlag, 0, sizeof(unsigned), st);
+    // check the arrays and plan on the device, then check every CTA's shared
+    // memory on the host
+    e = cudaMemsetAsync(scratch + kOffFlag, 0, 2 * sizeof(unsigned), st);  // flag and check words
     if (e == cudaSuccess) {
-        noalloc_plan_kernel<<<G, 256, 0, st>>>((const long long *)d->row_ptr, d->syn_code, d->syn_params, N, K, d->pulse_on,
-                                               d->pulse_off, scratch);
+        const int rows_grid = (int)std::max(1LL, std::min<long long>(4LL * sms, (N + 255) / 256));
+        noalloc_rows_kernel<<<rows_grid, 256, 0, st>>>((const long long *)d->row_ptr, d->syn_code, d->neuron_type,
+                                                       d->syn_params, N, d->n_synapses, d->n_syn_types,
+                                                       d->n_neuron_types, scratch);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        noalloc_plan_kernel<<<1, PLAN_THREADS, 0, st>>>(N, G, d->item_chunks, d->pulse_on, d->pulse_off, scratch);
         e = cudaGetLastError();
     }
     int split[kMaxGrid + 1], items[2 * kMaxGrid];
-    unsigned has2 = 0;
+    unsigned words[2] = {0u, 0u};  // has2, failed checks
+    int K = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(words, scratch + kOffFlag, sizeof(words), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&K, scratch + kOffK, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(split, scratch + kOffSplit, sizeof(int) * (G + 1), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(items, scratch + kOffItems, sizeof(int) * 2 * G, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&has2, scratch + kOffFlag, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return err_msg(PSST_ERR_CUDA, cudaGetErrorString(e));
+    if (words[1] != 0u) return err_msg(PSST_ERR_INVALID_ARG, "row_ptr, syn_code or neuron_type out of range");
+    const unsigned has2 = words[0];
     if (has2 && kOffTables + 2 * (size_t)M * (8 + 16) > kScratchBytes)
         return err_msg(PSST_ERR_UNSUPPORTED, "second-order network too large for the fixed scratch array");
     for (int c = 0; c < G; ++c) {
@@ -228,7 +307,7 @@ extern "C" int psst_integrate_grid_noalloc(const psst_device_network *d, int64_t
     psst::GridView g{};
     g.c1 = (float2 *)(scratch + kOffTables);
     g.c2 = has2 ? (float4 *)(scratch + kOffTables + 2 * (size_t)M * 8) : nullptr;
-    g.bar = (unsigned *)(scratch + kOffBar);
+    g.flag = (unsigned long long *)(scratch + kOffPhase);
     g.row_split = (const int *)(scratch + kOffSplit);
     g.items = (const int *)(scratch + kOffItems);
     g.K = K;

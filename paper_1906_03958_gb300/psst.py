@@ -56,7 +56,8 @@ class NetworkDesc(C.Structure):
 class DeviceNetwork(C.Structure):
     """psst_device_network: one network in caller-owned device arrays."""
     _fields_ = [("n_neurons", C.c_int64), ("n_synapses", C.c_int64), ("n_syn_types", C.c_int32),
-                ("item_chunks", C.c_int32), ("row_ptr", C.c_void_p), ("syn_code", C.c_void_p),
+                ("item_chunks", C.c_int32), ("n_neuron_types", C.c_int32), ("row_ptr", C.c_void_p),
+                ("syn_code", C.c_void_p),
                 ("weight", C.c_void_p), ("neuron_type", C.c_void_p), ("neuron_params", C.c_void_p),
                 ("syn_params", C.c_void_p), ("i_const", C.c_void_p), ("pulse_amp", C.c_void_p),
                 ("pulse_on", C.c_int64), ("pulse_off", C.c_int64), ("noise_seed", C.c_uint64),
