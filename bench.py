@@ -120,12 +120,24 @@ def measured_peaks():
         return {}
 
 
-def kernel_source_hash() -> str:
-    """Hash of the kernel sources' code (line comments and blank lines
-    dropped, so that a comment edit does not invalidate a capture)."""
+# Sources that decide each kernel's memory traffic: its own file, the
+# shared device headers and the host planner (launch shapes, layouts).
+KERNEL_SOURCES = {
+    "net_kernel": ("psst_cta.cu", "psst_syn.cuh"),
+    "grid_kernel": ("psst_grid.cu", "psst_syn.cuh"),
+    "adj_kernel": ("psst_adjoint.cu",),
+    "indep_kernel": ("psst_indep.cu",),
+}
+COMMON_SOURCES = ("psst_device.cuh", "psst_internal.h", "psst_api.cu")
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the code of the sources a kernel's traffic depends on (line
+    comments and blank lines dropped, so that a comment edit does not
+    invalidate a capture)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1906_03958_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(KERNEL_SOURCES[kernel] + COMMON_SOURCES):
         for line in open(os.path.join(csrc, f), encoding="utf-8"):
             code = line.split("//", 1)[0].rstrip()
             if code:
@@ -144,7 +156,7 @@ def traffic_for(kernel: str, workload: str, steps: int | None = None):
     except Exception:
         return None
     e = t.get(f"{kernel}:{workload}")
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     b = e.get("bytes_per_launch")
     if b is not None and steps and e.get("captured_steps"):
