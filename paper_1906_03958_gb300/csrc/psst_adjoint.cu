@@ -40,11 +40,17 @@
 //   us_p = -C_p G'(s_p) - K4 kbs_p               [second order]
 //   with the column sum C_p = sum_{k in p} w_k (q_i V_i - q_i E_k);
 //   dL/dw_k += -q_i G_p (V_i - E_k);  dL/dgNa += -q_i m^3 h (V - ENa), ...
-// The column sums go through per-warp partial rows summed in warp order when
-// no row holds two synapses of one pair (fixed order, reproducible), else
-// through shared-memory atomics (order not fixed).  The weight gradients are
-// summed over each step's stages in one pass, into an FP32 partial per
-// segment, then into an FP64 total.
+// The two CTAs hold the synapses in different layouts: the forward CTA
+// in row items (the synaptic current's row sums), the sweeping CTA in
+// column items, the synapses of each pair p cut into items of KC chunks of
+// 4 with the column's m-th synapse (rows in CSR order) in item m mod nq,
+// position m / nq (nq = the pair's items), so that the lanes of a warp
+// gather the stage products (q_i V_i, q_i) of consecutive rows.  One
+// thread per column item sums w (q_i V_i - E_p q_i) over its synapses;
+// the pair's owner adds its items' partials in item order (fixed order,
+// reproducible).  The weight gradients are summed over each step's stages
+// in one pass over the column items, into an FP32 partial per segment,
+// then into an FP64 total.
 #include <cuda_runtime.h>
 
 #include "psst_device.cuh"
@@ -80,12 +86,14 @@ __device__ __forceinline__ float ratio_u_deriv(float u) {
 }
 
 struct AdjSmem {
-    // items (row-aligned, K chunks of 4 synapses, slot-major)
+    // forward CTA: row items (row-aligned, K chunks of 4 synapses,
+    // slot-major) with the pair of each synapse in id; sweeping CTA: column
+    // items (KC chunks, slot-major) with the row of each synapse in id
     float4 *w;
     ushort4 *id;
-    float *pa, *pb;
-    int *ib;           // [N+1] first item of each row
-    unsigned short *irow;  // [n_items] row of each item
+    float *pa, *pb;    // forward: item partials A and B; sweep: column item partials (pa)
+    int *ib;           // forward: [N+1] first item of each row; sweep: [M+1] first item of each pair
+    unsigned short *irow;  // sweep: [n_citems] pair of each column item
     // per stage s = 0..3 (stored by the forward recompute)
     float *sV, *sm, *sh, *sn;  // [4][N]
     float *sr, *ss, *sG;       // [4][M]
@@ -97,24 +105,30 @@ struct AdjSmem {
     // adjoint
     float *lam, *yprev, *ysum; // [4N + 2M]
     float2 *ab;                // [4][N]: q_i V_i, q_i at each stage
-    float *csum;               // [M]
     float *uV;                 // [N] partial uV
     double *gp;                // [N][9] neuron parameter gradients
     float *Ep;                 // [M] reversal potential of each pair's type
     float *prm;                // [9][N] (row 0: 1/C)
     float *iext, *inp;         // [N], [2][N]
-    float *cpart;              // [ADJ_THREADS / 32][M] per-warp column-sum rows, or null (atomics)
 };
 
-__host__ __device__ inline long long adj_smem_bytes(int N, int M, int n_items, int K) {
+// Row items of the forward CTA (K chunks each) and column items of the
+// sweeping CTA (KC chunks each) share one region of shared memory.
+__host__ __device__ inline long long adj_item_chunks(int n_items, int K, int n_citems, int KC) {
+    const long long r = (long long)K * n_items, c = (long long)KC * n_citems;
+    return r > c ? r : c;
+}
+
+__host__ __device__ inline long long adj_smem_bytes(int N, int M, int n_items, int K, int n_citems, int KC) {
     long long b = 0;
-    const long long slots = (long long)K * n_items;
-    b += slots * (16 + 8);              // w, id
-    b += 8LL * n_items + 2LL * n_items + 16;  // pa, pb, irow
-    b += 4LL * (N + 1);
+    const long long chunks = adj_item_chunks(n_items, K, n_citems, KC);
+    const long long parts = 8LL * n_items > 4LL * n_citems ? 8LL * n_items : 4LL * n_citems;
+    b += chunks * (16 + 8);             // w, id
+    b += parts + 2LL * n_citems + 16;   // pa, pb (column partials), irow
+    b += 4LL * ((N > M ? N : M) + 1);   // ib
     b += 4LL * 4 * (6LL * N + 3LL * M);  // stage storage
     b += 4LL * 6 * (4LL * N + 2LL * M);  // y, ylo, acc, lam, yprev, ysum
-    b += 32LL * N + 4LL * M + 4LL * N;    // ab, csum, uV
+    b += 32LL * N + 4LL * N;             // ab, uV
     b += 8LL * 9 * N;                    // gp (double)
     b += 4LL * 9 * N + 4LL * 3 * N;      // prm, iext, inp
     b += 4LL * M;                        // Ep
@@ -129,7 +143,7 @@ __device__ inline unsigned char *take(unsigned char *&p, long long bytes) {
 }
 
 struct AdjNet {
-    int b, n0, N, nt, M, K, n_items, R;
+    int b, n0, N, nt, M, K, n_items, KC, n_citems, R;
     long long sbase, S;
 };
 
@@ -191,43 +205,61 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
         const float cnext = TAB ? (st < 3 ? v.rk_c[st] * dt : 0.0f) : (st == 2) ? dt : 0.5f * dt;
         const float dt6 = TAB ? v.rk_beta * dt : NST == 1 ? dt : dt * (1.0f / 6.0f);  // scale of the step's sum
         const float W0 = TAB ? v.rk_w[0] : 1.0f;  // weight of the first stage's slope
-        for (int i = tid; i < N; i += nthr) {
-            float A = 0.0f, B = 0.0f;
-            for (int it = S.ib[i]; it < S.ib[i + 1]; ++it) {
-                A += S.pa[it];
-                B += S.pb[it];
-            }
-            const float Vs = S.sV[st * N + i], ms = S.sm[st * N + i], hs = S.sh[st * N + i], ns = S.sn[st * N + i];
-            const Rates q = hh_rates(Vs);
-            const float *P = S.prm;
-            const float m3h = ms * ms * ms * hs, n4 = ns * ns * ns * ns;
-            const float iion = P[NP_GNA * N + i] * m3h * (Vs - P[NP_ENA * N + i]) +
-                               P[NP_GK * N + i] * n4 * (Vs - P[NP_EK * N + i]) +
-                               P[NP_GL * N + i] * (Vs - P[NP_EL * N + i]) +
-                               P[NP_GKL * N + i] * (Vs - P[NP_EKL * N + i]);
-            const float fV = (S.iext[i] - iion - fmaf(Vs, A, -B)) * P[NP_C * N + i];
-            const float d[4] = {fV, q.am * (1.0f - ms) - q.bm * ms, q.ah * (1.0f - hs) - q.bh * hs,
-                                q.an * (1.0f - ns) - q.bn * ns};
-            if (STORE) {
-                S.sA[st * N + i] = A;
-                S.sfv[st * N + i] = fV;
-            }
-            float *stg[4] = {S.sV, S.sm, S.sh, S.sn};
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                const int ix = x * N + i;
-                const float ac = (st == 0) ? W0 * d[x] : fmaf(WGT, d[x], S.acc[ix]);
-                if (st < NST - 1) {
-                    S.acc[ix] = ac;
-                    stg[x][(st + 1) * N + i] = ext_stage(S.y[ix], S.ylo[ix], cnext, d[x]);
-                } else {
-                    ext_step(S.y[ix], S.ylo[ix], dt6, ac);
+        // independent units, each on its own thread: the potential of each
+        // neuron (row sums, ionic current), its gates m, h, n (rate
+        // functions) and every gate pair (transmitter, r and s)
+        float *stg[4] = {S.sV, S.sm, S.sh, S.sn};
+        for (int u = tid; u < 2 * N + M; u += nthr) {
+            if (u < N) {
+                const int i = u;
+                float A = 0.0f, B = 0.0f;
+                for (int it = S.ib[i]; it < S.ib[i + 1]; ++it) {
+                    A += S.pa[it];
+                    B += S.pb[it];
                 }
-            }
-            // own gate pairs
-            for (int t = 0; t < nt; ++t) {
-                const int p = i * nt + t;
+                const float Vs = S.sV[st * N + i], ms = S.sm[st * N + i], hs = S.sh[st * N + i],
+                            ns = S.sn[st * N + i];
+                const float *P = S.prm;
+                const float m3h = ms * ms * ms * hs, n4 = ns * ns * ns * ns;
+                const float iion = P[NP_GNA * N + i] * m3h * (Vs - P[NP_ENA * N + i]) +
+                                   P[NP_GK * N + i] * n4 * (Vs - P[NP_EK * N + i]) +
+                                   P[NP_GL * N + i] * (Vs - P[NP_EL * N + i]) +
+                                   P[NP_GKL * N + i] * (Vs - P[NP_EKL * N + i]);
+                const float fV = (S.iext[i] - iion - fmaf(Vs, A, -B)) * P[NP_C * N + i];
+                if (STORE) {
+                    S.sA[st * N + i] = A;
+                    S.sfv[st * N + i] = fV;
+                }
+                const float ac = (st == 0) ? W0 * fV : fmaf(WGT, fV, S.acc[i]);
+                if (st < NST - 1) {
+                    S.acc[i] = ac;
+                    S.sV[(st + 1) * N + i] = ext_stage(S.y[i], S.ylo[i], cnext, fV);
+                } else {
+                    ext_step(S.y[i], S.ylo[i], dt6, ac);
+                }
+            } else if (u < 2 * N) {
+                const int i = u - N;
+                const float Vs = S.sV[st * N + i], ms = S.sm[st * N + i], hs = S.sh[st * N + i],
+                            ns = S.sn[st * N + i];
+                const Rates q = hh_rates(Vs);
+                const float d[3] = {q.am * (1.0f - ms) - q.bm * ms, q.ah * (1.0f - hs) - q.bh * hs,
+                                    q.an * (1.0f - ns) - q.bn * ns};
+#pragma unroll
+                for (int x = 1; x < 4; ++x) {
+                    const int ix = x * N + i;
+                    const float ac = (st == 0) ? W0 * d[x - 1] : fmaf(WGT, d[x - 1], S.acc[ix]);
+                    if (st < NST - 1) {
+                        S.acc[ix] = ac;
+                        stg[x][(st + 1) * N + i] = ext_stage(S.y[ix], S.ylo[ix], cnext, d[x - 1]);
+                    } else {
+                        ext_step(S.y[ix], S.ylo[ix], dt6, ac);
+                    }
+                }
+            } else {
+                // gate pair p = (presynaptic neuron i, type t)
+                const int p = u - 2 * N, i = p / nt, t = p - i * nt;
                 const float *sp = stab + t * 9;
+                const float Vs = S.sV[st * N + i];
                 const float rs = S.sr[st * M + p], ss = S.ss[st * M + p];
                 const float T = transmitter(Vs, sp[SP_VP], sp[SP_KP]);
                 const float dr = sp[SP_A] * T * (1.0f - rs) - sp[SP_B] * rs;
@@ -235,12 +267,11 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
                 const int ir = 4 * N + p, is = 4 * N + M + p;
                 const float ar = (st == 0) ? W0 * dr : fmaf(WGT, dr, S.acc[ir]);
                 const float as = (st == 0) ? W0 * ds : fmaf(WGT, ds, S.acc[is]);
-                float rn, sn;
                 if (st < NST - 1) {
                     S.acc[ir] = ar;
                     S.acc[is] = as;
-                    rn = ext_stage(S.y[ir], S.ylo[ir], cnext, dr);
-                    sn = ext_stage(S.y[is], S.ylo[is], cnext, ds);
+                    const float rn = ext_stage(S.y[ir], S.ylo[ir], cnext, dr);
+                    const float sn = ext_stage(S.y[is], S.ylo[is], cnext, ds);
                     S.sr[(st + 1) * M + p] = rn;
                     S.ss[(st + 1) * M + p] = sn;
                     const float s2 = sn * sn, s4 = s2 * s2;
@@ -257,44 +288,26 @@ __device__ void fwd_step(const NetView &v, const AdjNet &a, const AdjSmem &S, co
 
 // ---------------------------------------------------------------- reverse
 
-// Column sums C_p = sum_k w_k (q_i V_i - q_i E_k) of stage st into S.csum.
-// A warp walks one row's synapses at a time (their pairs are distinct, so
-// the lanes never meet on an address): into its own partial row when S.cpart
-// is set, then the rows are added in warp order; else with atomics.
+// Column sums of stage st: each column item's partial
+// sum_k w_k (q_i V_i - E_p q_i) over its synapses in slot order, into S.pa.
 __device__ __forceinline__ void column_sums(const AdjNet &a, const AdjSmem &S, int st) {
-    const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, M = a.M, K = a.K, ni = a.n_items;
-    const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
-    const int lk = __ffs(K) - 1;  // K is a power of two
-    const float *Wf = (const float *)S.w;
-    const unsigned short *Id = (const unsigned short *)S.id;
-    float *mine = S.cpart ? S.cpart + (long long)wid * M : nullptr;
-    for (int i = wid; i < N; i += nwarps) {
-        const float2 abv = S.ab[st * N + i];
-        const int t0 = S.ib[i], nslot = (S.ib[i + 1] - t0) * K * 4;
-#pragma unroll 2
-        for (int m = lane; m < nslot; m += 32) {
-            const int cq = m >> 2, q = cq >> lk, j = cq & (K - 1);
-            const int slot = ((j * ni + t0 + q) << 2) + (m & 3);
-            const float w = Wf[slot];
-            if (w != 0.0f) {
-                const int pp = Id[slot];
-                const float x = w * fmaf(-S.Ep[pp], abv.y, abv.x);
-                if (mine) mine[pp] += x;
-                else atomicAdd(&S.csum[pp], x);
-            }
+    const int tid = threadIdx.x, nthr = blockDim.x, KC = a.KC, nc = a.n_citems;
+    const float2 *ab = S.ab + st * a.N;
+    for (int t = tid; t < nc; t += nthr) {
+        const float E = S.Ep[S.irow[t]];
+        float c = 0.0f;
+#pragma unroll 4
+        for (int j = 0; j < KC; ++j) {
+            const int q = j * nc + t;
+            const float4 w = S.w[q];
+            const ushort4 r = S.id[q];
+            const float2 a0 = ab[r.x], a1 = ab[r.y], a2 = ab[r.z], a3 = ab[r.w];
+            c = fmaf(w.x, fmaf(-E, a0.y, a0.x), c);
+            c = fmaf(w.y, fmaf(-E, a1.y, a1.x), c);
+            c = fmaf(w.z, fmaf(-E, a2.y, a2.x), c);
+            c = fmaf(w.w, fmaf(-E, a3.y, a3.x), c);
         }
-        __syncwarp();  // the next row may touch the same pairs from other lanes
-    }
-    if (S.cpart) {
-        __syncthreads();
-        for (int q = tid; q < M; q += nthr) {
-            float c = 0.0f;
-            for (int w = 0; w < nwarps; ++w) {
-                c += S.cpart[(long long)w * M + q];
-                S.cpart[(long long)w * M + q] = 0.0f;
-            }
-            S.csum[q] = c;
-        }
+        S.pa[t] = c;
     }
 }
 
@@ -305,8 +318,7 @@ __device__ __forceinline__ void column_sums(const AdjNet &a, const AdjSmem &S, i
 template <int NST>
 __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, const float *cb, const float *ca,
                          float4 *gpart) {
-    const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M, K = a.K, ni = a.n_items;
-    const int D = 4 * N + 2 * M;
+    const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M;
 #pragma unroll 1
     for (int st = NST - 1; st >= 0; --st) {
         // A) owners: stage adjoint kb, neuron-local products, parameter gradients
@@ -360,8 +372,8 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
             for (int t = 0; t < nt; ++t) {
                 const int p = i * nt + t;
                 const float *sp = stab + t * 9;
-                const float C = S.csum[p];
-                S.csum[p] = 0.0f;
+                float C = 0.0f;  // the pair's column sum: its items' partials in item order
+                for (int q = S.ib[p]; q < S.ib[p + 1]; ++q) C += S.pa[q];
                 const int ir = 4 * N + p, is = 4 * N + M + p;
                 const float kbr = cb[st] * S.lam[ir] + (st < NST - 1 ? ca[st] * S.yprev[ir] : 0.0f);
                 const float kbs = cb[st] * S.lam[is] + (st < NST - 1 ? ca[st] * S.yprev[is] : 0.0f);
@@ -392,27 +404,41 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
         // the next stage's part A reads only owner-written values; its part B
         // reads ab after the barrier that follows part A
     }
-    // weight gradients of the step: dL/dw_k += sum_s -G_p^(s) q_i^(s) (V_i^(s) - E_k),
-    // into the per-segment FP32 partial of each item slot
-    for (int c = tid; c < K * ni; c += nthr) {
-        const int i = S.irow[c % ni];
-        const ushort4 id = S.id[c];
-        const int iv[4] = {id.x, id.y, id.z, id.w};
-        float4 g = gpart[c];
-        float gv[4] = {g.x, g.y, g.z, g.w};
+    // weight gradients of the step: dL/dw_k += sum_s -G_p^(s) q_i^(s) (V_i^(s) - E_p),
+    // into the per-segment FP32 partial of each column slot (the partials of
+    // up to four chunks loaded before any is updated)
+    const int KC = a.KC, nc = a.n_citems;
+    for (int t = tid; t < nc; t += nthr) {
+        const int p = S.irow[t];
+        const float E = S.Ep[p];
+        float G[NST];
 #pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-            const int p = iv[q4];
-            const float E = S.Ep[p];
-            float acc = 0.0f;
+        for (int st = 0; st < NST; ++st) G[st] = S.sG[st * M + p];
+        for (int j0 = 0; j0 < KC; j0 += 4) {
+            float4 g[4];
 #pragma unroll
-            for (int st = 0; st < NST; ++st) {
-                const float2 abv = S.ab[st * N + i];
-                acc = fmaf(S.sG[st * M + p], fmaf(E, abv.y, -abv.x), acc);
+            for (int u = 0; u < 4; ++u)
+                if (j0 + u < KC) g[u] = gpart[(j0 + u) * nc + t];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (j0 + u >= KC) break;
+                const int c = (j0 + u) * nc + t;
+                const ushort4 r = S.id[c];
+                const int iv[4] = {r.x, r.y, r.z, r.w};
+                float gv[4] = {g[u].x, g[u].y, g[u].z, g[u].w};
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int st = 0; st < NST; ++st) {
+                        const float2 abv = S.ab[st * N + iv[q4]];
+                        acc = fmaf(G[st], fmaf(E, abv.y, -abv.x), acc);
+                    }
+                    gv[q4] += acc;
+                }
+                gpart[c] = make_float4(gv[0], gv[1], gv[2], gv[3]);
             }
-            gv[q4] += acc;
         }
-        gpart[c] = make_float4(gv[0], gv[1], gv[2], gv[3]);
     }
     // lam_n = lam + sum of the stage adjoints (owner-only values)
     for (int i = tid; i < N; i += nthr) {
@@ -429,7 +455,6 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
             S.ysum[is] = 0.0f;
         }
     }
-    (void)D;
     __syncthreads();
 }
 
@@ -525,20 +550,25 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     a.M = a.N * a.nt;
     a.K = av.K[a.b];
     a.n_items = av.n_items[a.b];
+    a.KC = av.KC[a.b];
+    a.n_citems = av.n_citems[a.b];
     a.R = 4 * a.N + 2 * a.M;
     a.sbase = v.row_ptr[a.n0];
     a.S = v.row_ptr[a.n0 + a.N] - a.sbase;
-    const int N = a.N, M = a.M, nt = a.nt, K = a.K, ni = a.n_items;
+    const int N = a.N, M = a.M, nt = a.nt, K = a.K, ni = a.n_items, nc = a.n_citems;
+    // the two CTAs of the network's cluster: rank 0 recomputes segments
+    // forward, rank 1 sweeps them backward and owns the gradients
+    const bool fwd_cta = cluster_rank() == 0;
 
     AdjSmem S;
     unsigned char *p = smem;
-    const long long slots = (long long)K * ni;
-    S.w = (float4 *)take(p, 16 * slots);
-    S.id = (ushort4 *)take(p, 8 * slots);
-    S.pa = (float *)take(p, 4LL * ni);
-    S.pb = (float *)take(p, 4LL * ni);
-    S.irow = (unsigned short *)take(p, 2LL * ni);
-    S.ib = (int *)take(p, 4LL * (N + 1));
+    const long long chunks = adj_item_chunks(ni, K, nc, a.KC);
+    S.w = (float4 *)take(p, 16 * chunks);
+    S.id = (ushort4 *)take(p, 8 * chunks);
+    S.pa = (float *)take(p, 8LL * ni > 4LL * nc ? 8LL * ni : 4LL * nc);
+    S.pb = S.pa + ni;
+    S.irow = (unsigned short *)take(p, 2LL * nc);
+    S.ib = (int *)take(p, 4LL * ((N > M ? N : M) + 1));
     S.sV = (float *)take(p, 16LL * N);
     S.sm = (float *)take(p, 16LL * N);
     S.sh = (float *)take(p, 16LL * N);
@@ -555,14 +585,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     S.yprev = (float *)take(p, 4LL * a.R);
     S.ysum = (float *)take(p, 4LL * a.R);
     S.ab = (float2 *)take(p, 32LL * N);
-    S.csum = (float *)take(p, 4LL * M);
     S.uV = (float *)take(p, 4LL * N);
     S.gp = (double *)take(p, 72LL * N);
     S.Ep = (float *)take(p, 4LL * M);
     S.prm = (float *)take(p, 36LL * N);
     S.iext = (float *)take(p, 4LL * N);
     S.inp = (float *)take(p, 8LL * N);
-    S.cpart = av.col_warp[a.b] ? (float *)take(p, 4LL * (ADJ_THREADS / 32) * M) : nullptr;
 
     const long long *rp = v.row_ptr + a.n0;
     const uint32_t *gcode = v.syn_code + a.sbase;
@@ -578,48 +606,58 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         for (int x = 0; x < 9; ++x) S.gp[9 * i + x] = 0.0;
         S.uV[i] = 0.0f;
     }
-    for (int q = tid; q < M; q += nthr) {
-        S.Ep[q] = stab[(q % nt) * 9 + SP_E];
-        S.csum[q] = 0.0f;
-    }
-    if (S.cpart)
-        for (int q = tid; q < (ADJ_THREADS / 32) * M; q += nthr) S.cpart[q] = 0.0f;
+    for (int q = tid; q < M; q += nthr) S.Ep[q] = stab[(q % nt) * 9 + SP_E];
     for (int q = tid; q < a.R; q += nthr) {
         S.lam[q] = 0.0f;
         S.ysum[q] = 0.0f;
         S.yprev[q] = 0.0f;
     }
-    // items: row-aligned, each row's synapses in CSR order
-    int *cnt = (int *)S.acc;  // scratch: acc is written before it is read
-    for (int i = tid; i < N; i += nthr) cnt[i] = (int)((rp[i + 1] - rp[i] + 4 * K - 1) / (4 * K));
-    __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int i = 0; i < N; ++i) {
-            S.ib[i] = acc;
-            acc += cnt[i];
-        }
-        S.ib[N] = acc;
-    }
-    __syncthreads();
-    for (long long c = tid; c < slots; c += nthr) {
-        S.w[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-        S.id[c] = make_ushort4(0, 0, 0, 0);
-    }
-    for (int i = tid; i < N; i += nthr)
-        for (int it = S.ib[i]; it < S.ib[i + 1]; ++it) S.irow[it] = (unsigned short)i;
-    for (int it = S.ib[N] + tid; it < ni; it += nthr) S.irow[it] = 0;  // inert padding items (w = 0)
-    __syncthreads();
     float *W = (float *)S.w;
     unsigned short *ID = (unsigned short *)S.id;
-    for (int i = tid; i < N; i += nthr) {
-        const long long k0 = rp[i] - a.sbase;
-        for (long long k = k0; k < rp[i + 1] - a.sbase; ++k) {
-            const int m = (int)(k - k0);
-            const int t = S.ib[i] + m / (4 * K), j = (m % (4 * K)) >> 2;
-            const long long slot = ((long long)j * ni + t) * 4 + (m & 3);
-            W[slot] = gw[k];
-            ID[slot] = (unsigned short)(gcode[k] & 0xFFFFFFu);
+    const long long cslot0 = av.cslot_off[a.b];
+    if (fwd_cta) {
+        // row items: row-aligned, each row's synapses in CSR order
+        const long long slots = (long long)K * ni;
+        int *cnt = (int *)S.acc;  // scratch: acc is written before it is read
+        for (int i = tid; i < N; i += nthr) cnt[i] = (int)((rp[i + 1] - rp[i] + 4 * K - 1) / (4 * K));
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int i = 0; i < N; ++i) {
+                S.ib[i] = acc;
+                acc += cnt[i];
+            }
+            S.ib[N] = acc;
+        }
+        for (long long c = tid; c < slots; c += nthr) {
+            S.w[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            S.id[c] = make_ushort4(0, 0, 0, 0);
+        }
+        __syncthreads();
+        for (int i = tid; i < N; i += nthr) {
+            const long long k0 = rp[i] - a.sbase;
+            for (long long k = k0; k < rp[i + 1] - a.sbase; ++k) {
+                const int m = (int)(k - k0);
+                const int t = S.ib[i] + m / (4 * K), j = (m % (4 * K)) >> 2;
+                const long long slot = ((long long)j * ni + t) * 4 + (m & 3);
+                W[slot] = gw[k];
+                ID[slot] = (unsigned short)(gcode[k] & 0xFFFFFFu);
+            }
+        }
+    } else {
+        // column items (host plan): the pair of each item, each slot's
+        // synapse (-1: padding, w = 0) and row
+        const int *cib = av.cib + av.cib_off[a.b];
+        for (int q = tid; q <= M; q += nthr) S.ib[q] = cib[q];
+        __syncthreads();
+        for (int q = tid; q < M; q += nthr)
+            for (int t = S.ib[q]; t < S.ib[q + 1]; ++t) S.irow[t] = (unsigned short)q;
+        const int *ck = av.ck + cslot0;
+        const unsigned short *cr = av.crow + cslot0;
+        for (long long q = tid; q < 4LL * a.KC * nc; q += nthr) {
+            const int k = ck[q];
+            W[q] = k >= 0 ? gw[k] : 0.0f;
+            ID[q] = cr[q];
         }
     }
     __syncthreads();
@@ -646,16 +684,15 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
             cb[q] = v.rk_beta * v.rk_w[q] * dt;
             ca[q] = q < 3 ? v.rk_c[q] * dt : 0.0f;
         }
-    // the two CTAs of the network's cluster: rank 0 recomputes segments
-    // forward, rank 1 sweeps them backward and owns the gradients
-    const bool fwd_cta = cluster_rank() == 0;
     float *seg0 = av.seg + av.seg_off[a.b];
     const long long seg_buf = (long long)min(ckpt, nsteps) * step_floats;  // floats of one segment buffer
-    float4 *gpart = av.gpart + av.slot_off[a.b] / 4;
-    double *gtot = av.gtot + av.slot_off[a.b];
+    // per-segment FP32 and total FP64 weight gradients, column-slot order
+    const long long cchunks = (long long)a.KC * nc;
+    float4 *gpart = av.gpart + cslot0 / 4;
+    double *gtot = av.gtot + cslot0;
     if (!fwd_cta) {
-        for (long long c = tid; c < slots; c += nthr) gpart[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        for (long long c = tid; c < slots * 4; c += nthr) gtot[c] = 0.0;
+        for (long long c = tid; c < cchunks; c += nthr) gpart[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (long long c = tid; c < cchunks * 4; c += nthr) gtot[c] = 0.0;
     }
     // frames: global steps k in (step0, step0 + nsteps] with k % stride == 0
     const int stride = v.rec_stride;
@@ -704,7 +741,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
             __syncthreads();
         }
         // fold the segment's partial sums into the FP64 totals
-        for (long long q = tid; q < slots; q += nthr) {
+        for (long long q = tid; q < cchunks; q += nthr) {
             const float4 g = gpart[q];
             gtot[4 * q] += g.x;
             gtot[4 * q + 1] += g.y;
@@ -729,14 +766,14 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     }
     if (fwd_cta) return;
     // outputs (rank 1): weight gradients in CSR order, neuron parameter partials
-    for (int i = tid; i < N; i += nthr) {
-        const long long k0 = rp[i] - a.sbase;
-        for (long long k = k0; k < rp[i + 1] - a.sbase; ++k) {
-            const int m = (int)(k - k0);
-            const int t = S.ib[i] + m / (4 * K), j = (m % (4 * K)) >> 2;
-            const long long slot = ((long long)j * ni + t) * 4 + (m & 3);
-            av.grad_w[a.sbase + k] = (float)gtot[slot];
+    {
+        const int *ck = av.ck + cslot0;
+        for (long long q = tid; q < cchunks * 4; q += nthr) {
+            const int k = ck[q];
+            if (k >= 0) av.grad_w[a.sbase + k] = (float)gtot[q];
         }
+    }
+    for (int i = tid; i < N; i += nthr) {
         for (int x = 0; x < 9; ++x) av.gp_neuron[(long long)(a.n0 + i) * 9 + x] = S.gp[9 * i + x];
         for (int x = 0; x < 4; ++x) av.grad_y0[(long long)x * v.N + a.n0 + i] = S.lam[x * N + i];
     }
@@ -761,8 +798,8 @@ long long adj_segment_floats(int method, int rk_ns, int N, int nt) {
     return adj_step_floats(nst, N, (long long)N * nt);
 }
 
-long long adj_smem_need(int N, int nt, int n_items, int K, bool col_warp) {
-    return adj_smem_bytes(N, N * nt, n_items, K) + (col_warp ? 4LL * (ADJ_THREADS / 32) * N * nt + 16 : 0);
+long long adj_smem_need(int N, int nt, int n_items, int K, int n_citems, int KC) {
+    return adj_smem_bytes(N, N * nt, n_items, K, n_citems, KC);
 }
 
 cudaError_t adj_launch(const NetView &v, const AdjView &av, long long step0, int nsteps, int smem, int n_types,

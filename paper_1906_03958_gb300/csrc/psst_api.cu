@@ -67,7 +67,6 @@ struct PlanInput {
     std::vector<int> net_off, n1, n2;
     std::vector<int> tcnt;       // [N][nt] synapses of each type per row
     std::vector<int> pair_off;   // [n_nets + 1] used (presynaptic neuron, type) pairs of the networks
-    std::vector<uint8_t> rows_unique;  // [n_nets] no row holds two synapses of one pair
     std::vector<long long> net_syn;
     std::vector<uint8_t> flags;  // NET_HAS2 | NET_PAIR per network
 };
@@ -91,9 +90,10 @@ struct psst_net {
     // adjoint plan and scratch (allocated on the first psst_adjoint)
     std::vector<int> adj_K, adj_items;
     int adj_smem = 0;
-    int *d_adjK = nullptr, *d_adjI = nullptr;
-    long long *d_segoff = nullptr, *d_slotoff = nullptr;
-    uint8_t *d_colwarp = nullptr;  // [n_nets] adjoint column sums through per-warp rows
+    int *d_adjK = nullptr, *d_adjI = nullptr, *d_adjKC = nullptr, *d_adjCI = nullptr;
+    int *d_cib = nullptr, *d_ck = nullptr;  // column plan: items of each pair, synapse of each slot
+    unsigned short *d_crow = nullptr;       // row of each column slot
+    long long *d_segoff = nullptr, *d_cslotoff = nullptr, *d_ciboff = nullptr;
     float *adj_seg = nullptr, *adj_gy0 = nullptr;
     float4 *adj_gpart = nullptr;
     double *adj_gtot = nullptr;
@@ -781,19 +781,6 @@ int psst_create_network(const psst_network_desc *d, const psst_allocator *a, pss
             }
     }
     pair_off[n_nets] = (int)pof.size();
-    pin.rows_unique.assign((size_t)n_nets, 1);
-    {
-        std::vector<long long> last_row((size_t)N * nt, -1);  // last row that used each pair
-        for (int b = 0; b < n_nets; ++b) {
-            const long long base = (long long)d->net_neuron_off[b] * nt;
-            for (long long i = d->net_neuron_off[b]; i < d->net_neuron_off[b + 1]; ++i)
-                for (long long k = d->row_ptr[i]; k < d->row_ptr[i + 1]; ++k) {
-                    const size_t p = (size_t)(base + (long long)d->pre[k] * nt + d->syn_type[k]);
-                    if (last_row[p] == i) pin.rows_unique[b] = 0;
-                    last_row[p] = i;
-                }
-        }
-    }
     bool all_fit = true;
     for (int b = 0; b < n_nets && all_fit; ++b) {
         if (pin.net_syn[b] == 0) continue;  // independent neurons need no shared-memory plan
@@ -1459,16 +1446,21 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
         e = cudaMemcpy(off.data(), h->v.net_off, off.size() * sizeof(int), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = cudaMemcpy(rp.data(), h->v.row_ptr, rp.size() * sizeof(long long), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint plan");
+        std::vector<uint32_t> code((size_t)h->v.S);
+        e = cudaMemcpy(code.data(), h->v.syn_code, code.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint plan");
         h->adj_K.resize(n_nets);
         h->adj_items.resize(n_nets);
-        std::vector<long long> slot_off((size_t)n_nets), seg_rows((size_t)n_nets);
-        std::vector<uint8_t> col_warp((size_t)n_nets, 0);
+        std::vector<int> KC((size_t)n_nets), citems((size_t)n_nets), cib, ck;
+        std::vector<unsigned short> crow;
+        std::vector<long long> cslot_off((size_t)n_nets), cib_off((size_t)n_nets);
         long long slots = 0;
         int need = 0;
         for (int b = 0; b < n_nets; ++b) {
-            const int n0 = off[b], N = off[b + 1] - n0;
-            const long long S = rp[n0 + N] - rp[n0];
-            // chunks per item: a power of two (1..8), about 1024 items per network
+            const int n0 = off[b], N = off[b + 1] - n0, M = N * nt;
+            const long long S = rp[n0 + N] - rp[n0], sb = rp[n0];
+            // row items (forward CTA): chunks per item a power of two (1..8),
+            // about 1024 items per network
             const int K0 = (int)std::max(1LL, std::min(8LL, (S / 4 + 1023) / 1024));
             const int K = K0 >= 8 ? 8 : K0 >= 4 ? 4 : K0 >= 2 ? 2 : 1;
             int items = 0;
@@ -1478,27 +1470,61 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
             // consecutive synapses of a row (over planes j < K and items q < 8/K)
             // start on 8 different 4-bank groups
             while (items % 8 != (8 / K) % 8 && !(K == 8 && items % 2 == 1)) ++items;
-            if (N >= 65536 || (long long)N * nt >= 65536)
+            if (N >= 65536 || (long long)M >= 65536)
                 return fail(PSST_ERR_UNSUPPORTED, "adjoint: net %d too large (%d neurons)", b, N);
-            long long bytes = psst::adj_smem_need(N, nt, items, K, false);
+            // column items (sweeping CTA): the smallest chunks per item (1..8)
+            // that leave at most one item per thread, each pair's synapses
+            // dealt round-robin over its items (rows in CSR order)
+            std::vector<int> cnt((size_t)M, 0);
+            for (long long k = sb; k < sb + S; ++k) ++cnt[code[(size_t)k] & 0xFFFFFFu];
+            int kc = 1, nci = 0;
+            for (;; kc *= 2) {
+                nci = 0;
+                for (int q = 0; q < M; ++q) nci += (cnt[q] + 4 * kc - 1) / (4 * kc);
+                if (nci <= 1024 || kc == 8) break;
+            }
+            const long long bytes = psst::adj_smem_need(N, nt, items, K, nci, kc);
             if (bytes > h->max_dyn)
                 return fail(PSST_ERR_UNSUPPORTED, "adjoint: net %d needs %lld B of shared memory (max %d)", b, bytes,
                             h->max_dyn);
-            // per-warp column-sum rows when no row repeats a pair and they fit
-            const long long bytes_cw = psst::adj_smem_need(N, nt, items, K, true);
-            col_warp[b] = h->pin.rows_unique[b] && bytes_cw <= h->max_dyn;
-            if (col_warp[b]) bytes = bytes_cw;
             need = std::max<int>(need, (int)bytes);
+            cib_off[b] = (long long)cib.size();
+            std::vector<int> first((size_t)M + 1), seen((size_t)M, 0);
+            int acc = 0;
+            for (int q = 0; q < M; ++q) {
+                first[q] = acc;
+                acc += (cnt[q] + 4 * kc - 1) / (4 * kc);
+            }
+            first[M] = acc;
+            cib.insert(cib.end(), first.begin(), first.end());
+            cslot_off[b] = slots;
+            const long long cslots = 4LL * kc * nci;
+            ck.resize((size_t)(slots + cslots), -1);
+            crow.resize((size_t)(slots + cslots), 0);
+            for (int i = n0; i < n0 + N; ++i)
+                for (long long k = rp[i]; k < rp[i + 1]; ++k) {
+                    const int q = (int)(code[(size_t)k] & 0xFFFFFFu), nq = first[q + 1] - first[q];
+                    const int m = seen[q]++, t = first[q] + m % nq, pos = m / nq;
+                    const long long slot = slots + ((long long)(pos >> 2) * nci + t) * 4 + (pos & 3);
+                    ck[(size_t)slot] = (int)(k - sb);
+                    crow[(size_t)slot] = (unsigned short)(i - n0);
+                }
             h->adj_K[b] = K;
             h->adj_items[b] = items;
-            slot_off[b] = slots;
-            slots += 4LL * K * items;
+            KC[b] = kc;
+            citems[b] = nci;
+            slots += cslots;
         }
         h->adj_smem = need;
         e = upload(h, &h->d_adjK, h->adj_K.data(), h->adj_K.size());
         if (e == cudaSuccess) e = upload(h, &h->d_adjI, h->adj_items.data(), h->adj_items.size());
-        if (e == cudaSuccess) e = upload(h, &h->d_slotoff, slot_off.data(), slot_off.size());
-        if (e == cudaSuccess) e = upload(h, &h->d_colwarp, col_warp.data(), col_warp.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_adjKC, KC.data(), KC.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_adjCI, citems.data(), citems.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_cib, cib.data(), cib.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_ciboff, cib_off.data(), cib_off.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_ck, ck.data(), ck.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_crow, crow.data(), crow.size());
+        if (e == cudaSuccess) e = upload(h, &h->d_cslotoff, cslot_off.data(), cslot_off.size());
         if (e == cudaSuccess) e = h->alloc(&h->adj_gpart, (size_t)slots / 4);
         if (e == cudaSuccess) e = h->alloc(&h->adj_gtot, (size_t)slots);
         if (e == cudaSuccess) e = h->alloc(&h->adj_gpn, (size_t)h->v.N * 9);
@@ -1529,6 +1555,13 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
     psst::AdjView av{};
     av.K = h->d_adjK;
     av.n_items = h->d_adjI;
+    av.KC = h->d_adjKC;
+    av.n_citems = h->d_adjCI;
+    av.cib = h->d_cib;
+    av.cib_off = h->d_ciboff;
+    av.ck = h->d_ck;
+    av.crow = h->d_crow;
+    av.cslot_off = h->d_cslotoff;
     av.ckpt_every = ckpt_every;
     av.ck_full = h->rec_ck;
     av.ck_full_lo = h->rec_ck_lo;
@@ -1537,13 +1570,11 @@ int psst_adjoint(psst_net *h, int64_t n_steps, const float *dL_dV, int64_t n_fra
     av.seg_off = h->d_segoff;
     av.gpart = h->adj_gpart;
     av.gtot = h->adj_gtot;
-    av.slot_off = h->d_slotoff;
     av.dLdV = dL_dV;
     av.n_frames = (int)n_frames;
     av.grad_w = grad_w;
     av.gp_neuron = h->adj_gpn;
     av.grad_y0 = grad_state0 ? grad_state0 : h->adj_gy0;
-    av.col_warp = h->d_colwarp;
     e = psst::adj_launch(h->v, av, s0, (int)n_steps, h->adj_smem, h->n_ntypes, grad_neuron_params,
                          (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "psst_adjoint launch");

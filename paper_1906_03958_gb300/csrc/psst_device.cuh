@@ -91,23 +91,28 @@ enum { SP_KIND = 0, SP_A, SP_B, SP_K3, SP_K4, SP_KD, SP_E, SP_VP, SP_KP };
 // Device state of one adjoint launch (psst_adjoint): per-network work-item
 // size, checkpoint and segment storage, gradient accumulators, outputs.
 struct AdjView {
-    const int *K;               // [n_nets] chunks per work item
-    const int *n_items;         // [n_nets]
+    const int *K;               // [n_nets] chunks per row item (forward CTA)
+    const int *n_items;         // [n_nets] row items
+    const int *KC;              // [n_nets] chunks per column item (sweeping CTA)
+    const int *n_citems;        // [n_nets] column items
+    const int *cib;             // first column item of each pair, [M + 1] per network at cib_off
+    const long long *cib_off;   // [n_nets]
+    const int *ck;              // per column slot: the network's synapse index (-1: padding), at cslot_off
+    const unsigned short *crow; // per column slot: the synapse's row (postsynaptic neuron)
+    const long long *cslot_off; // [n_nets] column-slot offset of each network (multiple of 4)
     int ckpt_every;
     const float *ck_full;       // full states [4N+2S] every ckpt_every steps, recorded by the forward kernel
     const float *ck_full_lo;    // their remainders (same layout)
     long long dim;              // 4N + 2S
     float *seg;                 // step states of the segment being swept
     const long long *seg_off;   // [n_nets]
-    float4 *gpart;              // per-segment FP32 partial weight gradients, item-slot order (4 per chunk)
-    double *gtot;               // FP64 totals, item-slot order
-    const long long *slot_off;  // [n_nets] slot offset of each network (multiple of 4)
+    float4 *gpart;              // per-segment FP32 partial weight gradients, column-slot order (4 per chunk)
+    double *gtot;               // FP64 totals, column-slot order
     const float *dLdV;          // [n_frames][N]
     int n_frames;
     float *grad_w;              // [S] output, CSR order
     double *gp_neuron;          // [N][9] per-neuron parameter gradients
     float *grad_y0;             // [4][N] output: adjoint of V, m, h, n at the start
-    const uint8_t *col_warp;    // [n_nets] 1: column sums through per-warp partial rows (no atomics)
 };
 
 #define PSST_MAX_CL 4

@@ -33,7 +33,7 @@ cudaError_t grid_launch(const NetView &v, const GridView &g, long long step0, in
                         int smem, cudaStream_t stream);
 
 // Discrete adjoint (psst_adjoint.cu).
-long long adj_smem_need(int N, int nt, int n_items, int K, bool col_warp);
+long long adj_smem_need(int N, int nt, int n_items, int K, int n_citems, int KC);
 // Floats one step keeps in an adjoint segment buffer (its stages: RK4 four,
 // Euler one, a tableau rk_ns).
 long long adj_segment_floats(int method, int rk_ns, int N, int nt);
