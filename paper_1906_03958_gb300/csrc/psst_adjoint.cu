@@ -106,7 +106,8 @@ struct AdjSmem {
     float *lam, *yprev, *ysum; // [4N + 2M]
     float2 *ab;                // [4][N]: q_i V_i, q_i at each stage
     float *uV;                 // [N] partial uV
-    double *gp;                // [N][9] neuron parameter gradients
+    float2 *gp;                // [N][9] neuron parameter gradients, compensated FP32 sums (hi, lo)
+    float2 *uvc;               // [M] each pair's term of its presynaptic potential's adjoint
     float *Ep;                 // [M] reversal potential of each pair's type
     float *prm;                // [9][N] (row 0: 1/C)
     float *iext, *inp;         // [N], [2][N]
@@ -129,7 +130,8 @@ __host__ __device__ inline long long adj_smem_bytes(int N, int M, int n_items, i
     b += 4LL * 4 * (6LL * N + 3LL * M);  // stage storage
     b += 4LL * 6 * (4LL * N + 2LL * M);  // y, ylo, acc, lam, yprev, ysum
     b += 32LL * N + 4LL * N;             // ab, uV
-    b += 8LL * 9 * N;                    // gp (double)
+    b += 8LL * 9 * N;                    // gp (float2)
+    b += 8LL * M;                        // uvc
     b += 4LL * 9 * N + 4LL * 3 * N;      // prm, iext, inp
     b += 4LL * M;                        // Ep
     b += 16 * 32;                        // alignment slack
@@ -321,79 +323,100 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
     const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M;
 #pragma unroll 1
     for (int st = NST - 1; st >= 0; --st) {
-        // A) owners: stage adjoint kb, neuron-local products, parameter gradients
-        for (int i = tid; i < N; i += nthr) {
+        // A) two units per neuron: the potential's products (ab) and parameter
+        // gradients, and the gates' products (uV partial, gate adjoints)
+        for (int u = tid; u < 2 * N; u += nthr) {
+            const bool gates = u >= N;
+            const int i = gates ? u - N : u;
             const float Vs = S.sV[st * N + i], ms = S.sm[st * N + i], hs = S.sh[st * N + i], ns = S.sn[st * N + i];
-            float kb[4];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                const int ix = x * N + i;
-                kb[x] = cb[st] * S.lam[ix] + (st < NST - 1 ? ca[st] * S.yprev[ix] : 0.0f);
-            }
             const float *P = S.prm;
-            const float invC = P[NP_C * N + i];
-            const float q = kb[0] * invC;
-            S.ab[st * N + i] = make_float2(q * Vs, q);
-            const Rates rt = hh_rates(Vs);
-            const float dam = 0.1f * ratio_u_deriv((Vs + 40.0f) * 0.1f), dbm = -rt.bm * (1.0f / 18.0f);
-            const float dah = -rt.ah * (1.0f / 20.0f), dbh = rt.bh * (1.0f - rt.bh) * 0.1f;
-            const float dan = 0.01f * ratio_u_deriv((Vs + 55.0f) * 0.1f), dbn = -rt.bn * (1.0f / 80.0f);
+            const float kb0 = cb[st] * S.lam[i] + (st < NST - 1 ? ca[st] * S.yprev[i] : 0.0f);
+            const float q = kb0 * P[NP_C * N + i];
             const float m3h = ms * ms * ms * hs, n4 = ns * ns * ns * ns;
             const float gNa = P[NP_GNA * N + i], gK = P[NP_GK * N + i], gL = P[NP_GL * N + i], gKL = P[NP_GKL * N + i];
-            const float ENa = P[NP_ENA * N + i], EK = P[NP_EK * N + i], EL = P[NP_EL * N + i], EKL = P[NP_EKL * N + i];
-            const float diion = gNa * m3h + gK * n4 + gL + gKL;
-            float uV = q * (-diion - S.sA[st * N + i]);
-            uV = fmaf(kb[1], dam * (1.0f - ms) - dbm * ms, uV);
-            uV = fmaf(kb[2], dah * (1.0f - hs) - dbh * hs, uV);
-            uV = fmaf(kb[3], dan * (1.0f - ns) - dbn * ns, uV);
-            S.uV[i] = uV;
-            S.yprev[N + i] = -q * gNa * 3.0f * ms * ms * hs * (Vs - ENa) - kb[1] * (rt.am + rt.bm);
-            S.yprev[2 * N + i] = -q * gNa * ms * ms * ms * (Vs - ENa) - kb[2] * (rt.ah + rt.bh);
-            S.yprev[3 * N + i] = -q * gK * 4.0f * ns * ns * ns * (Vs - EK) - kb[3] * (rt.an + rt.bn);
-            double *g = S.gp + 9 * i;
-            g[NP_C] += (double)(-q * S.sfv[st * N + i]);
-            g[NP_GNA] += (double)(-q * m3h * (Vs - ENa));
-            g[NP_GK] += (double)(-q * n4 * (Vs - EK));
-            g[NP_GL] += (double)(-q * (Vs - EL));
-            g[NP_GKL] += (double)(-q * (Vs - EKL));
-            g[NP_ENA] += (double)(q * gNa * m3h);
-            g[NP_EK] += (double)(q * gK * n4);
-            g[NP_EL] += (double)(q * gL);
-            g[NP_EKL] += (double)(q * gKL);
+            const float ENa = P[NP_ENA * N + i], EK = P[NP_EK * N + i];
+            if (!gates) {
+                const float EL = P[NP_EL * N + i], EKL = P[NP_EKL * N + i];
+                S.ab[st * N + i] = make_float2(q * Vs, q);
+                // compensated FP32 sums (hi, lo) of the stage terms
+                float2 *g = S.gp + 9 * i;
+                auto add = [&](int x, float term) {
+                    float2 c = g[x];
+                    ext_add(c.x, c.y, term);
+                    g[x] = c;
+                };
+                add(NP_C, -q * S.sfv[st * N + i]);
+                add(NP_GNA, -q * m3h * (Vs - ENa));
+                add(NP_GK, -q * n4 * (Vs - EK));
+                add(NP_GL, -q * (Vs - EL));
+                add(NP_GKL, -q * (Vs - EKL));
+                add(NP_ENA, q * gNa * m3h);
+                add(NP_EK, q * gK * n4);
+                add(NP_EL, q * gL);
+                add(NP_EKL, q * gKL);
+            } else {
+                float kb[4];
+                kb[0] = kb0;
+#pragma unroll
+                for (int x = 1; x < 4; ++x) {
+                    const int ix = x * N + i;
+                    kb[x] = cb[st] * S.lam[ix] + (st < NST - 1 ? ca[st] * S.yprev[ix] : 0.0f);
+                }
+                const Rates rt = hh_rates(Vs);
+                const float dam = 0.1f * ratio_u_deriv((Vs + 40.0f) * 0.1f), dbm = -rt.bm * (1.0f / 18.0f);
+                const float dah = -rt.ah * (1.0f / 20.0f), dbh = rt.bh * (1.0f - rt.bh) * 0.1f;
+                const float dan = 0.01f * ratio_u_deriv((Vs + 55.0f) * 0.1f), dbn = -rt.bn * (1.0f / 80.0f);
+                const float diion = gNa * m3h + gK * n4 + gL + gKL;
+                float uV = q * (-diion - S.sA[st * N + i]);
+                uV = fmaf(kb[1], dam * (1.0f - ms) - dbm * ms, uV);
+                uV = fmaf(kb[2], dah * (1.0f - hs) - dbh * hs, uV);
+                uV = fmaf(kb[3], dan * (1.0f - ns) - dbn * ns, uV);
+                S.uV[i] = uV;
+                S.yprev[N + i] = -q * gNa * 3.0f * ms * ms * hs * (Vs - ENa) - kb[1] * (rt.am + rt.bm);
+                S.yprev[2 * N + i] = -q * gNa * ms * ms * ms * (Vs - ENa) - kb[2] * (rt.ah + rt.bh);
+                S.yprev[3 * N + i] = -q * gK * 4.0f * ns * ns * ns * (Vs - EK) - kb[3] * (rt.an + rt.bn);
+            }
         }
         __syncthreads();
         // B) column sums of the synaptic current's Jacobian
         column_sums(a, S, st);
         __syncthreads();
-        // C) owners: gate-pair products and the presynaptic voltage term
-        for (int i = tid; i < N; i += nthr) {
+        // C) one unit per gate pair (its adjoints and its term of the
+        // presynaptic potential's adjoint), then one per neuron (the terms in
+        // type order)
+        for (int p = tid; p < M; p += nthr) {
+            const int i = p / nt, t = p - i * nt;
             const float Vs = S.sV[st * N + i];
+            const float *sp = stab + t * 9;
+            float C = 0.0f;  // the pair's column sum: its items' partials in item order
+            for (int q = S.ib[p]; q < S.ib[p + 1]; ++q) C += S.pa[q];
+            const int ir = 4 * N + p, is = 4 * N + M + p;
+            const float kbr = cb[st] * S.lam[ir] + (st < NST - 1 ? ca[st] * S.yprev[ir] : 0.0f);
+            const float kbs = cb[st] * S.lam[is] + (st < NST - 1 ? ca[st] * S.yprev[is] : 0.0f);
+            const float rs = S.sr[st * M + p], ss = S.ss[st * M + p];
+            const float T = transmitter(Vs, sp[SP_VP], sp[SP_KP]);
+            const float dT = T * (1.0f - T) * sp[SP_KP];  // table holds 1/Kp
+            float ur = -(sp[SP_A] * T + sp[SP_B]) * kbr, us = 0.0f;
+            if (sp[SP_KIND] != 0.0f) {
+                const float s2 = ss * ss, s4 = s2 * s2, den = s4 + sp[SP_KD];
+                const float dG = __fdiv_rn(4.0f * s2 * ss * sp[SP_KD], den * den);
+                ur = fmaf(sp[SP_K3], kbs, ur);
+                us = -C * dG - sp[SP_K4] * kbs;
+            } else {
+                ur -= C;
+            }
+            S.uvc[p] = make_float2(kbr * sp[SP_A] * dT, 1.0f - rs);
+            S.yprev[ir] = ur;
+            S.yprev[is] = us;
+            S.ysum[ir] += ur;
+            S.ysum[is] += us;
+        }
+        __syncthreads();
+        for (int i = tid; i < N; i += nthr) {
             float uV = S.uV[i];
             for (int t = 0; t < nt; ++t) {
-                const int p = i * nt + t;
-                const float *sp = stab + t * 9;
-                float C = 0.0f;  // the pair's column sum: its items' partials in item order
-                for (int q = S.ib[p]; q < S.ib[p + 1]; ++q) C += S.pa[q];
-                const int ir = 4 * N + p, is = 4 * N + M + p;
-                const float kbr = cb[st] * S.lam[ir] + (st < NST - 1 ? ca[st] * S.yprev[ir] : 0.0f);
-                const float kbs = cb[st] * S.lam[is] + (st < NST - 1 ? ca[st] * S.yprev[is] : 0.0f);
-                const float rs = S.sr[st * M + p], ss = S.ss[st * M + p];
-                const float T = transmitter(Vs, sp[SP_VP], sp[SP_KP]);
-                const float dT = T * (1.0f - T) * sp[SP_KP];  // table holds 1/Kp
-                float ur = -(sp[SP_A] * T + sp[SP_B]) * kbr, us = 0.0f;
-                if (sp[SP_KIND] != 0.0f) {
-                    const float s2 = ss * ss, s4 = s2 * s2, den = s4 + sp[SP_KD];
-                    const float dG = __fdiv_rn(4.0f * s2 * ss * sp[SP_KD], den * den);
-                    ur = fmaf(sp[SP_K3], kbs, ur);
-                    us = -C * dG - sp[SP_K4] * kbs;
-                } else {
-                    ur -= C;
-                }
-                uV = fmaf(kbr * sp[SP_A] * dT, 1.0f - rs, uV);
-                S.yprev[ir] = ur;
-                S.yprev[is] = us;
-                S.ysum[ir] += ur;
-                S.ysum[is] += us;
+                const float2 c = S.uvc[i * nt + t];
+                uV = fmaf(c.x, c.y, uV);
             }
             S.yprev[i] = uV;
             S.ysum[i] += uV;
@@ -401,8 +424,7 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
             S.ysum[2 * N + i] += S.yprev[2 * N + i];
             S.ysum[3 * N + i] += S.yprev[3 * N + i];
         }
-        // the next stage's part A reads only owner-written values; its part B
-        // reads ab after the barrier that follows part A
+        __syncthreads();  // the next stage's part A reads yprev of both units of each neuron
     }
     // weight gradients of the step: dL/dw_k += sum_s -G_p^(s) q_i^(s) (V_i^(s) - E_p),
     // into the per-segment FP32 partial of each column slot (the partials of
@@ -586,7 +608,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     S.ysum = (float *)take(p, 4LL * a.R);
     S.ab = (float2 *)take(p, 32LL * N);
     S.uV = (float *)take(p, 4LL * N);
-    S.gp = (double *)take(p, 72LL * N);
+    S.gp = (float2 *)take(p, 72LL * N);
+    S.uvc = (float2 *)take(p, 8LL * M);
     S.Ep = (float *)take(p, 4LL * M);
     S.prm = (float *)take(p, 36LL * N);
     S.iext = (float *)take(p, 4LL * N);
@@ -603,7 +626,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         for (int x = 1; x < PSST_NEURON_NPARAM; ++x) S.prm[x * N + i] = pp[x];
         S.inp[i] = v.i_const[a.n0 + i];
         S.inp[N + i] = v.pulse_amp ? v.pulse_amp[a.n0 + i] : 0.0f;
-        for (int x = 0; x < 9; ++x) S.gp[9 * i + x] = 0.0;
+        for (int x = 0; x < 9; ++x) S.gp[9 * i + x] = make_float2(0.0f, 0.0f);
         S.uV[i] = 0.0f;
     }
     for (int q = tid; q < M; q += nthr) S.Ep[q] = stab[(q % nt) * 9 + SP_E];
@@ -774,7 +797,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
         }
     }
     for (int i = tid; i < N; i += nthr) {
-        for (int x = 0; x < 9; ++x) av.gp_neuron[(long long)(a.n0 + i) * 9 + x] = S.gp[9 * i + x];
+        for (int x = 0; x < 9; ++x) {
+            const float2 c = S.gp[9 * i + x];
+            av.gp_neuron[(long long)(a.n0 + i) * 9 + x] = (double)c.x + (double)c.y;
+        }
         for (int x = 0; x < 4; ++x) av.grad_y0[(long long)x * v.N + a.n0 + i] = S.lam[x * N + i];
     }
 }
