@@ -108,6 +108,7 @@ struct AdjSmem {
     float *uV;                 // [N] partial uV
     float2 *gp;                // [N][9] neuron parameter gradients, compensated FP32 sums (hi, lo)
     float2 *uvc;               // [M] each pair's term of its presynaptic potential's adjoint
+    float2 *uvg;               // [3][N] each gate's term of its neuron's potential adjoint (kb, derivative)
     float *Ep;                 // [M] reversal potential of each pair's type
     float *prm;                // [9][N] (row 0: 1/C)
     float *iext, *inp;         // [N], [2][N]
@@ -132,6 +133,7 @@ __host__ __device__ inline long long adj_smem_bytes(int N, int M, int n_items, i
     b += 32LL * N + 4LL * N;             // ab, uV
     b += 8LL * 9 * N;                    // gp (float2)
     b += 8LL * M;                        // uvc
+    b += 24LL * N;                       // uvg
     b += 4LL * 9 * N + 4LL * 3 * N;      // prm, iext, inp
     b += 4LL * M;                        // Ep
     b += 16 * 32;                        // alignment slack
@@ -323,11 +325,14 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
     const int tid = threadIdx.x, nthr = blockDim.x, N = a.N, nt = a.nt, M = a.M;
 #pragma unroll 1
     for (int st = NST - 1; st >= 0; --st) {
-        // A) two units per neuron: the potential's products (ab) and parameter
-        // gradients, and the gates' products (uV partial, gate adjoints)
-        for (int u = tid; u < 2 * N; u += nthr) {
-            const bool gates = u >= N;
-            const int i = gates ? u - N : u;
+        // A) four units per neuron: the potential's products (ab, the base of
+        // uV) and parameter gradients, and one per gate variable (its term of
+        // uV, kept for part C, and its adjoint); whole warps per unit kind
+        const int Nw = (N + 31) & ~31;
+        for (int u = tid; u < 4 * Nw; u += nthr) {
+            const int x = u / Nw, i = u - x * Nw;  // x = 0: potential, 1..3: gate m, h, n
+            if (i >= N) continue;
+            const bool gates = x > 0;
             const float Vs = S.sV[st * N + i], ms = S.sm[st * N + i], hs = S.sh[st * N + i], ns = S.sn[st * N + i];
             const float *P = S.prm;
             const float kb0 = cb[st] * S.lam[i] + (st < NST - 1 ? ca[st] * S.yprev[i] : 0.0f);
@@ -338,6 +343,8 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
             if (!gates) {
                 const float EL = P[NP_EL * N + i], EKL = P[NP_EKL * N + i];
                 S.ab[st * N + i] = make_float2(q * Vs, q);
+                const float diion = gNa * m3h + gK * n4 + gL + gKL;
+                S.uV[i] = q * (-diion - S.sA[st * N + i]);
                 // compensated FP32 sums (hi, lo) of the stage terms
                 float2 *g = S.gp + 9 * i;
                 auto add = [&](int x, float term) {
@@ -355,26 +362,34 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
                 add(NP_EL, q * gL);
                 add(NP_EKL, q * gKL);
             } else {
-                float kb[4];
-                kb[0] = kb0;
-#pragma unroll
-                for (int x = 1; x < 4; ++x) {
-                    const int ix = x * N + i;
-                    kb[x] = cb[st] * S.lam[ix] + (st < NST - 1 ? ca[st] * S.yprev[ix] : 0.0f);
+                // gate x: its rate functions (those of hh_rates) and their derivatives
+                const int ix = x * N + i;
+                const float kbx = cb[st] * S.lam[ix] + (st < NST - 1 ? ca[st] * S.yprev[ix] : 0.0f);
+                float al, be, dal, dbe, g, yp;
+                if (x == 1) {
+                    al = ratio_u((Vs + 40.0f) * 0.1f);
+                    be = 4.0f * expf((Vs + 65.0f) * (-1.0f / 18.0f));
+                    dal = 0.1f * ratio_u_deriv((Vs + 40.0f) * 0.1f);
+                    dbe = -be * (1.0f / 18.0f);
+                    g = ms;
+                    yp = -q * gNa * 3.0f * ms * ms * hs * (Vs - ENa);
+                } else if (x == 2) {
+                    al = 0.07f * expf((Vs + 65.0f) * (-1.0f / 20.0f));
+                    be = __frcp_rn(1.0f + expf((Vs + 35.0f) * (-0.1f)));
+                    dal = -al * (1.0f / 20.0f);
+                    dbe = be * (1.0f - be) * 0.1f;
+                    g = hs;
+                    yp = -q * gNa * ms * ms * ms * (Vs - ENa);
+                } else {
+                    al = 0.1f * ratio_u((Vs + 55.0f) * 0.1f);
+                    be = 0.125f * expf((Vs + 65.0f) * (-1.0f / 80.0f));
+                    dal = 0.01f * ratio_u_deriv((Vs + 55.0f) * 0.1f);
+                    dbe = -be * (1.0f / 80.0f);
+                    g = ns;
+                    yp = -q * gK * 4.0f * ns * ns * ns * (Vs - EK);
                 }
-                const Rates rt = hh_rates(Vs);
-                const float dam = 0.1f * ratio_u_deriv((Vs + 40.0f) * 0.1f), dbm = -rt.bm * (1.0f / 18.0f);
-                const float dah = -rt.ah * (1.0f / 20.0f), dbh = rt.bh * (1.0f - rt.bh) * 0.1f;
-                const float dan = 0.01f * ratio_u_deriv((Vs + 55.0f) * 0.1f), dbn = -rt.bn * (1.0f / 80.0f);
-                const float diion = gNa * m3h + gK * n4 + gL + gKL;
-                float uV = q * (-diion - S.sA[st * N + i]);
-                uV = fmaf(kb[1], dam * (1.0f - ms) - dbm * ms, uV);
-                uV = fmaf(kb[2], dah * (1.0f - hs) - dbh * hs, uV);
-                uV = fmaf(kb[3], dan * (1.0f - ns) - dbn * ns, uV);
-                S.uV[i] = uV;
-                S.yprev[N + i] = -q * gNa * 3.0f * ms * ms * hs * (Vs - ENa) - kb[1] * (rt.am + rt.bm);
-                S.yprev[2 * N + i] = -q * gNa * ms * ms * ms * (Vs - ENa) - kb[2] * (rt.ah + rt.bh);
-                S.yprev[3 * N + i] = -q * gK * 4.0f * ns * ns * ns * (Vs - EK) - kb[3] * (rt.an + rt.bn);
+                S.uvg[(x - 1) * N + i] = make_float2(kbx, dal * (1.0f - g) - dbe * g);
+                S.yprev[ix] = yp - kbx * (al + be);
             }
         }
         __syncthreads();
@@ -414,6 +429,11 @@ __device__ void rev_step(const AdjNet &a, const AdjSmem &S, const float *stab, c
         __syncthreads();
         for (int i = tid; i < N; i += nthr) {
             float uV = S.uV[i];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const float2 c = S.uvg[x * N + i];
+                uV = fmaf(c.x, c.y, uV);
+            }
             for (int t = 0; t < nt; ++t) {
                 const float2 c = S.uvc[i * nt + t];
                 uV = fmaf(c.x, c.y, uV);
@@ -610,6 +630,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(NetView v, AdjView av,
     S.uV = (float *)take(p, 4LL * N);
     S.gp = (float2 *)take(p, 72LL * N);
     S.uvc = (float2 *)take(p, 8LL * M);
+    S.uvg = (float2 *)take(p, 24LL * N);
     S.Ep = (float *)take(p, 4LL * M);
     S.prm = (float *)take(p, 36LL * N);
     S.iext = (float *)take(p, 4LL * N);
