@@ -218,7 +218,8 @@ def _with_duplicate_synapses(spec, seed=9):
 
 def test_duplicate_synapses_forward_and_adjoint():
     # two synapses of one pair in a row: the forward's per-pair gates and the
-    # adjoint's column sums (atomic path) against the oracle
+    # adjoint's column sums (two slots of one column item from the same row)
+    # against the oracle
     from paper_1906_03958_gb300 import psst
     from tests.helpers import step_error
     _, base = _spec(seed=11)
@@ -285,3 +286,25 @@ def test_autograd_two_windows_before_one_backward():
         assert grad_error(p1.grad.cpu().numpy(), r1[1].cpu().numpy()) <= 1e-5, record
         assert grad_error(w2.grad.cpu().numpy(), r2[0].cpu().numpy()) <= 1e-5, record
         assert grad_error(p2.grad.cpu().numpy(), r2[1].cpu().numpy()) <= 1e-5, record
+
+
+def test_adjoint_sparse_columns_against_oracle():
+    # the antennal-lobe network (p = 0.5 per type pair, not dense): each
+    # pair's column holds a random subset of rows, cut into several column
+    # items of several chunks (rows dealt round-robin over the items), so the
+    # sweep's gathers and item-order sums run on irregular columns
+    spec = ng.antennal_lobe(seed=21)
+    spec.pulse_on[:] = 5
+    spec.pulse_off[:] = 10_000
+    spec.pulse_amp[:] = np.where(spec.pulse_amp > 0, 8.0, 0.0)
+    N = spec.n_neurons
+    cnt = np.bincount(spec.pre * spec.syn_params.shape[0] + spec.syn_type)
+    assert cnt.max() > 16 and np.count_nonzero((cnt > 0) & (cnt < N - 1)) > 0  # partial columns
+    rng = np.random.default_rng(7)
+    nsteps, stride = 300, 10
+    g = rng.standard_normal((nsteps // stride, N))
+    gy64, gw64, gp64 = oracle.adjoint(spec, oracle.rest_state(spec), nsteps, g, stride, ckpt=100)
+    gw, gp, gy = _gpu_adjoint(spec, nsteps, g, stride, ckpt=100)
+    assert grad_error(gw, gw64) <= GRAD_TOL, grad_error(gw, gw64)
+    assert grad_error(gp, gp64) <= GRAD_TOL, grad_error(gp, gp64)
+    assert grad_error(gy.ravel(), gy64[:4 * N]) <= GRAD_TOL
