@@ -282,7 +282,9 @@ int psst_record_checkpoints(psst_net *h, int32_t every, int64_t max_steps);
    kernel integrates the span once, recording the full state and its
    remainders every ckpt_every steps (the record ring is not written), and
    each segment is recomputed from its checkpoint; the handle allocates the
-   storage on first use and grows it as needed.  The recomputation uses the
+   storage on first use and grows it as needed.  The first call also reads
+   the connectivity back (synchronous copies) to plan the sweep's
+   synapses by presynaptic column; later calls reuse the plan.  The recomputation uses the
    adjoint's own arithmetic, so its trajectory drifts slowly from the forward
    kernel's: spacings of up to about 1000 steps keep FP32 gradients within
    1e-3 of the exact map's on 20,000-step spiking spans.
