@@ -50,7 +50,12 @@
 // the pair's owner adds its items' partials in item order (fixed order,
 // reproducible).  The weight gradients are summed over each step's stages
 // in one pass over the column items, into an FP32 partial per segment,
-// then into an FP64 total.
+// then into an FP64 total.  Per stage the sweep runs its per-neuron work as
+// independent units on separate threads: part A (the potential's products
+// and parameter gradients; each gate variable's rates, its adjoint and its
+// term of uV), the column sums, part C (each pair's adjoints and its term of
+// uV; then each neuron adds its terms in a fixed order).  The parameter
+// gradients are compensated FP32 sums, combined in FP64 at the end.
 #include <cuda_runtime.h>
 
 #include "psst_device.cuh"
